@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""FWIME operator benchmark on one GB300 (or N, shot-sharded, weak scaling).
+
+One step = the extended Born operator B~ followed by its adjoint B~* (extended
+imaging condition) over every shot of the workload, all shots batched
+(Barnier et al., Theory section Eqs. 1-5; the computational-cost analysis
+counts each as two wavefield propagations, Eq. 10).  Default workload: the
+Marmousi2-shaped synthetic stand-in, 350 x 1700 at 10 m, 100 shots, 850
+receivers, nt = 4000, dt = 0.8 ms, nh = 21 subsurface offsets, sponge 50.
+
+value = useful grid-point updates per second: 4 propagations x shots x
+(padded NZ x NX) x (nt - 1) per step (the recomputation of the background
+wavefield is not counted as useful work), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "Gpt/s per propagation & FWIME-gradient shots/s, batched vs plain; %HBM peak"
+UNIT = "Gupd/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nshot", type=int, default=100)
+    ap.add_argument("--nt", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    return synth.marmousi2(nshot=args.nshot, nt=args.nt)
+
+
+def updates_per_step(wl) -> float:
+    NZ, NX = wl.padded
+    return 4.0 * wl.nshot * NZ * NX * (wl.nt - 1)
+
+
+def config(wl, args, n):
+    NZ, NX = wl.padded
+    return {"workload": wl.name, "nz": wl.nz, "nx": wl.nx, "padded": [NZ, NX], "dx_m": wl.dx, "dt_s": wl.dt,
+            "nt": wl.nt, "nshot": wl.nshot, "nrec": wl.nrec, "nh": wl.nh, "sponge": wl.W,
+            "operators": "B~ then B~* per step (extended Born + extended imaging), all shots batched",
+            "global_batch": wl.nshot * n, "parallelism": f"shots x{n}" if n > 1 else "single GPU",
+            "l2": "inputs larger than L2 (wavefields of 100 shots, tens of GB), no flush needed"}
+
+
+# --------------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if re.match(r"^[0-9.]+$", r[3])]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ oracle CPU
+
+def oracle_sample(wl, nt_sample: int, nshot_sample: int, threads: int):
+    """Times the FP64 oracle (as it stands) on B~ + B~* for a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    og = oracle.Grid(nz=wl.nz, nx=wl.nx, W=wl.W, nt=nt_sample, dt=wl.dt, dx=wl.dx, nh=wl.nh)
+    geo = oracle.Geometry(wl.src_iz[:nshot_sample], wl.src_ix[:nshot_sample], wl.rec_iz, wl.rec_ix)
+    rng = np.random.default_rng(synth.SEED0 + 11)
+    pt = rng.standard_normal((wl.nh, wl.nz, wl.nx))
+    w = np.asarray(wl.w[:nt_sample], dtype=np.float64)
+    v = wl.v.astype(np.float64)
+    t0 = time.perf_counter()
+    d = oracle.born_ext(og, v, geo, w, pt, nthreads=threads)
+    oracle.born_ext_adj(og, v, geo, w, d, nthreads=threads)
+    dt = time.perf_counter() - t0
+    NZ, NX = wl.padded
+    upd = 4.0 * nshot_sample * NZ * NX * (nt_sample - 1)
+    return upd / dt / 1e9, dt, f"{nshot_sample} shots x nt={nt_sample} of the {wl.name} grid (B~ + B~*)"
+
+
+def cpu_baseline(wl):
+    threads = max(1, min(os.cpu_count() or 1, 8))
+    val, dt, sample = oracle_sample(wl, 32, threads, threads)
+    return {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args)
+    threads = max(1, min(os.cpu_count() or 1, 8))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        val, dt, sample = oracle_sample(wl, 16, threads, threads)
+        if i >= args.warmup:
+            vals.append((val, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = statistics.mean(dt for _, dt in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": config(wl, args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the stencil kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2206_02362_gb300", "csrc", "k_prop.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "k_prop_marmousi2_ncu.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"k_prop\.cu sha256\[:16\]:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != h:
+        return None
+    return float(t.group(1))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_2206_02362_gb300 as fw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = workload(args)
+    grid = fw.Grid(nz=wl.nz, nx=wl.nx, sponge=wl.W, nt=wl.nt, dt=wl.dt, dx=wl.dx, nh=wl.nh)
+    geom = fw.Geometry(wl.src_iz, wl.src_ix, wl.rec_iz, wl.rec_ix)
+    rng = np.random.default_rng(synth.SEED0 + 11 + rank)
+    pt_h = rng.standard_normal((wl.nh, wl.nz, wl.nx)).astype(np.float32)
+    w_h = np.ascontiguousarray(np.broadcast_to(wl.w.astype(np.float32), (wl.nshot, wl.nt)))
+    dev = torch.device("cuda", local)
+    v = torch.from_numpy(wl.v).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    pt = torch.from_numpy(pt_h).to(dev)
+    d = torch.zeros((wl.nshot, wl.nt, wl.nrec), device=dev)
+    img = torch.zeros((wl.nh, wl.nz, wl.nx), device=dev)
+    ctx = fw.Context(grid, geom, profile=1)
+    launches = [0]
+
+    def step(c, vv, ww, pp, dd, ii):
+        c.born_ext(vv, ww, pp, dd, sync=False)
+        n = c.launches
+        c.born_ext_adj(vv, ww, dd, ii, sync=False)
+        launches[0] += n + c.launches
+        if world > 1:
+            dist.all_reduce(ii)        # images summed over the shots of all ranks
+
+    for _ in range(args.warmup):
+        step(ctx, v, w, pt, d, img)
+        ctx.sync()
+    ctx.profile_read(reset=True)
+    launches[0] = 0
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = Clocks(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(ctx, v, w, pt, d, img)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.sync()
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = updates_per_step(wl) * world / (ms_step * 1e-3) / 1e9
+    prof = ctx.profile_read(reset=True)
+    kern_ms = sum(p["ms"] for p in prof.values())
+    pk = prof["prop"]
+    peak, peak_kind = peaks()
+    achieved = pk["bytes"] / (pk["ms"] * 1e-3) / 1e9 if pk["ms"] > 0 else None
+    traffic = ncu_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_prop (wave-equation time step, forward and adjoint)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic,
+                "launches": pk["launches"], "avg_launch_us": 1e3 * pk["ms"] / max(pk["launches"], 1),
+                "algorithmic_bytes_per_launch": pk["bytes"] / max(pk["launches"], 1),
+                "time_share": {k: round(p["ms"] / kern_ms, 4) for k, p in prof.items()} if kern_ms else None,
+                "bytes_rule": "12 B per shot-point (q^n, q^n-1 in, q^n+1 out) + 4 B per output field "
+                              "(D2t, local sources) + 4 B per grid point per launch for c (shared by all shots); "
+                              "padded NZ x NX points"}
+    shots_per_s = wl.nshot * world / (ms_step * 1e-3)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Marmousi2-shaped stand-in)",
+            "config": config(wl, args, world), "roofline": roofline, "gpu_launches": launches[0],
+            "clocks": clocks, "shots_per_s": shots_per_s,
+            "executed_gupd_s": value * 5.0 / 4.0}
+
+    # plain path: one shot per launch, host-driven steps, same per-shot work
+    if not args.no_plain and rank == 0:
+        nps = 2
+        geom2 = fw.Geometry(wl.src_iz[:nps], wl.src_ix[:nps], wl.rec_iz, wl.rec_ix)
+        with fw.Context(grid, geom2, plain=1) as cp:
+            d2 = torch.zeros((nps, wl.nt, wl.nrec), device=dev)
+            step(cp, v, w[:nps].contiguous(), pt, d2, img)
+            cp.sync()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step(cp, v, w[:nps].contiguous(), pt, d2, img)
+            cp.sync()
+            tp = time.perf_counter() - t0
+        line["plain"] = {"shots_per_s": nps / tp, "sample": f"{nps} shots, one shot per launch, no graph"}
+        line["batched_vs_plain"] = shots_per_s / world / (nps / tp)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        ctx.set_option("profile", 0)
+        ctx.set_option("host_io", 1)
+        vh = torch.from_numpy(wl.v).pin_memory()
+        wh = torch.from_numpy(w_h).pin_memory()
+        ph = torch.from_numpy(pt_h).pin_memory()
+        dh = torch.zeros((wl.nshot, wl.nt, wl.nrec)).pin_memory()
+        ih = torch.zeros((wl.nh, wl.nz, wl.nx)).pin_memory()
+        arr = lambda t: t.numpy()  # noqa: E731
+        ctx.born_ext(arr(vh), arr(wh), arr(ph), arr(dh))     # warm (staging allocation)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = 1
+        for _ in range(ne):
+            ctx.born_ext(arr(vh), arr(wh), arr(ph), arr(dh))
+            ctx.born_ext_adj(arr(vh), arr(wh), arr(dh), arr(ih))
+        te = (time.perf_counter() - t0) / ne
+        nb = 4
+        h2d = 2 * (wl.v.nbytes + w_h.nbytes) + pt_h.nbytes + dh.numel() * nb
+        d2h = dh.numel() * nb + ih.numel() * nb
+        line["e2e"] = {"value": updates_per_step(wl) / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "seconds_per_step": te}
+        ctx.set_option("host_io", 0)
+
+    if not args.no_cpu and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

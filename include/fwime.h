@@ -1,0 +1,179 @@
+/*
+ * libfwime -- C ABI of the GB300 (sm_103a) implementation of the FWIME operators.
+ *
+ * Barnier, Biondi, Clapp & Biondi, "Full waveform inversion by model extension:
+ * practical applications" (arXiv 2206.02362).  Every entry point below applies
+ * one operator named in the paper's Theory section:
+ *   fwime_forward       f(m)            nonlinear forward modelling, Eq. 1
+ *   fwime_born          B(m) dm         non-extended Born modelling, Eq. 8
+ *   fwime_born_adj      B*(m) d         its adjoint (Born gradient operator), Eq. 8
+ *   fwime_born_ext      B~(m) p~        Born extended with horizontal subsurface
+ *                                       offsets, Eq. 1 (data-correcting term)
+ *   fwime_born_ext_adj  B~*(m) d        extended imaging condition, Eqs. 2-5
+ *   fwime_tomo          T(m,p~) dm      data-space tomographic operator, Eq. 9
+ *   fwime_tomo_adj      T*(m,p~) d      its adjoint (tomographic gradient), Eq. 9
+ *   fwime_gradient      Phi_eps and B* r + T* r with r = f + B~ p~ - d_obs at a
+ *                       fixed p~ (Eqs. 1, 7-9), the spline operator S = I.
+ *
+ * Discretisation (the paper defers it to a companion paper; this library fixes
+ * one reading and documents it): 2-D acoustic constant-density wave equation,
+ * 2nd order in time, 8th order in space on a uniform grid; a Cerjan-type sponge
+ * of `sponge` points on every side plus a 4-point zero halo; point sources with
+ * amplitude w[n]/(dx dz); receivers record the pressure at time n dt, n=0..nt-1
+ * (sample 0 is always zero).  Subsurface offsets h = (ih - (nh-1)/2) dx act
+ * along x with the symmetric convention: p~(x, h) couples the source wavefield
+ * at x-h to the receiver side at x+h.
+ *
+ * Memory layout, all row-major with x fastest, FP32:
+ *   v        [nz][nx]            velocity in m/s (the model m of the paper, S = I)
+ *   w        [nshot][nt]         source wavelet of each shot
+ *   d        [nshot][nt][nrec]   data (shot records), time-major per shot
+ *   dv, grad [nz][nx]            model-space perturbation / gradient
+ *   pt       [nh][nz][nx]        extended perturbation p~ (on the FD grid)
+ *
+ * Ownership: every float pointer is caller-owned and is a DEVICE pointer unless
+ * the context was switched to host I/O with FWIME_OPT_HOST_IO, in which case it
+ * is a host pointer (pinned memory recommended) and the library copies through
+ * its own device staging buffers.  The library never frees caller memory.  The
+ * context owns its workspace (wavefields, rings, checkpoints, status word).
+ *
+ * Execution: calls enqueue work on the context's CUDA stream and return without
+ * waiting, except that with FWIME_OPT_HOST_IO the call waits for its outputs.
+ * Device-side errors are latched in a status word read by fwime_sync().
+ *
+ * Errors: every int-returning call returns FWIME_OK (0) or a negative code;
+ * no exception, abort or trap crosses the ABI.  fwime_last_error_detail()
+ * returns a one-line description of the last failure on that context.
+ */
+#ifndef FWIME_H
+#define FWIME_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FWIME_OK        0
+#define FWIME_EINVAL   -1   /* bad argument, shape or geometry */
+#define FWIME_ENOMEM   -2   /* workspace does not fit the budget or cudaMalloc failed */
+#define FWIME_ECFL     -3   /* dt * vmax * sqrt(6.5016 (1/dx^2 + 1/dz^2)) >= 2 */
+#define FWIME_ECUDA    -4   /* a CUDA runtime call failed */
+#define FWIME_ETIMEOUT -5   /* a device-side bounded wait gave up */
+#define FWIME_EBUSY    -6   /* the context is in use (graph capture in progress) */
+
+typedef struct fwime_ctx fwime_ctx;
+
+/* Physical grid nz x nx at spacing dz, dx; `sponge` absorbing points per side;
+ * nt time samples at dt; nh subsurface offsets (odd, 1 = non-extended). */
+typedef struct {
+    int nz, nx, sponge, nt, nh;
+    float dz, dx, dt;
+} fwime_grid;
+
+/* One point source per shot and a fixed receiver spread, physical-grid indices.
+ * The arrays are host memory and are copied by fwime_create. */
+typedef struct {
+    int nshot;
+    const int *src_iz, *src_ix;
+    int nrec;
+    const int *rec_iz, *rec_ix;
+} fwime_geom;
+
+/* Options for fwime_set_option / fwime_get_option. */
+enum {
+    FWIME_OPT_SHOTS_PER_BATCH = 1, /* shots advanced together per launch; 0 = as many as fit */
+    FWIME_OPT_SEGMENT = 2,         /* checkpoint/ring segment length K in time steps; 0 = auto */
+    FWIME_OPT_PLAIN = 3,           /* 1 = plain path: one shot per launch, host-driven steps */
+    FWIME_OPT_GRAPH = 4,           /* 1 = capture each operator call in a CUDA graph and replay */
+    FWIME_OPT_HOST_IO = 5,         /* 1 = I/O pointers are host memory */
+    FWIME_OPT_ZCHUNK = 6,          /* rows per warp in the stencil kernel; 0 = auto */
+    FWIME_OPT_LAUNCHES = 7,        /* read-only: kernels launched by the last operator call */
+    FWIME_OPT_WORKSPACE = 8,       /* read-only: bytes of device workspace held */
+    FWIME_OPT_PROFILE = 9          /* 1 = bracket every kernel launch with CUDA events (no graphs) */
+};
+
+/* Kernel families, for fwime_profile_read. */
+enum {
+    FWIME_K_PROP = 0,     /* wave-equation time step (forward and adjoint) */
+    FWIME_K_SCATTER = 1,  /* extended scattering and its transpose */
+    FWIME_K_IMAGE = 2,    /* imaging-condition reductions */
+    FWIME_K_POINTS = 3,   /* receiver recording / injection */
+    FWIME_K_OTHER = 4     /* model preparation, copies, reductions */
+};
+
+/* Operators, for fwime_workspace_bytes. */
+enum {
+    FWIME_OP_FORWARD = 0, FWIME_OP_BORN, FWIME_OP_BORN_ADJ, FWIME_OP_BORN_EXT,
+    FWIME_OP_BORN_EXT_ADJ, FWIME_OP_TOMO, FWIME_OP_TOMO_ADJ, FWIME_OP_GRADIENT
+};
+
+/* Creates a context on the current CUDA device.  `max_workspace_bytes` caps the
+ * device memory the context may hold (0 = no cap); `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Returns FWIME_EINVAL for an
+ * invalid grid/geometry (receivers or sources outside the physical grid, nh
+ * even, nt < 2, non-positive spacing). */
+int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo,
+                 size_t max_workspace_bytes, void *cuda_stream);
+
+/* Device bytes operator `op` needs for `shots_per_batch` shots advanced
+ * together with segment length `segment` (0 = the defaults). */
+int fwime_workspace_bytes(const fwime_grid *g, const fwime_geom *geo, int op,
+                          int shots_per_batch, int segment, size_t *bytes);
+
+int fwime_set_option(fwime_ctx *ctx, int option, long long value);
+int fwime_get_option(fwime_ctx *ctx, int option, long long *value);
+
+/* f(m): d[nshot][nt][nrec] = recorded pressure of every shot (Eq. 1). */
+int fwime_forward(fwime_ctx *ctx, const float *v, const float *w, float *d);
+
+/* B(m) dv: Born data of the velocity perturbation dv[nz][nx] (Eq. 8). */
+int fwime_born(fwime_ctx *ctx, const float *v, const float *w, const float *dv, float *d);
+
+/* B*(m) d: dv[nz][nx] (=, or += when accumulate=1) summed over shots. */
+int fwime_born_adj(fwime_ctx *ctx, const float *v, const float *w, const float *d,
+                   float *dv, int accumulate);
+
+/* B~(m) p~: data of the extended perturbation pt[nh][nz][nx] (Eq. 1). */
+int fwime_born_ext(fwime_ctx *ctx, const float *v, const float *w, const float *pt, float *d);
+
+/* B~*(m) d: extended image pt[nh][nz][nx] (=, or +=), summed over shots. */
+int fwime_born_ext_adj(fwime_ctx *ctx, const float *v, const float *w, const float *d,
+                       float *pt, int accumulate);
+
+/* T(m, p~) dv: derivative of m -> B~(m) p~ along dv (Eq. 9). */
+int fwime_tomo(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
+               const float *dv, float *d);
+
+/* T*(m, p~) d: dv[nz][nx] (=, or +=), summed over shots (Eq. 9). */
+int fwime_tomo_adj(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
+                   const float *d, float *dv, int accumulate);
+
+/* FWIME objective at fixed p~ and its gradient (Eqs. 1, 7-9):
+ *   r = f(m) + B~(m) p~ - d_obs,  Phi = 1/2 ||r||^2 + eps^2/2 ||D p~||^2,
+ *   grad[nz][nx] = B* r + T* r (overwritten), *objective = Phi (host double,
+ *   written when the call's work has completed, i.e. after fwime_sync).
+ * D = diag(|ih - (nh-1)/2| + 1) is this library's reading of the paper's
+ * "invertible modified DSO" operator; it does not enter the gradient. */
+int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
+                   const float *dobs, float eps, float *grad, double *objective);
+
+/* Waits for the context's stream and returns the latched device status
+ * (FWIME_OK, FWIME_ECFL, FWIME_ETIMEOUT) or FWIME_ECUDA; clears the latch. */
+int fwime_sync(fwime_ctx *ctx);
+
+/* With FWIME_OPT_PROFILE on: waits for the stream, then returns for kernel
+ * family `kernel` the summed CUDA-event duration (ms) of its launches since the
+ * last reset, the number of launches, and the algorithmic bytes they moved
+ * (the compulsory reads/writes of the operator's definition, e.g. 16 bytes per
+ * grid-point update of a plain time step).  reset = 1 clears the counters. */
+int fwime_profile_read(fwime_ctx *ctx, int kernel, double *ms, long long *launches, double *bytes, int reset);
+
+int fwime_last_error_detail(fwime_ctx *ctx, char *buf, size_t n);
+const char *fwime_strerror(int code);
+void fwime_destroy(fwime_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FWIME_H */

@@ -1,0 +1,302 @@
+"""GB300-native (sm_103a) FWIME operators: thin Python binding of libfwime.
+
+Barnier et al., "Full waveform inversion by model extension: practical
+applications" (arXiv 2206.02362).  The operators of the Theory section --
+f (Eq. 1), B and B* (Eq. 8), the subsurface-offset extended Born operator B~
+and its adjoint B~* (Eqs. 1-5), the tomographic operator T and T* (Eq. 9) and
+the FWIME gradient B* r + T* r (Eqs. 7-9) -- run entirely in the CUDA kernels
+of ``libfwime.so`` (C ABI in ``include/fwime.h``).  This module only marshals
+arguments: torch tensors provide device memory and streams.
+
+There is no CPU fallback.  Importing this package loads ``libfwime.so`` (and
+builds it with nvcc if it is missing); if that fails the import raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+FWIME_OK, FWIME_EINVAL, FWIME_ENOMEM, FWIME_ECFL, FWIME_ECUDA, FWIME_ETIMEOUT, FWIME_EBUSY = 0, -1, -2, -3, -4, -5, -6
+OPT_SHOTS_PER_BATCH, OPT_SEGMENT, OPT_PLAIN, OPT_GRAPH, OPT_HOST_IO, OPT_ZCHUNK, OPT_LAUNCHES, OPT_WORKSPACE = \
+    1, 2, 3, 4, 5, 6, 7, 8
+OPT_PROFILE = 9
+K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
+KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
+(OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
+ OP_GRADIENT) = range(8)
+
+ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
+                 "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_sync", "fwime_profile_read",
+                 "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
+
+
+class FwimeError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {strerror(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class GridC(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("sponge", ctypes.c_int), ("nt", ctypes.c_int),
+                ("nh", ctypes.c_int), ("dz", ctypes.c_float), ("dx", ctypes.c_float), ("dt", ctypes.c_float)]
+
+
+class GeomC(ctypes.Structure):
+    _fields_ = [("nshot", ctypes.c_int), ("src_iz", ctypes.POINTER(ctypes.c_int)),
+                ("src_ix", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
+                ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int))]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libfwime.so (building it first if absent); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libfwime.so not built at {path}")
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp, fp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
+    lib.fwime_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(GridC), ctypes.POINTER(GeomC), ctypes.c_size_t, vp]
+    lib.fwime_workspace_bytes.argtypes = [ctypes.POINTER(GridC), ctypes.POINTER(GeomC), ip, ip, ip,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    lib.fwime_set_option.argtypes = [vp, ip, ctypes.c_longlong]
+    lib.fwime_get_option.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_longlong)]
+    lib.fwime_forward.argtypes = [vp, fp, fp, fp]
+    lib.fwime_born.argtypes = [vp, fp, fp, fp, fp]
+    lib.fwime_born_adj.argtypes = [vp, fp, fp, fp, fp, ip]
+    lib.fwime_born_ext.argtypes = [vp, fp, fp, fp, fp]
+    lib.fwime_born_ext_adj.argtypes = [vp, fp, fp, fp, fp, ip]
+    lib.fwime_tomo.argtypes = [vp, fp, fp, fp, fp, fp]
+    lib.fwime_tomo_adj.argtypes = [vp, fp, fp, fp, fp, fp, ip]
+    lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_sync.argtypes = [vp]
+    lib.fwime_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ip]
+    lib.fwime_last_error_detail.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.fwime_strerror.argtypes = [ip]
+    lib.fwime_strerror.restype = ctypes.c_char_p
+    lib.fwime_destroy.argtypes = [vp]
+    lib.fwime_destroy.restype = None
+    for name in ABI_FUNCTIONS:
+        if name not in ("fwime_strerror", "fwime_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().fwime_strerror(int(code)).decode()
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Physical grid nz x nx at dz, dx; `sponge` absorbing points per side; nt samples at dt; nh offsets."""
+    nz: int
+    nx: int
+    sponge: int
+    nt: int
+    dt: float
+    dx: float
+    dz: float | None = None
+    nh: int = 1
+
+    def c(self) -> GridC:
+        dz = self.dx if self.dz is None else self.dz
+        return GridC(self.nz, self.nx, self.sponge, self.nt, self.nh, float(dz), float(self.dx), float(self.dt))
+
+
+@dataclass
+class Geometry:
+    """One point source per shot and a fixed receiver spread (physical-grid indices)."""
+    src_iz: np.ndarray
+    src_ix: np.ndarray
+    rec_iz: np.ndarray
+    rec_ix: np.ndarray
+
+    @property
+    def nshot(self) -> int:
+        return int(len(self.src_iz))
+
+    @property
+    def nrec(self) -> int:
+        return int(len(self.rec_iz))
+
+    def c(self):
+        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (self.src_iz, self.src_ix, self.rec_iz, self.rec_ix)]
+        P = ctypes.POINTER(ctypes.c_int)
+        g = GeomC(self.nshot, arrs[0].ctypes.data_as(P), arrs[1].ctypes.data_as(P), self.nrec,
+                  arrs[2].ctypes.data_as(P), arrs[3].ctypes.data_as(P))
+        return g, arrs
+
+
+def workspace_bytes(grid: Grid, geom: Geometry, op: int, shots_per_batch: int = 0, segment: int = 0) -> int:
+    gc = grid.c()
+    gm, keep = geom.c()
+    out = ctypes.c_size_t(0)
+    rc = load().fwime_workspace_bytes(ctypes.byref(gc), ctypes.byref(gm), op, shots_per_batch, segment,
+                                      ctypes.byref(out))
+    if rc != FWIME_OK:
+        raise FwimeError(rc, "fwime_workspace_bytes")
+    return int(out.value)
+
+
+def _ptr(t) -> int:
+    """Device (or, in host-I/O mode, host) address of a contiguous float32 tensor/array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float32 or not t.flags.c_contiguous:
+            raise TypeError("arrays must be contiguous float32")
+        return t.ctypes.data
+    if t.dtype.__str__() != "torch.float32" or not t.is_contiguous():
+        raise TypeError("tensors must be contiguous float32")
+    return t.data_ptr()
+
+
+class Context:
+    """One fwime_ctx: a grid, an acquisition geometry, a CUDA stream and a workspace.
+
+    Methods mirror the C ABI (``fwime_forward`` -> ``forward`` ...).  Arguments are
+    contiguous float32 CUDA tensors (host arrays with ``host_io=True``); outputs are
+    written into the given tensors.  Each call is asynchronous on the stream unless
+    ``sync=True`` (the default), which waits and raises on device-side errors.
+    """
+
+    def __init__(self, grid: Grid, geom: Geometry, max_workspace_bytes: int = 0, stream=None, **options):
+        self.grid, self.geom = grid, geom
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        gc = grid.c()
+        gm, keep = geom.c()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(int(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream))
+        self.stream = stream
+        rc = lib.fwime_create(ctypes.byref(self._h), ctypes.byref(gc), ctypes.byref(gm),
+                              ctypes.c_size_t(max_workspace_bytes), s)
+        if rc != FWIME_OK:
+            raise FwimeError(rc, "fwime_create")
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    _OPTS = {"shots_per_batch": OPT_SHOTS_PER_BATCH, "segment": OPT_SEGMENT, "plain": OPT_PLAIN,
+             "graph": OPT_GRAPH, "host_io": OPT_HOST_IO, "zchunk": OPT_ZCHUNK, "profile": OPT_PROFILE}
+
+    def set_option(self, name, value):
+        opt = self._OPTS[name] if isinstance(name, str) else int(name)
+        self._check(self._lib.fwime_set_option(self._h, opt, int(value)), "fwime_set_option")
+
+    def get_option(self, name) -> int:
+        opt = {**self._OPTS, "launches": OPT_LAUNCHES, "workspace": OPT_WORKSPACE}[name] \
+            if isinstance(name, str) else int(name)
+        v = ctypes.c_longlong(0)
+        self._check(self._lib.fwime_get_option(self._h, opt, ctypes.byref(v)), "fwime_get_option")
+        return int(v.value)
+
+    @property
+    def launches(self) -> int:
+        """Kernels launched by the last operator call."""
+        return self.get_option("launches")
+
+    def detail(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self._lib.fwime_last_error_detail(self._h, buf, 512)
+        return buf.value.decode(errors="replace")
+
+    def _check(self, rc, where):
+        if rc != FWIME_OK:
+            raise FwimeError(rc, where, self.detail())
+
+    def sync(self):
+        self._check(self._lib.fwime_sync(self._h), "fwime_sync")
+
+    def profile_read(self, reset: bool = False) -> dict:
+        """Per kernel family: summed CUDA-event ms, launches and algorithmic bytes (profile mode)."""
+        out = {}
+        for k, name in enumerate(KERNEL_NAMES):
+            ms, n, b = ctypes.c_double(0), ctypes.c_longlong(0), ctypes.c_double(0)
+            self._check(self._lib.fwime_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                                     0), "fwime_profile_read")
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value}
+        if reset:
+            self._check(self._lib.fwime_profile_read(self._h, 0, None, None, None, 1), "fwime_profile_read")
+        return out
+
+    def _done(self, rc, where, sync):
+        self._check(rc, where)
+        if sync:
+            self.sync()
+
+    def forward(self, v, w, d, sync=True):
+        self._done(self._lib.fwime_forward(self._h, _ptr(v), _ptr(w), _ptr(d)), "fwime_forward", sync)
+        return d
+
+    def born(self, v, w, dv, d, sync=True):
+        self._done(self._lib.fwime_born(self._h, _ptr(v), _ptr(w), _ptr(dv), _ptr(d)), "fwime_born", sync)
+        return d
+
+    def born_adj(self, v, w, d, dv, accumulate=False, sync=True):
+        self._done(self._lib.fwime_born_adj(self._h, _ptr(v), _ptr(w), _ptr(d), _ptr(dv), int(accumulate)),
+                   "fwime_born_adj", sync)
+        return dv
+
+    def born_ext(self, v, w, pt, d, sync=True):
+        self._done(self._lib.fwime_born_ext(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(d)), "fwime_born_ext", sync)
+        return d
+
+    def born_ext_adj(self, v, w, d, pt, accumulate=False, sync=True):
+        self._done(self._lib.fwime_born_ext_adj(self._h, _ptr(v), _ptr(w), _ptr(d), _ptr(pt), int(accumulate)),
+                   "fwime_born_ext_adj", sync)
+        return pt
+
+    def tomo(self, v, w, pt, dv, d, sync=True):
+        self._done(self._lib.fwime_tomo(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dv), _ptr(d)), "fwime_tomo", sync)
+        return d
+
+    def tomo_adj(self, v, w, pt, d, dv, accumulate=False, sync=True):
+        self._done(self._lib.fwime_tomo_adj(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(d), _ptr(dv),
+                                            int(accumulate)), "fwime_tomo_adj", sync)
+        return dv
+
+    def gradient(self, v, w, pt, dobs, grad, eps=0.0, sync=True):
+        """Returns Phi (host float, valid once synced) and fills grad = B* r + T* r."""
+        self._J = ctypes.c_double(0.0)
+        self._done(self._lib.fwime_gradient(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs), ctypes.c_float(eps),
+                                            _ptr(grad), ctypes.byref(self._J)), "fwime_gradient", sync)
+        return float(self._J.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fwime_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,1111 @@
+// libfwime C ABI: argument validation, workspace planning, and the schedules
+// that compose the kernels into the paper's operators (Barnier et al., Theory
+// section, Eqs. 1, 7-9; Computational aspects: a shot is simulated on one GPU
+// over the full FD domain, shots are independent).
+//
+// Schedules.  Shots are processed in batches of S advanced together (one
+// launch per kernel per time step covers the whole batch).  Time is cut into
+// segments of K steps:
+//   * forward-type operators (f, B, B~, T) run segment by segment: the
+//     background wavefield's D2t over K steps goes to a ring, one scatter
+//     launch turns the whole ring (K x S pairs) into secondary sources, then
+//     the scattered field steps through the segment;
+//   * adjoint-type operators (B*, B~*, T*, gradient) store the background (and
+//     scattered) state at every segment start during a forward sweep, then walk
+//     the segments backwards: recompute the segment's D2t fields into rings,
+//     step the adjoint fields down through it, and reduce the imaging
+//     conditions over the segment's K x S pairs in one launch.
+// The adjoint wavefield uses mu = c g lambda, which obeys the forward recursion
+// run backwards, so forward and adjoint share the stencil kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fwime.h"
+#include "fwime_kernels.cuh"
+
+using namespace fwk;
+
+namespace {
+
+const double LAMBDA_MAX = 6.5015873015873;   // max eigenvalue of -D2 (8th order) times h^2
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+};
+
+}  // namespace
+
+struct fwime_ctx {
+    fwime_grid g{};
+    int nshot = 0, nrec = 0;
+    std::vector<int> src_iz, src_ix, rec_iz, rec_ix;
+    int NZ = 0, NX = 0, NXP = 0, o = 0;
+    long long P = 0;
+    cudaStream_t st = nullptr;
+    size_t max_ws = 0;
+    int device = 0;
+    // options
+    int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0;
+    long long launches = 0;
+    // persistent device memory
+    int *d_src_off = nullptr, *d_rec_off = nullptr, *d_status = nullptr;
+    double *d_J = nullptr, *d_part = nullptr, *h_J = nullptr;
+    double *user_J = nullptr;
+    // workspace arena
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::map<std::string, Graph> graphs;
+    bool capturing = false;
+    // per-launch CUDA-event profiling (FWIME_OPT_PROFILE)
+    int opt_profile = 0;
+    struct Pend { int ev; int kind; double bytes; };
+    std::vector<cudaEvent_t> ev;
+    std::vector<Pend> pend;
+    double prof_ms[5] = {0, 0, 0, 0, 0}, prof_bytes[5] = {0, 0, 0, 0, 0};
+    long long prof_n[5] = {0, 0, 0, 0, 0};
+    int last_err = 0;
+    char err[320] = {0};
+};
+
+// ------------------------------------------------------------------ helpers
+
+static int fail(fwime_ctx *x, int code, const char *fmt, ...)
+{
+    if (x) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(x->err, sizeof(x->err), fmt, ap);
+        va_end(ap);
+        x->last_err = code;
+    }
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(x, FWIME_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(call)                                                                                  \
+    do {                                                                                           \
+        int r_ = (call);                                                                           \
+        if (r_ != FWIME_OK) return r_;                                                             \
+    } while (0)
+
+// Event pair around one launch when profiling; `bytes` are the launch's algorithmic bytes.
+static int prof_begin(fwime_ctx *x, int &slot)
+{
+    slot = -1;
+    if (!x->opt_profile) return FWIME_OK;
+    const size_t need = 2 * (x->pend.size() + 1);
+    while (x->ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        x->ev.push_back(e);
+    }
+    slot = (int)(2 * x->pend.size());
+    CK(cudaEventRecord(x->ev[slot], x->st));
+    return FWIME_OK;
+}
+
+static int prof_end(fwime_ctx *x, int slot, int kind, double bytes)
+{
+    if (slot < 0) return FWIME_OK;
+    CK(cudaEventRecord(x->ev[slot + 1], x->st));
+    x->pend.push_back({slot, kind, bytes});
+    return FWIME_OK;
+}
+
+static int prof_collect(fwime_ctx *x)
+{
+    if (x->pend.empty()) return FWIME_OK;
+    CK(x->st ? cudaStreamSynchronize(x->st) : cudaDeviceSynchronize());
+    for (const auto &p : x->pend) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, x->ev[p.ev], x->ev[p.ev + 1]));
+        x->prof_ms[p.kind] += ms;
+        x->prof_bytes[p.kind] += p.bytes;
+        x->prof_n[p.kind] += 1;
+    }
+    x->pend.clear();
+    return FWIME_OK;
+}
+
+// a kernel launch: counts it and, when profiling, brackets it with events
+#define LAUNCH(kind, bytes, call)                                                                  \
+    do {                                                                                           \
+        int slot_;                                                                                 \
+        TRY(prof_begin(x, slot_));                                                                 \
+        x->launches++;                                                                             \
+        CK(call);                                                                                  \
+        TRY(prof_end(x, slot_, (kind), (bytes)));                                                  \
+    } while (0)
+
+static int auto_K(int nt)
+{
+    int K = (int)std::lround(std::sqrt((double)std::max(nt - 1, 1)));
+    return std::min(std::max(K, 8), 128);
+}
+
+// Floats of workspace: model part (independent of S) and per-shot part.
+struct Sizes {
+    size_t model = 0, per_shot = 0, staging = 0;
+};
+
+static size_t al(size_t n) { return (n + 63) & ~(size_t)63; }   // 256-byte granules
+
+static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int NZ, int NXP, int op, int K,
+                      bool host_io)
+{
+    Sizes s;
+    const size_t nh = g.nh, nseg = (size_t)((g.nt - 1 + K - 1) / K), R = K + 2;
+    s.model = al(P) * 2 + al(NZ) + al(NXP);   // c, bpad, gz, gx
+    size_t f = 0;
+    switch (op) {
+    case FWIME_OP_FORWARD: f = 2; break;
+    case FWIME_OP_BORN: s.model += al(P); f = 5; break;
+    case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 4 + 2 * K; break;
+    case FWIME_OP_BORN_ADJ: s.model += al(P); f = 2 + K + R + 2 * nseg; break;
+    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + 2 * nseg; break;
+    case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
+    case FWIME_OP_TOMO_ADJ:
+    case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + 4 * nseg; break;
+    default: break;
+    }
+    s.per_shot = f * (size_t)P;
+    if (op == FWIME_OP_GRADIENT) s.per_shot += (size_t)g.nt * nrec;
+    if (host_io) {
+        const size_t nd = (size_t)nshot * g.nt * nrec, nm = (size_t)g.nz * g.nx;
+        s.staging = al(nm) + al((size_t)nshot * g.nt) + 2 * al(nd) + al(nh * nm) + al(nm) + al(nh * nm);
+    }
+    return s;
+}
+
+static int validate(const fwime_grid *g, const fwime_geom *geo, fwime_ctx *x)
+{
+    if (!g || !geo) return fail(x, FWIME_EINVAL, "null grid or geometry");
+    if (g->nz < 1 || g->nx < 1 || g->sponge < 0 || g->nt < 2)
+        return fail(x, FWIME_EINVAL, "grid sizes: nz=%d nx=%d sponge=%d nt=%d", g->nz, g->nx, g->sponge, g->nt);
+    if (g->nh < 1 || g->nh % 2 == 0 || g->nh > MAX_NH)
+        return fail(x, FWIME_EINVAL, "nh=%d must be odd, 1..%d", g->nh, MAX_NH);
+    if (!(g->dx > 0.f) || !(g->dz > 0.f) || !(g->dt > 0.f)) return fail(x, FWIME_EINVAL, "spacings must be > 0");
+    if (geo->nshot < 1 || geo->nrec < 1) return fail(x, FWIME_EINVAL, "nshot=%d nrec=%d", geo->nshot, geo->nrec);
+    if (!geo->src_iz || !geo->src_ix || !geo->rec_iz || !geo->rec_ix) return fail(x, FWIME_EINVAL, "null geometry");
+    for (int s = 0; s < geo->nshot; ++s)
+        if (geo->src_iz[s] < 0 || geo->src_iz[s] >= g->nz || geo->src_ix[s] < 0 || geo->src_ix[s] >= g->nx)
+            return fail(x, FWIME_EINVAL, "source %d at (%d,%d) outside the grid", s, geo->src_iz[s], geo->src_ix[s]);
+    for (int r = 0; r < geo->nrec; ++r)
+        if (geo->rec_iz[r] < 0 || geo->rec_iz[r] >= g->nz || geo->rec_ix[r] < 0 || geo->rec_ix[r] >= g->nx)
+            return fail(x, FWIME_EINVAL, "receiver %d at (%d,%d) outside the grid", r, geo->rec_iz[r], geo->rec_ix[r]);
+    return FWIME_OK;
+}
+
+// ------------------------------------------------------------ workspace
+
+struct WS {
+    int S = 1, K = 8, nseg = 1, R = 10;
+    // model
+    float *c, *bpad, *gz, *gx, *coef, *W, *W2, *ptp, *acc1, *acc2;
+    // per batch
+    float *f[8];
+    float *ring[6];    // rings of K slots (ring[0..3]) and of R slots (ring[3..5] in adjoint ops)
+    float *ckpt, *pred;
+    // host-io staging
+    float *sv, *sw, *sd1, *sd2, *sm1, *sdv, *smo;
+};
+
+static int plan(fwime_ctx *x, int op, WS &w)
+{
+    w.K = x->opt_K > 0 ? x->opt_K : auto_K(x->g.nt);
+    w.K = std::min(w.K, x->g.nt - 1);
+    w.K = std::max(w.K, 1);
+    w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;
+    w.R = w.K + 2;
+    Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0);
+    size_t budget = x->max_ws;
+    if (budget == 0 && x->capturing) budget = x->ws_bytes;   // the workspace was planned before capture
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        budget = x->ws_bytes + fr;
+        budget = budget > ((size_t)2 << 30) ? budget - ((size_t)2 << 30) : budget / 2;   // keep 2 GB slack
+    }
+    const size_t fixed = (sz.model + sz.staging) * sizeof(float);
+    const size_t per = sz.per_shot * sizeof(float);
+    int S;
+    if (x->opt_plain) S = 1;
+    else if (x->opt_S > 0) S = std::min(x->opt_S, x->nshot);
+    else {
+        if (fixed + per > budget) S = 1;
+        else S = (int)std::min<size_t>((size_t)x->nshot, (budget - fixed) / per);
+    }
+    w.S = std::max(S, 1);
+    const size_t need = fixed + per * (size_t)w.S + 4096;
+    if (x->max_ws && need > x->max_ws)
+        return fail(x, FWIME_ENOMEM, "operator needs %zu bytes for S=%d, K=%d; budget %zu", need, w.S, w.K, x->max_ws);
+    if (need > x->ws_bytes) {
+        if (x->capturing) return fail(x, FWIME_EBUSY, "workspace growth during graph capture");
+        if (x->ws) {
+            cudaStreamSynchronize(x->st);
+            for (auto &kv : x->graphs) cudaGraphExecDestroy(kv.second.exec);
+            x->graphs.clear();
+            cudaFree(x->ws);
+            x->ws = nullptr;
+            x->ws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&x->ws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(x, FWIME_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        }
+        x->ws_bytes = need;
+    }
+    // carve
+    float *p = reinterpret_cast<float *>(x->ws);
+    auto take = [&](size_t n) { float *r = p; p += al(n); return r; };
+    const long long P = x->P;
+    const size_t nh = x->g.nh;
+    w.c = take(P); w.bpad = take(P); w.gz = take(x->NZ); w.gx = take(x->NXP);
+    w.coef = w.W = w.W2 = w.ptp = w.acc1 = w.acc2 = nullptr;
+    switch (op) {
+    case FWIME_OP_BORN: w.coef = take(P); break;
+    case FWIME_OP_BORN_EXT: w.W = take(nh * P); break;
+    case FWIME_OP_BORN_ADJ: w.acc1 = take(P); break;
+    case FWIME_OP_BORN_EXT_ADJ: w.acc1 = take(nh * P); break;
+    case FWIME_OP_TOMO: w.W = take(nh * P); w.W2 = take(nh * P); w.coef = take(P); break;
+    case FWIME_OP_TOMO_ADJ:
+    case FWIME_OP_GRADIENT: w.W = take(nh * P); w.ptp = take(nh * P); w.acc1 = take(P); w.acc2 = take(P); break;
+    default: break;
+    }
+    const size_t SP = (size_t)w.S * P;
+    for (auto &q : w.f) q = nullptr;
+    for (auto &q : w.ring) q = nullptr;
+    w.ckpt = w.pred = nullptr;
+    int nf = 0, nk = 0, nr = 0, nck = 0;
+    switch (op) {
+    case FWIME_OP_FORWARD: nf = 2; break;
+    case FWIME_OP_BORN: nf = 5; break;
+    case FWIME_OP_BORN_EXT: nf = 4; nk = 2; break;
+    case FWIME_OP_BORN_ADJ:
+    case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = 2; break;
+    case FWIME_OP_TOMO: nf = 8; nk = 4; break;
+    default: nf = 4; nk = 3; nr = 3; nck = 4; break;
+    }
+    for (int i = 0; i < nf; ++i) w.f[i] = take(SP);
+    for (int i = 0; i < nk; ++i) w.ring[i] = take((size_t)w.K * SP);
+    for (int i = 0; i < nr; ++i) w.ring[nk + i] = take((size_t)w.R * SP);
+    if (nck) w.ckpt = take((size_t)w.nseg * nck * SP);
+    if (op == FWIME_OP_GRADIENT) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
+    w.sv = w.sw = w.sd1 = w.sd2 = w.sm1 = w.sdv = w.smo = nullptr;
+    if (x->opt_host_io) {
+        const size_t nd = (size_t)x->nshot * x->g.nt * x->nrec, nm = (size_t)x->g.nz * x->g.nx;
+        w.sv = take(nm); w.sw = take((size_t)x->nshot * x->g.nt); w.sd1 = take(nd); w.sd2 = take(nd);
+        w.sm1 = take(nh * nm); w.sdv = take(nm); w.smo = take(nh * nm);
+    }
+    if ((char *)p > x->ws + x->ws_bytes) return fail(x, FWIME_ENOMEM, "workspace layout overflow");
+    return FWIME_OK;
+}
+
+// --------------------------------------------------------------- launches
+
+struct Run {
+    fwime_ctx *x;
+    WS w;
+    int zchunk, nstrip, nchunk;
+    PropArgs base{};
+};
+
+static void init_run(fwime_ctx *x, Run &r, int S)
+{
+    r.x = x;
+    const int rows = x->NZ - 8;
+    r.nstrip = (x->NXP + STRIP - 1) / STRIP;
+    int zc = x->opt_zchunk;
+    if (zc <= 0) {
+        const long long target = 152LL * 32;   // resident warps to aim for
+        long long per = (long long)r.nstrip * std::max(S, 1);
+        long long nchunk_t = std::max<long long>(1, (target + per - 1) / per);
+        zc = (int)((rows + nchunk_t - 1) / nchunk_t);
+        zc = std::min(std::max(zc, 8), 256);
+    }
+    r.zchunk = zc;
+    r.nchunk = (rows + zc - 1) / zc;
+    PropArgs &a = r.base;
+    std::memset(&a, 0, sizeof(a));
+    a.NZ = x->NZ; a.NXP = x->NXP; a.zchunk = r.zchunk; a.nstrip = r.nstrip; a.nchunk = r.nchunk; a.P = x->P;
+    const double A8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+    for (int k = 0; k < 5; ++k) {
+        a.ax[k] = (float)(A8[k] / ((double)x->g.dx * x->g.dx));
+        a.az[k] = (float)(A8[k] / ((double)x->g.dz * x->g.dz));
+    }
+    a.inv_dt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
+    a.src_scale = (float)(1.0 / ((double)x->g.dx * x->g.dz));
+}
+
+static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out, float *d2, const float *wsrc,
+                int src_shot0, const float *f0 = nullptr, float a0 = 0.f, const float *f1 = nullptr, float a1 = 0.f,
+                const float *f2 = nullptr, float a2 = 0.f, const float *coef = nullptr, const float *fc = nullptr)
+{
+    fwime_ctx *x = r.x;
+    PropArgs a = r.base;
+    a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx;
+    a.cur = cur; a.prev = prev; a.out = out; a.d2 = d2;
+    if (wsrc) {
+        a.src_off = x->d_src_off + src_shot0;
+        a.src_amp = wsrc;
+        a.src_stride = x->g.nt;
+    }
+    a.f0 = f0; a.a0 = a0; a.f1 = f1; a.a1 = a1; a.f2 = f2; a.a2 = a2; a.coef = coef; a.fc = fc;
+    // compulsory bytes: per shot-point read q^n, q^{n-1}, write q^{n+1} (+ D2t out, + local
+    // source fields); per point once per launch the shared c (and coef)
+    const double pts = (double)x->NZ * x->NX;
+    const double per = 12.0 + (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) +
+                       (fc ? 4 : 0);
+    LAUNCH(FWIME_K_PROP, pts * (Sb * per + 4.0 + (coef ? 4.0 : 0.0)), launch_prop(a, Sb, x->st));
+    return FWIME_OK;
+}
+
+static int record(Run &r, int Sb, const float *f1, const float *f2, float *d, int accumulate)
+{
+    fwime_ctx *x = r.x;
+    PointsArgs a{};
+    a.nrec = x->nrec; a.P = x->P; a.rec_off = x->d_rec_off;
+    a.f1 = f1; a.f2 = f2; a.d = d; a.dstride = (long long)x->g.nt * x->nrec; a.accumulate = accumulate;
+    LAUNCH(FWIME_K_POINTS, (double)Sb * x->nrec * (8.0 + (f2 ? 4 : 0) + (accumulate ? 4 : 0)),
+           launch_points(a, Sb, x->st));
+    return FWIME_OK;
+}
+
+static int inject(Run &r, int Sb, float *fld, const float *val)
+{
+    fwime_ctx *x = r.x;
+    PointsArgs a{};
+    a.nrec = x->nrec; a.P = x->P; a.rec_off = x->d_rec_off;
+    a.fld = fld; a.val = val; a.vstride = (long long)x->g.nt * x->nrec; a.c = r.w.c;
+    LAUNCH(FWIME_K_POINTS, (double)Sb * x->nrec * 12.0, launch_points(a, Sb, x->st));
+    return FWIME_OK;
+}
+
+static RingRef ringref(const float *base, long long slot_stride, int mod, int shift)
+{
+    RingRef rr;
+    rr.base = base; rr.slot_stride = slot_stride; rr.mod = mod; rr.shift = shift;
+    return rr;
+}
+
+// x-range of points a scatter can reach: physical columns +- hm, within the active region
+static void ext_cols(fwime_ctx *x, int &lo, int &hi)
+{
+    const int hm = (x->g.nh - 1) / 2;
+    lo = std::max(4, x->o - hm);
+    hi = std::min(x->NX - 4, x->o + x->g.nx + hm);
+}
+
+static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, RingRef out, int sigma, int accumulate)
+{
+    fwime_ctx *x = r.x;
+    ExtArgs a{};
+    a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
+    a.z_lo = x->o; a.z_hi = x->o + x->g.nz;
+    ext_cols(x, a.x_lo, a.x_hi);
+    a.sigma = sigma; a.W = W; a.in = in; a.outr = out; a.accumulate = accumulate;
+    const double pts = (double)x->g.nz * (a.x_hi - a.x_lo);
+    LAUNCH(FWIME_K_SCATTER, pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0)) + 4.0 * x->g.nh),
+           launch_scatter(a, x->st));
+    return FWIME_OK;
+}
+
+static int image(Run &r, int Sb, int n0, int kk, int mode, RingRef D, RingRef L, RingRef M2, RingRef Ds, float alpha,
+                 const float *pt, float *img)
+{
+    fwime_ctx *x = r.x;
+    ImgArgs a{};
+    a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
+    a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;
+    a.D = D; a.L = L; a.M2 = M2; a.Ds = Ds; a.alpha = alpha; a.pt = pt; a.img = img;
+    const double pts = (double)x->g.nz * x->g.nx;
+    const double per = 8.0 + (M2.base ? 4 : 0) + (Ds.base ? 4 : 0);
+    const double once = mode == IMG_EXT ? 8.0 * x->g.nh : (mode == IMG_CONTRACT ? 8.0 + 4.0 * x->g.nh : 8.0);
+    LAUNCH(FWIME_K_IMAGE, pts * ((double)a.npair * per + once), launch_image(a, mode, x->st));
+    return FWIME_OK;
+}
+
+static int zero(fwime_ctx *x, void *p, size_t bytes)
+{
+    if (bytes == 0) return FWIME_OK;
+    CK(cudaMemsetAsync(p, 0, bytes, x->st));
+    return FWIME_OK;
+}
+
+static int copyf(fwime_ctx *x, float *dst, const float *src, size_t n)
+{
+    LAUNCH(FWIME_K_OTHER, 8.0 * n, launch_copy_fields(dst, src, (long long)n, x->st));
+    return FWIME_OK;
+}
+
+static int prep_model(fwime_ctx *x, Run &r, const float *v)
+{
+    PrepArgs a{};
+    a.nz = x->g.nz; a.nx = x->g.nx; a.o = x->o; a.NZ = x->NZ; a.NX = x->NX; a.NXP = x->NXP; a.W = x->g.sponge;
+    a.dt = x->g.dt;
+    const double lim = 2.0 / ((double)x->g.dt *
+                              std::sqrt(LAMBDA_MAX * (1.0 / ((double)x->g.dx * x->g.dx) + 1.0 / ((double)x->g.dz * x->g.dz))));
+    a.cfl_limit2 = (float)(lim * lim);
+    a.v = v; a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx; a.bpad = r.w.bpad; a.status = x->d_status;
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->NZ * x->NXP, launch_prep(a, x->st));
+    return FWIME_OK;
+}
+
+// ------------------------------------------------------------- schedules
+
+static int run_forward(fwime_ctx *x, Run &r, const float *v, const float *w, float *d)
+{
+    const int nt = x->g.nt, S = r.w.S;
+    const size_t nd = (size_t)nt * x->nrec;
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *cur = r.w.f[0], *prv = r.w.f[1];
+        TRY(zero(x, cur, sizeof(float) * Sb * x->P));
+        TRY(zero(x, prv, sizeof(float) * Sb * x->P));
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        for (int n = 0; n + 1 < nt; ++n) {
+            TRY(prop(r, Sb, cur, prv, prv, nullptr, w + (size_t)s0 * nt + n, s0));
+            TRY(record(r, Sb, prv, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+            std::swap(cur, prv);
+        }
+    }
+    return FWIME_OK;
+}
+
+static int run_born(fwime_ctx *x, Run &r, const float *v, const float *w, const float *dv, float *d)
+{
+    const int nt = x->g.nt, S = r.w.S;
+    const size_t nd = (size_t)nt * x->nrec;
+    TRY(zero(x, r.w.coef, sizeof(float) * x->P));
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nz * x->g.nx,
+           launch_embed_scale(dv, r.w.bpad, r.w.coef, x->g.nz, x->g.nx, x->o, x->NXP, 1.f, x->st));
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *c0 = r.w.f[0], *p0 = r.w.f[1], *c1 = r.w.f[2], *p1 = r.w.f[3], *D = r.w.f[4];
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        for (int n = 0; n + 1 < nt; ++n) {
+            TRY(prop(r, Sb, c0, p0, p0, D, w + (size_t)s0 * nt + n, s0));
+            TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, r.w.coef, D));
+            TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+            std::swap(c0, p0);
+            std::swap(c1, p1);
+        }
+    }
+    return FWIME_OK;
+}
+
+static int run_born_ext(fwime_ctx *x, Run &r, const float *v, const float *w, const float *pt, float *d)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * x->g.nh * x->P));
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * x->g.nz * x->g.nx,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    float *Dr = r.w.ring[0], *Er = r.w.ring[1];
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *c0 = r.w.f[0], *p0 = r.w.f[1], *c1 = r.w.f[2], *p1 = r.w.f[3];
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        for (int n0 = 0; n0 < nt - 1; n0 += K) {
+            const int n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, c0, p0, p0, Dr + (n - n0) * SP, w + (size_t)s0 * nt + n, s0));
+                std::swap(c0, p0);
+            }
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Dr, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                std::swap(c1, p1);
+            }
+        }
+    }
+    return FWIME_OK;
+}
+
+// B* (ext = false) and B~* (ext = true)
+static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const float *w, const float *d, float *out,
+                        int accumulate)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    const int planes = ext ? x->g.nh : 1;
+    TRY(zero(x, r.w.acc1, sizeof(float) * planes * x->P));
+    float *Dr = r.w.ring[0], *Mu = r.w.ring[1], *ck = r.w.ckpt;
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        const size_t fb = sizeof(float) * (size_t)Sb * x->P;
+        float *cur = r.w.f[0], *prv = r.w.f[1];
+        TRY(zero(x, cur, fb));
+        TRY(zero(x, prv, fb));
+        TRY(zero(x, Mu, sizeof(float) * R * SP));
+        const float *ws = w + (size_t)s0 * nt;
+        // forward sweep: checkpoint (q^{n0}, q^{n0-1}) at every segment start
+        for (int j = 0; j < nseg; ++j) {
+            TRY(copyf(x, ck + (2LL * j) * SP, cur, (size_t)Sb * x->P));
+            TRY(copyf(x, ck + (2LL * j + 1) * SP, prv, (size_t)Sb * x->P));
+            if (j == nseg - 1) break;
+            for (int n = j * K; n < (j + 1) * K; ++n) {
+                TRY(prop(r, Sb, cur, prv, prv, nullptr, ws + n, s0));
+                std::swap(cur, prv);
+            }
+        }
+        // backward sweep
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            TRY(copyf(x, cur, ck + (2LL * j) * SP, (size_t)Sb * x->P));
+            TRY(copyf(x, prv, ck + (2LL * j + 1) * SP, (size_t)Sb * x->P));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, cur, prv, prv, Dr + (n - n0) * SP, ws + n, s0));
+                std::swap(cur, prv);
+            }
+            for (int m = n1; m >= n0 + 1; --m) {
+                float *mo = Mu + (m % R) * SP;
+                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
+                TRY(inject(r, Sb, mo, d + s0 * nd + (size_t)m * x->nrec));
+            }
+            if (ext)
+                TRY(image(r, Sb, n0, kk, IMG_EXT, ringref(Dr, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(nullptr, 0, 0, 0),
+                          ringref(nullptr, 0, 0, 0), 1.f, nullptr, r.w.acc1));
+            else
+                TRY(image(r, Sb, n0, kk, IMG_LOCAL, ringref(Dr, SP, 0, 0), ringref(Mu, SP, R, 1),
+                          ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 1.f, nullptr, r.w.acc1));
+        }
+    }
+    LAUNCH(FWIME_K_OTHER, 12.0 * planes * x->g.nz * x->g.nx,
+           launch_finalize(r.w.acc1, nullptr, r.w.bpad, v, out, planes, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                           accumulate, x->st));
+    return FWIME_OK;
+}
+
+static int run_tomo(fwime_ctx *x, Run &r, const float *v, const float *w, const float *pt, const float *dv, float *d)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    const size_t nhP = (size_t)x->g.nh * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * nhP));
+    TRY(zero(x, r.w.W2, sizeof(float) * nhP));
+    TRY(zero(x, r.w.coef, sizeof(float) * x->P));
+    const double nm = (double)x->g.nz * x->g.nx;
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    LAUNCH(FWIME_K_OTHER, 20.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, dv, v, r.w.W2, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1, x->st));
+    LAUNCH(FWIME_K_OTHER, 12.0 * nm,
+           launch_embed_scale(dv, r.w.bpad, r.w.coef, x->g.nz, x->g.nx, x->o, x->NXP, 1.f, x->st));
+    float *D0r = r.w.ring[0], *D0d = r.w.ring[1], *Er = r.w.ring[2], *Dsr = r.w.ring[3];
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *f[8];
+        for (int i = 0; i < 8; ++i) {
+            f[i] = r.w.f[i];
+            TRY(zero(x, f[i], sizeof(float) * Sb * x->P));
+        }
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        const float *ws = w + (size_t)s0 * nt;
+        for (int n0 = 0; n0 < nt - 1; n0 += K) {
+            const int n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            for (int n = n0; n < n1; ++n) {   // background q0
+                TRY(prop(r, Sb, f[0], f[1], f[1], D0r + (n - n0) * SP, ws + n, s0));
+                std::swap(f[0], f[1]);
+            }
+            for (int n = n0; n < n1; ++n) {   // Born wavefield of dv
+                TRY(prop(r, Sb, f[2], f[3], f[3], D0d + (n - n0) * SP, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0,
+                         r.w.coef, D0r + (n - n0) * SP));
+                std::swap(f[2], f[3]);
+            }
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+            for (int n = n0; n < n1; ++n) {   // extended Born wavefield of p~
+                TRY(prop(r, Sb, f[4], f[5], f[5], Dsr + (n - n0) * SP, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                std::swap(f[4], f[5]);
+            }
+            TRY(scatter(r, Sb, n0, kk, r.w.W2, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0d, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 1));
+            for (int n = n0; n < n1; ++n) {   // tomographic wavefield
+                TRY(prop(r, Sb, f[6], f[7], f[7], nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0, nullptr, 0,
+                         r.w.coef, Dsr + (n - n0) * SP));
+                TRY(record(r, Sb, f[7], nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                std::swap(f[6], f[7]);
+            }
+        }
+    }
+    return FWIME_OK;
+}
+
+// T* (grad = false, r = d) and the FWIME gradient (grad = true, r = f + B~p~ - dobs)
+static int run_tomo_adj(fwime_ctx *x, Run &r, bool grad, const float *v, const float *w, const float *pt,
+                        const float *d, float *out, int accumulate, float eps)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    const size_t nhP = (size_t)x->g.nh * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * nhP));
+    TRY(zero(x, r.w.ptp, sizeof(float) * nhP));
+    TRY(zero(x, r.w.acc1, sizeof(float) * x->P));
+    TRY(zero(x, r.w.acc2, sizeof(float) * x->P));
+    const double nm = (double)x->g.nz * x->g.nx;
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    LAUNCH(FWIME_K_OTHER, 8.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.ptp, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 2,
+                              x->st));
+    float *D0r = r.w.ring[0], *Er = r.w.ring[1], *Dsr = r.w.ring[2];
+    float *Mu = r.w.ring[3], *Zr = r.w.ring[4], *Mu2 = r.w.ring[5];
+    float *ck = r.w.ckpt;
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    if (grad) TRY(zero(x, x->d_J, sizeof(double)));
+    const int nred = 1024;
+    const float idt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        const size_t fb = sizeof(float) * (size_t)Sb * x->P;
+        float *q0c = r.w.f[0], *q0p = r.w.f[1], *qsc = r.w.f[2], *qsp = r.w.f[3];
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], fb));
+        TRY(zero(x, Mu, sizeof(float) * R * SP));
+        TRY(zero(x, Zr, sizeof(float) * R * SP));
+        TRY(zero(x, Mu2, sizeof(float) * R * SP));
+        const float *ws = w + (size_t)s0 * nt;
+        float *pred = r.w.pred;
+        if (grad) TRY(zero(x, pred, sizeof(float) * Sb * nd));
+        // forward sweep
+        for (int j = 0; j < nseg; ++j) {
+            const long long cb = 4LL * j * SP;
+            TRY(copyf(x, ck + cb, q0c, (size_t)Sb * x->P));
+            TRY(copyf(x, ck + cb + SP, q0p, (size_t)Sb * x->P));
+            TRY(copyf(x, ck + cb + 2 * SP, qsc, (size_t)Sb * x->P));
+            TRY(copyf(x, ck + cb + 3 * SP, qsp, (size_t)Sb * x->P));
+            if (!grad && j == nseg - 1) break;
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
+                if (grad) TRY(record(r, Sb, q0p, nullptr, pred + (size_t)(n + 1) * x->nrec, 0));
+                std::swap(q0c, q0p);
+            }
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                if (grad) TRY(record(r, Sb, qsp, nullptr, pred + (size_t)(n + 1) * x->nrec, 1));
+                std::swap(qsc, qsp);
+            }
+        }
+        const float *rr = d + s0 * nd;
+        if (grad) {
+            LAUNCH(FWIME_K_OTHER, 12.0 * Sb * nd,
+                   launch_residual(pred, d + s0 * nd, pred, (long long)Sb * nd, x->d_part, nred, x->st));
+            LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
+            rr = pred;
+        }
+        // backward sweep
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            const long long cb = 4LL * j * SP;
+            TRY(copyf(x, q0c, ck + cb, (size_t)Sb * x->P));
+            TRY(copyf(x, q0p, ck + cb + SP, (size_t)Sb * x->P));
+            TRY(copyf(x, qsc, ck + cb + 2 * SP, (size_t)Sb * x->P));
+            TRY(copyf(x, qsp, ck + cb + 3 * SP, (size_t)Sb * x->P));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
+                std::swap(q0c, q0p);
+            }
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, qsc, qsp, qsp, Dsr + (n - n0) * SP, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                std::swap(qsc, qsp);
+            }
+            // adjoint of the residual: mu^m, m = n1 .. n0+1 (lambda^ at step n is mu^{n+1})
+            for (int m = n1; m >= n0 + 1; --m) {
+                float *mo = Mu + (m % R) * SP;
+                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
+                TRY(inject(r, Sb, mo, rr + (size_t)m * x->nrec));
+            }
+            // z^n = E_D^T(W, lambda^n) for n in [n0, n1)
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Mu, SP, R, 1), ringref(Zr, SP, R, 0), -1, 0));
+            // second adjoint field driven by d2t^T z
+            for (int m = n1; m >= n0 + 1; --m) {
+                TRY(prop(r, Sb, Mu2 + ((m + 1) % R) * SP, Mu2 + ((m + 2) % R) * SP, Mu2 + (m % R) * SP, nullptr,
+                         nullptr, 0, Zr + ((m - 1) % R) * SP, idt2, Zr + (m % R) * SP, -2.f * idt2,
+                         Zr + ((m + 1) % R) * SP, idt2));
+            }
+            TRY(image(r, Sb, n0, kk, IMG_LOCAL, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(Mu2, SP, R, 1),
+                      ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc1));
+            TRY(image(r, Sb, n0, kk, IMG_CONTRACT, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1),
+                      ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, r.w.ptp, r.w.acc2));
+        }
+    }
+    LAUNCH(FWIME_K_OTHER, 20.0 * nm,
+           launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
+                           accumulate, x->st));
+    if (grad) {
+        LAUNCH(FWIME_K_OTHER, 4.0 * x->g.nh * nm,
+               launch_dso(pt, x->g.nh, (long long)x->g.nz * x->g.nx, x->d_part, nred, x->st));
+        LAUNCH(FWIME_K_OTHER, 8.0 * nred,
+               launch_sum_partials(x->d_part, nred, x->d_J, 1, 0.5 * (double)eps * (double)eps, x->st));
+        CK(cudaMemcpyAsync(x->h_J, x->d_J, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    }
+    return FWIME_OK;
+}
+
+// ----------------------------------------------------------- dispatch
+
+struct Call {
+    int op;
+    const float *v, *w, *in1, *in2;
+    float *out;
+    int accumulate;
+    float eps;
+};
+
+static int enqueue(fwime_ctx *x, const Call &c)
+{
+    Run r;
+    TRY(plan(x, c.op, r.w));
+    init_run(x, r, r.w.S);
+    TRY(prep_model(x, r, c.v));
+    switch (c.op) {
+    case FWIME_OP_FORWARD: return run_forward(x, r, c.v, c.w, c.out);
+    case FWIME_OP_BORN: return run_born(x, r, c.v, c.w, c.in1, c.out);
+    case FWIME_OP_BORN_ADJ: return run_born_adj(x, r, false, c.v, c.w, c.in1, c.out, c.accumulate);
+    case FWIME_OP_BORN_EXT: return run_born_ext(x, r, c.v, c.w, c.in1, c.out);
+    case FWIME_OP_BORN_EXT_ADJ: return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate);
+    case FWIME_OP_TOMO: return run_tomo(x, r, c.v, c.w, c.in1, c.in2, c.out);
+    case FWIME_OP_TOMO_ADJ: return run_tomo_adj(x, r, false, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, 0.f);
+    case FWIME_OP_GRADIENT: return run_tomo_adj(x, r, true, c.v, c.w, c.in1, c.in2, c.out, 0, c.eps);
+    }
+    return fail(x, FWIME_EINVAL, "unknown operator %d", c.op);
+}
+
+static int run_call(fwime_ctx *x, const Call &c)
+{
+    if (!x->opt_graph || x->opt_plain || x->opt_profile) {
+        x->launches = 0;
+        return enqueue(x, c);
+    }
+    if (x->st == nullptr) return fail(x, FWIME_EINVAL, "graph mode needs a non-default stream");
+    // plan first so the workspace never grows inside a capture
+    {
+        WS w;
+        TRY(plan(x, c.op, w));
+    }
+    char key[256];
+    snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d", c.op, (const void *)c.v, (const void *)c.w,
+             (const void *)c.in1, (const void *)c.in2, (void *)c.out, c.accumulate, (double)c.eps, x->opt_S, x->opt_K,
+             x->opt_zchunk);
+    auto it = x->graphs.find(key);
+    if (it == x->graphs.end()) {
+        CK(cudaStreamBeginCapture(x->st, cudaStreamCaptureModeThreadLocal));
+        x->capturing = true;
+        x->launches = 0;
+        int rc = enqueue(x, c);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(x->st, &graph);
+        x->capturing = false;
+        if (rc != FWIME_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CK(e);
+        Graph gr;
+        gr.launches = x->launches;
+        e = cudaGraphInstantiate(&gr.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        it = x->graphs.emplace(key, gr).first;
+    }
+    x->launches = it->second.launches;
+    CK(cudaGraphLaunch(it->second.exec, x->st));
+    return FWIME_OK;
+}
+
+// host-I/O wrapper: stage inputs, run, copy outputs back, wait
+enum { K_NONE = 0, K_DATA, K_MODEL, K_EXT };
+
+static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!c.v || !c.w || !c.out) return fail(x, FWIME_EINVAL, "null pointer argument");
+    if (!x->opt_host_io) return run_call(x, c);
+    WS w;
+    TRY(plan(x, c.op, w));
+    const size_t nm = (size_t)x->g.nz * x->g.nx, nd = (size_t)x->nshot * x->g.nt * x->nrec;
+    auto count = [&](int k) -> size_t {
+        return k == K_DATA ? nd : (k == K_MODEL ? nm : (k == K_EXT ? (size_t)x->g.nh * nm : 0));
+    };
+    // staging: data in -> sd1, dv -> sdv, p~ -> sm1, data out -> sd2, model/image out -> smo
+    auto stage_in = [&](int k) -> float * { return k == K_DATA ? w.sd1 : (k == K_MODEL ? w.sdv : w.sm1); };
+    float *in1 = kin1 ? stage_in(kin1) : nullptr;
+    float *in2 = kin2 ? stage_in(kin2) : nullptr;
+    float *out = kout == K_DATA ? w.sd2 : w.smo;
+    CK(cudaMemcpyAsync(w.sv, c.v, nm * sizeof(float), cudaMemcpyHostToDevice, x->st));
+    CK(cudaMemcpyAsync(w.sw, c.w, (size_t)x->nshot * x->g.nt * sizeof(float), cudaMemcpyHostToDevice, x->st));
+    if (in1) CK(cudaMemcpyAsync(in1, c.in1, count(kin1) * sizeof(float), cudaMemcpyHostToDevice, x->st));
+    if (in2) CK(cudaMemcpyAsync(in2, c.in2, count(kin2) * sizeof(float), cudaMemcpyHostToDevice, x->st));
+    if (c.accumulate) CK(cudaMemcpyAsync(out, c.out, count(kout) * sizeof(float), cudaMemcpyHostToDevice, x->st));
+    float *user_out = c.out;
+    c.v = w.sv; c.w = w.sw; c.in1 = in1; c.in2 = in2; c.out = out;
+    x->launches = 0;
+    TRY(enqueue(x, c));
+    CK(cudaMemcpyAsync(user_out, out, count(kout) * sizeof(float), cudaMemcpyDeviceToHost, x->st));
+    return fwime_sync(x);
+}
+
+// ================================================================ C ABI
+
+extern "C" {
+
+const char *fwime_strerror(int code)
+{
+    switch (code) {
+    case FWIME_OK: return "ok";
+    case FWIME_EINVAL: return "invalid argument";
+    case FWIME_ENOMEM: return "out of device memory or over the workspace budget";
+    case FWIME_ECFL: return "CFL condition violated or non-positive velocity";
+    case FWIME_ECUDA: return "CUDA runtime error";
+    case FWIME_ETIMEOUT: return "device-side wait timed out";
+    case FWIME_EBUSY: return "context busy";
+    }
+    return "unknown error";
+}
+
+int fwime_workspace_bytes(const fwime_grid *g, const fwime_geom *geo, int op, int shots_per_batch, int segment,
+                          size_t *bytes)
+{
+    if (validate(g, geo, nullptr) != FWIME_OK || !bytes || op < 0 || op > FWIME_OP_GRADIENT) return FWIME_EINVAL;
+    const int NZ = g->nz + 2 * (g->sponge + 4), NX = g->nx + 2 * (g->sponge + 4), NXP = (NX + 31) / 32 * 32;
+    const long long P = (long long)NZ * NXP;
+    int K = segment > 0 ? segment : auto_K(g->nt);
+    K = std::max(1, std::min(K, g->nt - 1));
+    Sizes s = op_sizes(*g, geo->nshot, geo->nrec, P, NZ, NXP, op, K, false);
+    const int S = shots_per_batch > 0 ? std::min(shots_per_batch, geo->nshot) : geo->nshot;
+    *bytes = (s.model + s.per_shot * (size_t)S) * sizeof(float) + 4096;
+    return FWIME_OK;
+}
+
+int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo, size_t max_workspace_bytes,
+                 void *cuda_stream)
+{
+    if (!out) return FWIME_EINVAL;
+    *out = nullptr;
+    if (validate(g, geo, nullptr) != FWIME_OK) return FWIME_EINVAL;
+    fwime_ctx *x = new fwime_ctx();
+    x->g = *g;
+    x->nshot = geo->nshot;
+    x->nrec = geo->nrec;
+    x->src_iz.assign(geo->src_iz, geo->src_iz + geo->nshot);
+    x->src_ix.assign(geo->src_ix, geo->src_ix + geo->nshot);
+    x->rec_iz.assign(geo->rec_iz, geo->rec_iz + geo->nrec);
+    x->rec_ix.assign(geo->rec_ix, geo->rec_ix + geo->nrec);
+    x->o = g->sponge + 4;
+    x->NZ = g->nz + 2 * x->o;
+    x->NX = g->nx + 2 * x->o;
+    x->NXP = (x->NX + 31) / 32 * 32;
+    x->P = (long long)x->NZ * x->NXP;
+    x->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    x->max_ws = max_workspace_bytes;
+    cudaGetDevice(&x->device);
+    std::vector<int> so(x->nshot), ro(x->nrec);
+    for (int s = 0; s < x->nshot; ++s) so[s] = (x->src_iz[s] + x->o) * x->NXP + x->src_ix[s] + x->o;
+    for (int r = 0; r < x->nrec; ++r) ro[r] = (x->rec_iz[r] + x->o) * x->NXP + x->rec_ix[r] + x->o;
+    bool ok = cudaMalloc(&x->d_src_off, so.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&x->d_rec_off, ro.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&x->d_status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&x->d_J, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&x->d_part, 1024 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&x->h_J, sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMemcpy(x->d_src_off, so.data(), so.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(x->d_rec_off, ro.data(), ro.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemset(x->d_status, 0, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemset(x->d_J, 0, sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        fwime_destroy(x);
+        return FWIME_ENOMEM;
+    }
+    *x->h_J = 0.0;
+    *out = x;
+    return FWIME_OK;
+}
+
+void fwime_destroy(fwime_ctx *x)
+{
+    if (!x) return;
+    if (x->st) cudaStreamSynchronize(x->st);
+    else cudaDeviceSynchronize();
+    for (auto &kv : x->graphs) cudaGraphExecDestroy(kv.second.exec);
+    for (auto e : x->ev) cudaEventDestroy(e);
+    cudaFree(x->ws);
+    cudaFree(x->d_src_off);
+    cudaFree(x->d_rec_off);
+    cudaFree(x->d_status);
+    cudaFree(x->d_J);
+    cudaFree(x->d_part);
+    if (x->h_J) cudaFreeHost(x->h_J);
+    delete x;
+}
+
+int fwime_set_option(fwime_ctx *x, int option, long long value)
+{
+    if (!x) return FWIME_EINVAL;
+    if (x->capturing) return FWIME_EBUSY;
+    switch (option) {
+    case FWIME_OPT_SHOTS_PER_BATCH: if (value < 0) break; x->opt_S = (int)value; return FWIME_OK;
+    case FWIME_OPT_SEGMENT: if (value < 0) break; x->opt_K = (int)value; return FWIME_OK;
+    case FWIME_OPT_PLAIN: x->opt_plain = value != 0; return FWIME_OK;
+    case FWIME_OPT_GRAPH: x->opt_graph = value != 0; return FWIME_OK;
+    case FWIME_OPT_HOST_IO: x->opt_host_io = value != 0; return FWIME_OK;
+    case FWIME_OPT_ZCHUNK: if (value < 0 || value > 4096) break; x->opt_zchunk = (int)value; return FWIME_OK;
+    case FWIME_OPT_PROFILE: x->opt_profile = value != 0; return FWIME_OK;
+    default: break;
+    }
+    return fail(x, FWIME_EINVAL, "bad option %d = %lld", option, value);
+}
+
+int fwime_get_option(fwime_ctx *x, int option, long long *value)
+{
+    if (!x || !value) return FWIME_EINVAL;
+    switch (option) {
+    case FWIME_OPT_SHOTS_PER_BATCH: *value = x->opt_S; return FWIME_OK;
+    case FWIME_OPT_SEGMENT: *value = x->opt_K; return FWIME_OK;
+    case FWIME_OPT_PLAIN: *value = x->opt_plain; return FWIME_OK;
+    case FWIME_OPT_GRAPH: *value = x->opt_graph; return FWIME_OK;
+    case FWIME_OPT_HOST_IO: *value = x->opt_host_io; return FWIME_OK;
+    case FWIME_OPT_ZCHUNK: *value = x->opt_zchunk; return FWIME_OK;
+    case FWIME_OPT_LAUNCHES: *value = x->launches; return FWIME_OK;
+    case FWIME_OPT_WORKSPACE: *value = (long long)x->ws_bytes; return FWIME_OK;
+    case FWIME_OPT_PROFILE: *value = x->opt_profile; return FWIME_OK;
+    }
+    return fail(x, FWIME_EINVAL, "bad option %d", option);
+}
+
+int fwime_forward(fwime_ctx *x, const float *v, const float *w, float *d)
+{
+    Call c{FWIME_OP_FORWARD, v, w, nullptr, nullptr, d, 0, 0.f};
+    if (!x) return FWIME_EINVAL;
+    return call_op(x, c, K_NONE, K_NONE, K_DATA);
+}
+
+int fwime_born(fwime_ctx *x, const float *v, const float *w, const float *dv, float *d)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!dv) return fail(x, FWIME_EINVAL, "null dv");
+    Call c{FWIME_OP_BORN, v, w, dv, nullptr, d, 0, 0.f};
+    return call_op(x, c, K_MODEL, K_NONE, K_DATA);
+}
+
+int fwime_born_adj(fwime_ctx *x, const float *v, const float *w, const float *d, float *dv, int accumulate)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!d) return fail(x, FWIME_EINVAL, "null data");
+    Call c{FWIME_OP_BORN_ADJ, v, w, d, nullptr, dv, accumulate ? 1 : 0, 0.f};
+    return call_op(x, c, K_DATA, K_NONE, K_MODEL);
+}
+
+int fwime_born_ext(fwime_ctx *x, const float *v, const float *w, const float *pt, float *d)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!pt) return fail(x, FWIME_EINVAL, "null p~");
+    Call c{FWIME_OP_BORN_EXT, v, w, pt, nullptr, d, 0, 0.f};
+    return call_op(x, c, K_EXT, K_NONE, K_DATA);
+}
+
+int fwime_born_ext_adj(fwime_ctx *x, const float *v, const float *w, const float *d, float *pt, int accumulate)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!d) return fail(x, FWIME_EINVAL, "null data");
+    Call c{FWIME_OP_BORN_EXT_ADJ, v, w, d, nullptr, pt, accumulate ? 1 : 0, 0.f};
+    return call_op(x, c, K_DATA, K_NONE, K_EXT);
+}
+
+int fwime_tomo(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dv, float *d)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!pt || !dv) return fail(x, FWIME_EINVAL, "null p~ or dv");
+    Call c{FWIME_OP_TOMO, v, w, pt, dv, d, 0, 0.f};
+    return call_op(x, c, K_EXT, K_MODEL, K_DATA);
+}
+
+int fwime_tomo_adj(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *d, float *dv,
+                   int accumulate)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!pt || !d) return fail(x, FWIME_EINVAL, "null p~ or data");
+    Call c{FWIME_OP_TOMO_ADJ, v, w, pt, d, dv, accumulate ? 1 : 0, 0.f};
+    return call_op(x, c, K_EXT, K_DATA, K_MODEL);
+}
+
+int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
+                   float *grad, double *objective)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!pt || !dobs) return fail(x, FWIME_EINVAL, "null p~ or observed data");
+    if (!(eps >= 0.f)) return fail(x, FWIME_EINVAL, "eps must be >= 0");
+    x->user_J = objective;
+    Call c{FWIME_OP_GRADIENT, v, w, pt, dobs, grad, 0, eps};
+    return call_op(x, c, K_EXT, K_DATA, K_MODEL);
+}
+
+int fwime_sync(fwime_ctx *x)
+{
+    if (!x) return FWIME_EINVAL;
+    CK(x->st ? cudaStreamSynchronize(x->st) : cudaDeviceSynchronize());
+    TRY(prof_collect(x));
+    int st = 0;
+    CK(cudaMemcpy(&st, x->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(x->d_status, 0, sizeof(int)));
+    if (x->user_J) {
+        *x->user_J = *x->h_J;
+        x->user_J = nullptr;
+    }
+    if (st & ST_CFL) return fail(x, FWIME_ECFL, "velocity violates the CFL bound or is not positive");
+    return FWIME_OK;
+}
+
+int fwime_profile_read(fwime_ctx *x, int kernel, double *ms, long long *launches, double *bytes, int reset)
+{
+    if (!x || kernel < 0 || kernel > FWIME_K_OTHER) return FWIME_EINVAL;
+    TRY(prof_collect(x));
+    if (ms) *ms = x->prof_ms[kernel];
+    if (launches) *launches = x->prof_n[kernel];
+    if (bytes) *bytes = x->prof_bytes[kernel];
+    if (reset)
+        for (int k = 0; k < 5; ++k) { x->prof_ms[k] = 0; x->prof_bytes[k] = 0; x->prof_n[k] = 0; }
+    return FWIME_OK;
+}
+
+int fwime_last_error_detail(fwime_ctx *x, char *buf, size_t n)
+{
+    if (!x || !buf || n == 0) return FWIME_EINVAL;
+    snprintf(buf, n, "%s", x->err);
+    return FWIME_OK;
+}
+
+}  // extern "C"

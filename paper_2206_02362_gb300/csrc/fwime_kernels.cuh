@@ -1,0 +1,130 @@
+// Internal kernel interfaces of libfwime (not part of the C ABI).
+//
+// Field layout on the device: every wavefield of one shot is a padded grid
+// [NZ][NXP] of FP32, NZ = nz + 2(W+4), NX = nx + 2(W+4), NXP = NX rounded up to
+// a multiple of 32 floats (128-byte rows).  The physical point (iz, ix) sits at
+// (iz + W + 4, ix + W + 4).  "Active" points are 4 <= IZ < NZ-4, 4 <= IX < NX-4;
+// every other point of every field is zero and stays zero because the sponge
+// factors gz[IZ] gx[IX] (and c) are zero there.
+//
+// Shots advanced together ("a batch") are consecutive fields P = NZ*NXP apart;
+// a ring of K time slots holds [K][S][P].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwk {
+
+constexpr int STRIP = 128;      // x-points per warp in the stencil kernel (32 lanes x float4)
+constexpr int PROP_WARPS = 4;   // warps per CTA in the stencil kernel
+constexpr int EXT_TX = 128;     // x-points per CTA in the scatter / imaging kernels
+constexpr int MAX_NH = 201;     // largest supported number of subsurface offsets
+
+// status bits latched by kernels
+constexpr int ST_CFL = 1;
+constexpr int ST_BADV = 2;
+
+struct PropArgs {
+    int NZ, NXP, zchunk, nstrip, nchunk;
+    long long P;                   // floats per shot field
+    float ax[5], az[5];            // 8th-order coefficients divided by dx^2, dz^2
+    float inv_dt2;
+    const float *c, *gz, *gx;      // model: c = v^2 dt^2 [P], sponge factors [NZ], [NXP]
+    const float *cur;              // q^n           (shot s at + s*P)
+    const float *prev;             // q^{n-1}
+    float *out;                    // q^{n+1}       (may alias prev)
+    float *d2;                     // optional (q^{n+1} - 2 q^n + q^{n-1}) / dt^2
+    // optional point source: s += amp at src_off[s]
+    const int *src_off;
+    const float *src_amp;          // amplitude of shot s at src_amp[s * src_stride]
+    long long src_stride;
+    float src_scale;               // 1 / (dx dz)
+    // optional dense local source: s += sum_i alpha_i f_i + coef * fc
+    const float *f0, *f1, *f2;
+    float a0, a1, a2;
+    const float *coef, *fc;
+};
+
+struct PointsArgs {
+    int nrec;
+    long long P;
+    const int *rec_off;            // [nrec] linear offsets in a field
+    // record: d[s*dstride + r] (= or +=) f1[s*P + off] (+ f2[s*P + off])
+    const float *f1, *f2;
+    float *d;
+    long long dstride;
+    int accumulate;
+    // inject: fld[s*P + off] += c[off] * val[s*vstride + r]   (c g at a receiver; g = 1 on the
+    // physical grid, where receivers live)
+    float *fld;
+    const float *val;
+    long long vstride;
+    const float *c;
+};
+
+// A ring operand of the segment kernels: slot of time step n (pair row j) is
+//   mod > 0 : (n + shift) % mod        mod == 0 : j + shift
+struct RingRef {
+    const float *base;
+    long long slot_stride;         // floats between slots (S_cap * P)
+    int mod, shift;
+};
+
+struct ExtArgs {
+    int NXP, nh, hm, S, npair, n0;
+    long long P;
+    int z_lo, z_hi, x_lo, x_hi;    // output rows/cols processed
+    int sigma;                     // +1: out(y) = sum_h W(y-h,h) D(y-2h); -1: W(y+h,h) D(y+2h)
+    const float *W;                // [nh][P] weights (zero off the physical grid)
+    RingRef in;                    // D
+    RingRef outr;                  // output ring (written through a non-const cast)
+    int accumulate;
+};
+
+enum { IMG_EXT = 0, IMG_CONTRACT = 1, IMG_LOCAL = 2 };
+
+struct ImgArgs {
+    int NXP, nh, hm, S, npair, n0;
+    long long P;
+    int z_lo, z_hi, x_lo, x_hi;
+    RingRef D;                     // source-side field  D(x - h)
+    RingRef L;                     // receiver-side field L(x + h)
+    RingRef M2;                    // IMG_LOCAL: second adjoint field (may be null base)
+    RingRef Ds;                    // IMG_LOCAL: scattered D2t field (may be null base)
+    float alpha;                   // IMG_LOCAL: weight of D * L
+    const float *pt;               // IMG_CONTRACT: p~ padded [nh][P]
+    float *img;                    // IMG_EXT: [nh][P]; others: [P]
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
+cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st);
+cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
+cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
+
+// model preparation
+struct PrepArgs {
+    int nz, nx, o, NZ, NX, NXP, W;
+    float dt, cfl_limit2;          // (2 / (dt sqrt(6.5016 (1/dx^2 + 1/dz^2))))^2 = vmax^2 bound
+    const float *v;                // [nz][nx]
+    float *c, *gz, *gx, *bpad;     // padded outputs
+    int *status;
+};
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st);
+
+// elementwise helpers on padded / physical grids
+cudaError_t launch_embed_scale(const float *phys, const float *scale_pad, float *out_pad, int nz, int nx,
+                               int o, int NXP, float alpha, cudaStream_t st);
+cudaError_t launch_ext_weights(const float *pt, const float *bpad, const float *dv, const float *v, float *Wout,
+                               int nh, int nz, int nx, int o, int NXP, long long P, int mode, cudaStream_t st);
+cudaError_t launch_finalize(const float *acc1, const float *acc2, const float *bpad, const float *v, float *out,
+                            int nplanes, int nz, int nx, int o, int NXP, long long P, int mode, int accumulate,
+                            cudaStream_t st);
+cudaError_t launch_residual(const float *pred, const float *dobs, float *r, long long n, double *partials,
+                            int nblocks, cudaStream_t st);
+cudaError_t launch_sum_partials(const double *partials, int n, double *out, int accumulate, double scale,
+                                cudaStream_t st);
+cudaError_t launch_dso(const float *pt, int nh, long long PP, double *partials, int nblocks, cudaStream_t st);
+cudaError_t launch_copy_fields(float *dst, const float *src, long long n, cudaStream_t st);
+
+}  // namespace fwk

@@ -1,0 +1,180 @@
+// One time step of the 2-D acoustic constant-density wave equation, 2nd order
+// in time and 8th order in space, with the Cerjan-type sponge fused in
+// (Barnier et al., Theory section: the acoustic isotropic constant-density
+// two-way operator f of Eq. 1; Marmousi2 section: absorbing boundaries on all
+// sides):
+//
+//   q^{n+1} = g (2 q^n - g q^{n-1} + c (L q^n + s^n)),   g = gz[IZ] gx[IX],  c = v^2 dt^2
+//
+// The same kernel advances the adjoint wavefield backward in time: with
+// mu = c g lambda the exact transpose of the recursion takes the same form
+// (mu^n from mu^{n+1}, mu^{n+2}), so forward and adjoint share this code.
+//
+// Work decomposition (HBM-bound, no tensor cores): one warp owns a strip of
+// 128 x-points (32 lanes x float4) and a chunk of rows, marching down z with a
+// 9-row register queue, so every row of q^n is read from memory once per
+// strip; the +-4 x-neighbours come from the adjacent lanes by warp shuffles
+// and, at the strip edges, one extra float4 per row.  q^{n-1}, c and the
+// output are touched once, coalesced.  Sources (point, dense local terms) and
+// the second time derivative (for Born-type scattering) are fused in.
+#include "fwime_kernels.cuh"
+
+namespace fwk {
+
+__device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float cmp(const float4 &v, int j)
+{
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 shfl_up4(float4 v)
+{
+    v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
+    v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
+    v.z = __shfl_up_sync(0xffffffffu, v.z, 1);
+    v.w = __shfl_up_sync(0xffffffffu, v.w, 1);
+    return v;
+}
+__device__ __forceinline__ float4 shfl_down4(float4 v)
+{
+    v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
+    v.z = __shfl_down_sync(0xffffffffu, v.z, 1);
+    v.w = __shfl_down_sync(0xffffffffu, v.w, 1);
+    return v;
+}
+
+template <bool LOCAL, bool D2, bool SRC>
+__global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * PROP_WARPS + (threadIdx.x >> 5);
+    if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
+    const int strip = wid % a.nstrip, chunk = wid / a.nstrip;
+    const int x = strip * STRIP + lane * 4;
+    const int z0 = 4 + chunk * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.NZ - 4);
+    const bool xin = x < a.NXP;
+    const long long so = (long long)blockIdx.y * a.P;
+    const float *__restrict__ cur = a.cur + so;
+    const float *prev = a.prev + so;
+    float *out = a.out + so;
+    const long long NXP = a.NXP;
+
+    float4 q[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = xin ? ldg4(cur + (long long)(z0 - 4 + k) * NXP + x) : f4zero();
+    const float4 gxv = xin ? ldg4(a.gx + x) : f4zero();
+    long long soff = -1;
+    float amp = 0.f;
+    if (SRC) {
+        soff = a.src_off[blockIdx.y];
+        amp = a.src_amp[(long long)blockIdx.y * a.src_stride] * a.src_scale;
+    }
+    const float axc = a.ax[0] + a.az[0];
+
+    for (int z = z0; z < z1; ++z) {
+        const long long row = (long long)z * NXP;
+        q[8] = xin ? ldg4(cur + row + 4 * NXP + x) : f4zero();
+        float4 L = shfl_up4(q[4]);
+        float4 R = shfl_down4(q[4]);
+        if (lane == 0) L = (x >= 4) ? ldg4(cur + row + x - 4) : f4zero();
+        if (lane == 31) R = (x + 4 < a.NXP) ? ldg4(cur + row + x + 4) : f4zero();
+        const float r[12] = {L.x, L.y, L.z, L.w, q[4].x, q[4].y, q[4].z, q[4].w, R.x, R.y, R.z, R.w};
+        if (xin) {
+            const long long idx = row + x;
+            const float4 pv = ld4(prev + idx);
+            const float4 cv = ldg4(a.c + idx);
+            const float gzz = __ldg(a.gz + z);
+            float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();
+            if (LOCAL) {
+                if (a.f0) lf0 = ldg4(a.f0 + so + idx);
+                if (a.f1) lf1 = ldg4(a.f1 + so + idx);
+                if (a.f2) lf2 = ldg4(a.f2 + so + idx);
+                if (a.fc) { lcf = ldg4(a.coef + idx); lfc = ldg4(a.fc + so + idx); }
+            }
+            float o[4], d2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float c0 = r[j + 4];
+                float lap = axc * c0;
+                lap = fmaf(a.ax[1], r[j + 3] + r[j + 5], lap);
+                lap = fmaf(a.ax[2], r[j + 2] + r[j + 6], lap);
+                lap = fmaf(a.ax[3], r[j + 1] + r[j + 7], lap);
+                lap = fmaf(a.ax[4], r[j + 0] + r[j + 8], lap);
+                lap = fmaf(a.az[1], cmp(q[3], j) + cmp(q[5], j), lap);
+                lap = fmaf(a.az[2], cmp(q[2], j) + cmp(q[6], j), lap);
+                lap = fmaf(a.az[3], cmp(q[1], j) + cmp(q[7], j), lap);
+                lap = fmaf(a.az[4], cmp(q[0], j) + cmp(q[8], j), lap);
+                float s = 0.f;
+                if (LOCAL) {
+                    s = fmaf(a.a0, cmp(lf0, j), s);
+                    s = fmaf(a.a1, cmp(lf1, j), s);
+                    s = fmaf(a.a2, cmp(lf2, j), s);
+                    s = fmaf(cmp(lcf, j), cmp(lfc, j), s);
+                }
+                if (SRC) s += (soff == idx + j) ? amp : 0.f;
+                const float g = gzz * cmp(gxv, j);
+                const float pj = cmp(pv, j);
+                o[j] = g * (2.f * c0 - g * pj + cmp(cv, j) * (lap + s));
+                d2[j] = (o[j] - 2.f * c0 + pj) * a.inv_dt2;
+            }
+            st4(out + idx, make_float4(o[0], o[1], o[2], o[3]));
+            if (D2) st4(a.d2 + so + idx, make_float4(d2[0], d2[1], d2[2], d2[3]));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
+    }
+}
+
+cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st)
+{
+    const int nwarps = a.nstrip * a.nchunk;
+    dim3 grid((nwarps + PROP_WARPS - 1) / PROP_WARPS, nshot);
+    dim3 block(PROP_WARPS * 32);
+    const bool local = a.f0 || a.f1 || a.f2 || a.fc;
+    const bool d2 = a.d2 != nullptr;
+    const bool src = a.src_off != nullptr;
+    const int key = (local ? 4 : 0) | (d2 ? 2 : 0) | (src ? 1 : 0);
+    switch (key) {
+    case 0: k_prop<false, false, false><<<grid, block, 0, st>>>(a); break;
+    case 1: k_prop<false, false, true><<<grid, block, 0, st>>>(a); break;
+    case 2: k_prop<false, true, false><<<grid, block, 0, st>>>(a); break;
+    case 3: k_prop<false, true, true><<<grid, block, 0, st>>>(a); break;
+    case 4: k_prop<true, false, false><<<grid, block, 0, st>>>(a); break;
+    case 5: k_prop<true, false, true><<<grid, block, 0, st>>>(a); break;
+    case 6: k_prop<true, true, false><<<grid, block, 0, st>>>(a); break;
+    default: k_prop<true, true, true><<<grid, block, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- points
+// Receiver recording d[n][r] = q^n(rec_r) and adjoint injection of the data
+// residual at the receivers (the transpose of recording, scaled by c g so it
+// enters the mu-form adjoint recursion inside c (L mu + R^T r)).
+__global__ void k_points(const PointsArgs a)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (r >= a.nrec) return;
+    const long long off = (long long)s * a.P + a.rec_off[r];
+    if (a.d) {
+        float val = a.f1[off];
+        if (a.f2) val += a.f2[off];
+        float *dp = a.d + (long long)s * a.dstride + r;
+        *dp = a.accumulate ? *dp + val : val;
+    }
+    if (a.fld) atomicAdd(a.fld + off, a.c[a.rec_off[r]] * a.val[(long long)s * a.vstride + r]);
+}
+
+cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st)
+{
+    dim3 grid((a.nrec + 127) / 128, nshot);
+    k_points<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fwk
