@@ -204,6 +204,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2206_02362_gb300 as fw
+    from paper_2206_02362_gb300.shard import allreduce_model
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -232,7 +233,7 @@ def main():
         c.born_ext_adj(vv, ww, dd, ii, sync=False)
         launches[0] += n + c.launches
         if world > 1:
-            dist.all_reduce(ii)        # images summed over the shots of all ranks
+            allreduce_model(ii)        # images summed over the shots of all ranks
 
     for _ in range(args.warmup):
         step(ctx, v, w, pt, d, img)

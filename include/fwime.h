@@ -105,7 +105,7 @@ enum {
 /* Operators, for fwime_workspace_bytes. */
 enum {
     FWIME_OP_FORWARD = 0, FWIME_OP_BORN, FWIME_OP_BORN_ADJ, FWIME_OP_BORN_EXT,
-    FWIME_OP_BORN_EXT_ADJ, FWIME_OP_TOMO, FWIME_OP_TOMO_ADJ, FWIME_OP_GRADIENT
+    FWIME_OP_BORN_EXT_ADJ, FWIME_OP_TOMO, FWIME_OP_TOMO_ADJ, FWIME_OP_GRADIENT, FWIME_OP_OBJECTIVE
 };
 
 /* Creates a context on the current CUDA device.  `max_workspace_bytes` caps the
@@ -157,6 +157,13 @@ int fwime_tomo_adj(fwime_ctx *ctx, const float *v, const float *w, const float *
  * "invertible modified DSO" operator; it does not enter the gradient. */
 int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                    const float *dobs, float eps, float *grad, double *objective);
+
+/* The objective Phi of fwime_gradient alone (Eq. 1 at fixed p~): the forward
+ * sweep f + B~ p~ and the residual norm, without the adjoint sweep -- the
+ * extra objective evaluation a line search makes (Computational aspects).
+ * *objective (host double) is written when the work has completed. */
+int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
+                    const float *dobs, float eps, double *objective);
 
 /* Waits for the context's stream and returns the latched device status
  * (FWIME_OK, FWIME_ECFL, FWIME_ETIMEOUT) or FWIME_ECUDA; clears the latch. */

@@ -30,11 +30,11 @@ OPT_PROFILE = 9
 K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
 KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 (OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
- OP_GRADIENT) = range(8)
+ OP_GRADIENT, OP_OBJECTIVE) = range(9)
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_sync", "fwime_profile_read",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_sync", "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
 
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_tomo.argtypes = [vp, fp, fp, fp, fp, fp]
     lib.fwime_tomo_adj.argtypes = [vp, fp, fp, fp, fp, fp, ip]
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_sync.argtypes = [vp]
     lib.fwime_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ip]
@@ -282,6 +283,13 @@ class Context:
         self._J = ctypes.c_double(0.0)
         self._done(self._lib.fwime_gradient(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs), ctypes.c_float(eps),
                                             _ptr(grad), ctypes.byref(self._J)), "fwime_gradient", sync)
+        return float(self._J.value)
+
+    def objective(self, v, w, pt, dobs, eps=0.0, sync=True):
+        """Phi = 1/2||f + B~p~ - dobs||^2 + eps^2/2||D p~||^2 alone (no adjoint sweep); valid once synced."""
+        self._J = ctypes.c_double(0.0)
+        self._done(self._lib.fwime_objective(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs), ctypes.c_float(eps),
+                                             ctypes.byref(self._J)), "fwime_objective", sync)
         return float(self._J.value)
 
     def close(self):

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -59,6 +61,9 @@ struct fwime_ctx {
     // persistent device memory
     int *d_src_off = nullptr, *d_rec_off = nullptr, *d_status = nullptr;
     double *d_J = nullptr, *d_part = nullptr, *h_J = nullptr;
+    int *h_status = nullptr;
+    void *small = nullptr;          // one stream-ordered block: J, partials, status, offsets
+    std::vector<int> h_off;         // host copy of the offsets (source of the async upload)
     double *user_J = nullptr;
     // workspace arena
     char *ws = nullptr;
@@ -77,6 +82,25 @@ struct fwime_ctx {
 };
 
 // ------------------------------------------------------------------ helpers
+
+// A process-wide pinned block handing every context two 8-byte slots (objective and
+// status read-back) so that creating a context never calls a synchronising host
+// allocator.  Slots are reused round-robin.
+static double *pinned_slot()
+{
+    static double *pool = nullptr;
+    static std::atomic<unsigned> next{0};
+    static std::once_flag once;
+    constexpr unsigned NSLOT = 8192;
+    std::call_once(once, [] {
+        if (cudaMallocHost(reinterpret_cast<void **>(&pool), 2 * NSLOT * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            pool = nullptr;
+        }
+    });
+    if (!pool) return nullptr;
+    return pool + 2 * (next.fetch_add(1) % NSLOT);
+}
 
 static int fail(fwime_ctx *x, int code, const char *fmt, ...)
 {
@@ -180,10 +204,11 @@ static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int
     case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
     case FWIME_OP_TOMO_ADJ:
     case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + 4 * nseg; break;
+    case FWIME_OP_OBJECTIVE: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 2 * K; break;
     default: break;
     }
     s.per_shot = f * (size_t)P;
-    if (op == FWIME_OP_GRADIENT) s.per_shot += (size_t)g.nt * nrec;
+    if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) s.per_shot += (size_t)g.nt * nrec;
     if (host_io) {
         const size_t nd = (size_t)nshot * g.nt * nrec, nm = (size_t)g.nz * g.nx;
         s.staging = al(nm) + al((size_t)nshot * g.nt) + 2 * al(nd) + al(nh * nm) + al(nm) + al(nh * nm);
@@ -255,18 +280,19 @@ static int plan(fwime_ctx *x, int op, WS &w)
         return fail(x, FWIME_ENOMEM, "operator needs %zu bytes for S=%d, K=%d; budget %zu", need, w.S, w.K, x->max_ws);
     if (need > x->ws_bytes) {
         if (x->capturing) return fail(x, FWIME_EBUSY, "workspace growth during graph capture");
+        // stream-ordered (re)allocation: no device-wide synchronisation, so contexts of other
+        // streams keep running while this one grows
         if (x->ws) {
-            cudaStreamSynchronize(x->st);
             for (auto &kv : x->graphs) cudaGraphExecDestroy(kv.second.exec);
             x->graphs.clear();
-            cudaFree(x->ws);
+            CK(cudaFreeAsync(x->ws, x->st));
             x->ws = nullptr;
             x->ws_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&x->ws, need);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&x->ws), need, x->st);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(x, FWIME_ENOMEM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+            return fail(x, FWIME_ENOMEM, "cudaMallocAsync(%zu): %s", need, cudaGetErrorString(e));
         }
         x->ws_bytes = need;
     }
@@ -284,7 +310,8 @@ static int plan(fwime_ctx *x, int op, WS &w)
     case FWIME_OP_BORN_EXT_ADJ: w.acc1 = take(nh * P); break;
     case FWIME_OP_TOMO: w.W = take(nh * P); w.W2 = take(nh * P); w.coef = take(P); break;
     case FWIME_OP_TOMO_ADJ:
-    case FWIME_OP_GRADIENT: w.W = take(nh * P); w.ptp = take(nh * P); w.acc1 = take(P); w.acc2 = take(P); break;
+    case FWIME_OP_GRADIENT:
+    case FWIME_OP_OBJECTIVE: w.W = take(nh * P); w.ptp = take(nh * P); w.acc1 = take(P); w.acc2 = take(P); break;
     default: break;
     }
     const size_t SP = (size_t)w.S * P;
@@ -299,13 +326,14 @@ static int plan(fwime_ctx *x, int op, WS &w)
     case FWIME_OP_BORN_ADJ:
     case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = 2; break;
     case FWIME_OP_TOMO: nf = 8; nk = 4; break;
+    case FWIME_OP_OBJECTIVE: nf = 4; nk = 2; break;
     default: nf = 4; nk = 3; nr = 3; nck = 4; break;
     }
     for (int i = 0; i < nf; ++i) w.f[i] = take(SP);
     for (int i = 0; i < nk; ++i) w.ring[i] = take((size_t)w.K * SP);
     for (int i = 0; i < nr; ++i) w.ring[nk + i] = take((size_t)w.R * SP);
     if (nck) w.ckpt = take((size_t)w.nseg * nck * SP);
-    if (op == FWIME_OP_GRADIENT) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
+    if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
     w.sv = w.sw = w.sd1 = w.sd2 = w.sm1 = w.sdv = w.smo = nullptr;
     if (x->opt_host_io) {
         const size_t nd = (size_t)x->nshot * x->g.nt * x->nrec, nm = (size_t)x->g.nz * x->g.nx;
@@ -660,10 +688,12 @@ static int run_tomo(fwime_ctx *x, Run &r, const float *v, const float *w, const 
     return FWIME_OK;
 }
 
-// T* (grad = false, r = d) and the FWIME gradient (grad = true, r = f + B~p~ - dobs)
-static int run_tomo_adj(fwime_ctx *x, Run &r, bool grad, const float *v, const float *w, const float *pt,
+// T* (mode 0, r = d), the FWIME gradient (mode 1, r = f + B~p~ - dobs) and the
+// objective alone (mode 2: forward sweep and residual norm, no adjoint sweep)
+static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const float *w, const float *pt,
                         const float *d, float *out, int accumulate, float eps)
 {
+    const bool grad = mode >= 1, objective_only = mode == 2;
     const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
     const size_t nd = (size_t)nt * x->nrec;
     const long long SP = (long long)S * x->P;
@@ -691,19 +721,23 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, bool grad, const float *v, const f
         const size_t fb = sizeof(float) * (size_t)Sb * x->P;
         float *q0c = r.w.f[0], *q0p = r.w.f[1], *qsc = r.w.f[2], *qsp = r.w.f[3];
         for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], fb));
-        TRY(zero(x, Mu, sizeof(float) * R * SP));
-        TRY(zero(x, Zr, sizeof(float) * R * SP));
-        TRY(zero(x, Mu2, sizeof(float) * R * SP));
+        if (!objective_only) {
+            TRY(zero(x, Mu, sizeof(float) * R * SP));
+            TRY(zero(x, Zr, sizeof(float) * R * SP));
+            TRY(zero(x, Mu2, sizeof(float) * R * SP));
+        }
         const float *ws = w + (size_t)s0 * nt;
         float *pred = r.w.pred;
         if (grad) TRY(zero(x, pred, sizeof(float) * Sb * nd));
         // forward sweep
         for (int j = 0; j < nseg; ++j) {
             const long long cb = 4LL * j * SP;
-            TRY(copyf(x, ck + cb, q0c, (size_t)Sb * x->P));
-            TRY(copyf(x, ck + cb + SP, q0p, (size_t)Sb * x->P));
-            TRY(copyf(x, ck + cb + 2 * SP, qsc, (size_t)Sb * x->P));
-            TRY(copyf(x, ck + cb + 3 * SP, qsp, (size_t)Sb * x->P));
+            if (!objective_only) {
+                TRY(copyf(x, ck + cb, q0c, (size_t)Sb * x->P));
+                TRY(copyf(x, ck + cb + SP, q0p, (size_t)Sb * x->P));
+                TRY(copyf(x, ck + cb + 2 * SP, qsc, (size_t)Sb * x->P));
+                TRY(copyf(x, ck + cb + 3 * SP, qsp, (size_t)Sb * x->P));
+            }
             if (!grad && j == nseg - 1) break;
             const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
             for (int n = n0; n < n1; ++n) {
@@ -725,6 +759,7 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, bool grad, const float *v, const f
             LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
             rr = pred;
         }
+        if (objective_only) continue;
         // backward sweep
         for (int j = nseg - 1; j >= 0; --j) {
             const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
@@ -762,9 +797,10 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, bool grad, const float *v, const f
                       ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, r.w.ptp, r.w.acc2));
         }
     }
-    LAUNCH(FWIME_K_OTHER, 20.0 * nm,
-           launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
-                           accumulate, x->st));
+    if (!objective_only)
+        LAUNCH(FWIME_K_OTHER, 20.0 * nm,
+               launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
+                               accumulate, x->st));
     if (grad) {
         LAUNCH(FWIME_K_OTHER, 4.0 * x->g.nh * nm,
                launch_dso(pt, x->g.nh, (long long)x->g.nz * x->g.nx, x->d_part, nred, x->st));
@@ -798,8 +834,9 @@ static int enqueue(fwime_ctx *x, const Call &c)
     case FWIME_OP_BORN_EXT: return run_born_ext(x, r, c.v, c.w, c.in1, c.out);
     case FWIME_OP_BORN_EXT_ADJ: return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate);
     case FWIME_OP_TOMO: return run_tomo(x, r, c.v, c.w, c.in1, c.in2, c.out);
-    case FWIME_OP_TOMO_ADJ: return run_tomo_adj(x, r, false, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, 0.f);
-    case FWIME_OP_GRADIENT: return run_tomo_adj(x, r, true, c.v, c.w, c.in1, c.in2, c.out, 0, c.eps);
+    case FWIME_OP_TOMO_ADJ: return run_tomo_adj(x, r, 0, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, 0.f);
+    case FWIME_OP_GRADIENT: return run_tomo_adj(x, r, 1, c.v, c.w, c.in1, c.in2, c.out, 0, c.eps);
+    case FWIME_OP_OBJECTIVE: return run_tomo_adj(x, r, 2, c.v, c.w, c.in1, c.in2, nullptr, 0, c.eps);
     }
     return fail(x, FWIME_EINVAL, "unknown operator %d", c.op);
 }
@@ -852,7 +889,7 @@ enum { K_NONE = 0, K_DATA, K_MODEL, K_EXT };
 static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
 {
     if (!x) return FWIME_EINVAL;
-    if (!c.v || !c.w || !c.out) return fail(x, FWIME_EINVAL, "null pointer argument");
+    if (!c.v || !c.w || (!c.out && c.op != FWIME_OP_OBJECTIVE)) return fail(x, FWIME_EINVAL, "null pointer argument");
     if (!x->opt_host_io) return run_call(x, c);
     WS w;
     TRY(plan(x, c.op, w));
@@ -864,7 +901,7 @@ static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
     auto stage_in = [&](int k) -> float * { return k == K_DATA ? w.sd1 : (k == K_MODEL ? w.sdv : w.sm1); };
     float *in1 = kin1 ? stage_in(kin1) : nullptr;
     float *in2 = kin2 ? stage_in(kin2) : nullptr;
-    float *out = kout == K_DATA ? w.sd2 : w.smo;
+    float *out = kout == K_DATA ? w.sd2 : (kout == K_NONE ? nullptr : w.smo);
     CK(cudaMemcpyAsync(w.sv, c.v, nm * sizeof(float), cudaMemcpyHostToDevice, x->st));
     CK(cudaMemcpyAsync(w.sw, c.w, (size_t)x->nshot * x->g.nt * sizeof(float), cudaMemcpyHostToDevice, x->st));
     if (in1) CK(cudaMemcpyAsync(in1, c.in1, count(kin1) * sizeof(float), cudaMemcpyHostToDevice, x->st));
@@ -874,7 +911,7 @@ static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
     c.v = w.sv; c.w = w.sw; c.in1 = in1; c.in2 = in2; c.out = out;
     x->launches = 0;
     TRY(enqueue(x, c));
-    CK(cudaMemcpyAsync(user_out, out, count(kout) * sizeof(float), cudaMemcpyDeviceToHost, x->st));
+    if (kout != K_NONE) CK(cudaMemcpyAsync(user_out, out, count(kout) * sizeof(float), cudaMemcpyDeviceToHost, x->st));
     return fwime_sync(x);
 }
 
@@ -899,7 +936,7 @@ const char *fwime_strerror(int code)
 int fwime_workspace_bytes(const fwime_grid *g, const fwime_geom *geo, int op, int shots_per_batch, int segment,
                           size_t *bytes)
 {
-    if (validate(g, geo, nullptr) != FWIME_OK || !bytes || op < 0 || op > FWIME_OP_GRADIENT) return FWIME_EINVAL;
+    if (validate(g, geo, nullptr) != FWIME_OK || !bytes || op < 0 || op > FWIME_OP_OBJECTIVE) return FWIME_EINVAL;
     const int NZ = g->nz + 2 * (g->sponge + 4), NX = g->nx + 2 * (g->sponge + 4), NXP = (NX + 31) / 32 * 32;
     const long long P = (long long)NZ * NXP;
     int K = segment > 0 ? segment : auto_K(g->nt);
@@ -932,19 +969,27 @@ int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo, si
     x->st = reinterpret_cast<cudaStream_t>(cuda_stream);
     x->max_ws = max_workspace_bytes;
     cudaGetDevice(&x->device);
-    std::vector<int> so(x->nshot), ro(x->nrec);
-    for (int s = 0; s < x->nshot; ++s) so[s] = (x->src_iz[s] + x->o) * x->NXP + x->src_ix[s] + x->o;
-    for (int r = 0; r < x->nrec; ++r) ro[r] = (x->rec_iz[r] + x->o) * x->NXP + x->rec_ix[r] + x->o;
-    bool ok = cudaMalloc(&x->d_src_off, so.size() * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&x->d_rec_off, ro.size() * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&x->d_status, sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&x->d_J, sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&x->d_part, 1024 * sizeof(double)) == cudaSuccess &&
-              cudaMallocHost(&x->h_J, sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMemcpy(x->d_src_off, so.data(), so.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemcpy(x->d_rec_off, ro.data(), ro.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemset(x->d_status, 0, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMemset(x->d_J, 0, sizeof(double)) == cudaSuccess;
+    // offsets: [src_off(nshot)][rec_off(nrec)]
+    x->h_off.resize(x->nshot + x->nrec);
+    for (int s = 0; s < x->nshot; ++s) x->h_off[s] = (x->src_iz[s] + x->o) * x->NXP + x->src_ix[s] + x->o;
+    for (int r = 0; r < x->nrec; ++r)
+        x->h_off[x->nshot + r] = (x->rec_iz[r] + x->o) * x->NXP + x->rec_ix[r] + x->o;
+    const size_t small_bytes = (1 + 1024) * sizeof(double) + sizeof(int) * (1 + x->h_off.size());
+    double *slot = pinned_slot();
+    bool ok = slot != nullptr &&
+              cudaMallocAsync(&x->small, small_bytes, x->st) == cudaSuccess;
+    if (ok) {
+        x->h_J = slot;
+        x->h_status = reinterpret_cast<int *>(slot + 1);
+        x->d_J = reinterpret_cast<double *>(x->small);
+        x->d_part = x->d_J + 1;
+        x->d_status = reinterpret_cast<int *>(x->d_part + 1024);
+        x->d_src_off = x->d_status + 1;
+        x->d_rec_off = x->d_src_off + x->nshot;
+        ok = cudaMemsetAsync(x->small, 0, small_bytes, x->st) == cudaSuccess &&
+             cudaMemcpyAsync(x->d_src_off, x->h_off.data(), x->h_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             x->st) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         fwime_destroy(x);
@@ -962,13 +1007,9 @@ void fwime_destroy(fwime_ctx *x)
     else cudaDeviceSynchronize();
     for (auto &kv : x->graphs) cudaGraphExecDestroy(kv.second.exec);
     for (auto e : x->ev) cudaEventDestroy(e);
-    cudaFree(x->ws);
-    cudaFree(x->d_src_off);
-    cudaFree(x->d_rec_off);
-    cudaFree(x->d_status);
-    cudaFree(x->d_J);
-    cudaFree(x->d_part);
-    if (x->h_J) cudaFreeHost(x->h_J);
+    if (x->ws) cudaFreeAsync(x->ws, x->st);
+    if (x->small) cudaFreeAsync(x->small, x->st);
+    cudaGetLastError();
     delete x;
 }
 
@@ -1073,14 +1114,26 @@ int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt
     return call_op(x, c, K_EXT, K_DATA, K_MODEL);
 }
 
+int fwime_objective(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
+                    double *objective)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!pt || !dobs || !objective) return fail(x, FWIME_EINVAL, "null p~, observed data or objective");
+    if (!(eps >= 0.f)) return fail(x, FWIME_EINVAL, "eps must be >= 0");
+    x->user_J = objective;
+    Call c{FWIME_OP_OBJECTIVE, v, w, pt, dobs, nullptr, 0, eps};
+    return call_op(x, c, K_EXT, K_DATA, K_NONE);
+}
+
 int fwime_sync(fwime_ctx *x)
 {
     if (!x) return FWIME_EINVAL;
     CK(x->st ? cudaStreamSynchronize(x->st) : cudaDeviceSynchronize());
     TRY(prof_collect(x));
-    int st = 0;
-    CK(cudaMemcpy(&st, x->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (st) CK(cudaMemset(x->d_status, 0, sizeof(int)));
+    CK(cudaMemcpyAsync(x->h_status, x->d_status, sizeof(int), cudaMemcpyDeviceToHost, x->st));
+    CK(cudaStreamSynchronize(x->st));
+    const int st = *x->h_status;
+    if (st) CK(cudaMemsetAsync(x->d_status, 0, sizeof(int), x->st));
     if (x->user_J) {
         *x->user_J = *x->h_J;
         x->user_J = nullptr;
