@@ -165,6 +165,13 @@ int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *
 int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                     const float *dobs, float eps, double *objective);
 
+/* Autotuner of the stencil kernel's tiling: plans the workspace of operator
+ * `op` (so the batch size is the one the operator will use), then times the
+ * time-step kernel on that batch for candidate rows-per-warp chunkings with
+ * CUDA events and keeps the fastest (FWIME_OPT_ZCHUNK).  Synchronous.  Returns
+ * the chosen chunking and its time per launch (either pointer may be NULL). */
+int fwime_autotune(fwime_ctx *ctx, int op, int *zchunk, float *us_per_launch);
+
 /* Waits for the context's stream and returns the latched device status
  * (FWIME_OK, FWIME_ECFL, FWIME_ETIMEOUT) or FWIME_ECUDA; clears the latch. */
 int fwime_sync(fwime_ctx *ctx);
@@ -177,6 +184,7 @@ int fwime_sync(fwime_ctx *ctx);
 int fwime_profile_read(fwime_ctx *ctx, int kernel, double *ms, long long *launches, double *bytes, int reset);
 
 int fwime_last_error_detail(fwime_ctx *ctx, char *buf, size_t n);
+
 const char *fwime_strerror(int code);
 void fwime_destroy(fwime_ctx *ctx);
 

@@ -34,7 +34,8 @@ KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_sync", "fwime_profile_read",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_autotune", "fwime_sync",
+                 "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
 
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_tomo_adj.argtypes = [vp, fp, fp, fp, fp, fp, ip]
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.fwime_sync.argtypes = [vp]
     lib.fwime_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ip]
@@ -284,6 +286,13 @@ class Context:
         self._done(self._lib.fwime_gradient(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs), ctypes.c_float(eps),
                                             _ptr(grad), ctypes.byref(self._J)), "fwime_gradient", sync)
         return float(self._J.value)
+
+    def autotune(self, op: int) -> tuple[int, float]:
+        """Times the stencil kernel on this operator's batch for candidate chunkings; keeps the fastest.
+        Returns (rows per warp chosen, microseconds per launch)."""
+        zc, us = ctypes.c_int(0), ctypes.c_float(0)
+        self._check(self._lib.fwime_autotune(self._h, int(op), ctypes.byref(zc), ctypes.byref(us)), "fwime_autotune")
+        return int(zc.value), float(us.value)
 
     def objective(self, v, w, pt, dobs, eps=0.0, sync=True):
         """Phi = 1/2||f + B~p~ - dobs||^2 + eps^2/2||D p~||^2 alone (no adjoint sweep); valid once synced."""

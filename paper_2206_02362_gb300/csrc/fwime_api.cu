@@ -1114,6 +1114,52 @@ int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt
     return call_op(x, c, K_EXT, K_DATA, K_MODEL);
 }
 
+int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_out)
+{
+    if (!x || op < 0 || op > FWIME_OP_OBJECTIVE) return FWIME_EINVAL;
+    if (x->capturing) return FWIME_EBUSY;
+    Run r;
+    TRY(plan(x, op, r.w));
+    const int S = r.w.S;
+    // timing needs no model: zero c, the sponge tables and two batch fields
+    TRY(zero(x, r.w.c, sizeof(float) * x->P));
+    TRY(zero(x, r.w.gz, sizeof(float) * x->NZ));
+    TRY(zero(x, r.w.gx, sizeof(float) * x->NXP));
+    TRY(zero(x, r.w.f[0], sizeof(float) * S * x->P));
+    TRY(zero(x, r.w.f[1], sizeof(float) * S * x->P));
+    const int rows = x->NZ - 8;
+    const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int saved = x->opt_zchunk, saved_prof = x->opt_profile;
+    x->opt_profile = 0;
+    int best = 0;
+    float best_us = 1e30f;
+    for (int zc : cand) {
+        if (zc > rows && zc != cand[0]) break;
+        x->opt_zchunk = zc;
+        init_run(x, r, S);
+        for (int it = 0; it < 2; ++it) TRY(prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0));
+        const int reps = 6;
+        CK(cudaEventRecord(e0, x->st));
+        for (int it = 0; it < reps; ++it) TRY(prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0));
+        CK(cudaEventRecord(e1, x->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const float us = 1e3f * ms / reps;
+        if (us < best_us) { best_us = us; best = zc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    x->opt_profile = saved_prof;
+    x->opt_zchunk = best > 0 ? best : saved;
+    if (zchunk_out) *zchunk_out = x->opt_zchunk;
+    if (us_per_launch_out) *us_per_launch_out = best_us;
+    return FWIME_OK;
+}
+
 int fwime_objective(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
                     double *objective)
 {

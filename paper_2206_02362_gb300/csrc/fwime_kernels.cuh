@@ -43,6 +43,7 @@ struct PropArgs {
     const float *f0, *f1, *f2;
     float a0, a1, a2;
     const float *coef, *fc;
+    int naux_max;                  // rows per aux stage (set by launch_prop)
 };
 
 struct PointsArgs {

@@ -29,12 +29,101 @@ __device__ __forceinline__ long long ring_off(const RingRef &r, int n, int j)
 
 // ------------------------------------------------------------------ scatter
 
-template <int NH>
-__global__ void __launch_bounds__(EXT_TX) k_scatter(const ExtArgs a)
+// Register-blocked scatter: a thread owns PY outputs y_j = ybase + 2j (j < PY), so the D
+// samples they need, y_j - 2 sigma h, fall on the NH + PY - 1 even-spaced positions
+// ybase + 2m: one shared-memory load per position serves up to PY multiply-adds.  The
+// thread's PY x NH weights stay in registers for the whole segment.  Outputs are staged
+// through shared memory and stored coalesced.
+template <int NH, int PY, int SIGMA>
+__global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
 {
     extern __shared__ float sm[];
-    const int nh = NH > 0 ? NH : a.nh;
-    const int hm = (nh - 1) / 2;
+    constexpr int HM = (NH - 1) / 2;
+    constexpr int TXS = EXT_TX * PY;               // outputs per CTA
+    constexpr int SPAN = TXS + 4 * HM;             // D window
+    constexpr int NPF = (SPAN + EXT_TX - 1) / EXT_TX;
+    constexpr int NM = NH + PY - 1;
+    const int Z = a.z_lo + blockIdx.y;
+    const int y0 = a.x_lo + blockIdx.x * TXS;
+    const int t = threadIdx.x;
+    const int yb_off = 2 * PY * (t >> 1) + (t & 1);     // offset of this thread's first output
+    const int ybase = y0 + yb_off;
+    const long long rowoff = (long long)Z * a.NXP;
+    const int wbase = y0 - 2 * HM;
+    float *win = sm;                                   // 2 x SPAN
+    float *obuf = sm + 2 * SPAN;                       // TXS staged outputs
+    float *out_base = const_cast<float *>(a.outr.base);
+
+    float Wr[PY][NH];
+#pragma unroll
+    for (int j = 0; j < PY; ++j) {
+        const int y = ybase + 2 * j;
+#pragma unroll
+        for (int ih = 0; ih < NH; ++ih) {
+            const int xs = y - SIGMA * (ih - HM);
+            Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
+        }
+    }
+    float pre[NPF];
+    auto load_window = [&](int p) {
+        const int j = p / a.S, s = p % a.S, n = a.n0 + j;
+        const float *src = a.in.base + ring_off(a.in, n, j) + (long long)s * a.P + rowoff;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int i = t + k * EXT_TX;
+            const int xp = wbase + i;
+            pre[k] = (i < SPAN && xp >= 0 && xp < a.NXP) ? __ldg(src + xp) : 0.f;
+        }
+    };
+    if (a.npair > 0) load_window(0);
+    for (int p = 0; p < a.npair; ++p) {
+        float *buf = win + (p & 1) * SPAN;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int i = t + k * EXT_TX;
+            if (i < SPAN) buf[i] = pre[k];
+        }
+        __syncthreads();
+        if (p + 1 < a.npair) load_window(p + 1);
+        // dv[m] = D(ybase + 2(m - HM)), m = 0 .. NM-1; window index (ybase - wbase) + 2(m - HM)
+        float dv[NM];
+        const float *bb = buf + yb_off;                 // = buf + (ybase - wbase) - 2 HM
+#pragma unroll
+        for (int m = 0; m < NM; ++m) dv[m] = bb[2 * m];
+        float acc[PY];
+#pragma unroll
+        for (int j = 0; j < PY; ++j) {
+            float s = 0.f;
+#pragma unroll
+            for (int ih = 0; ih < NH; ++ih) {
+                // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
+                constexpr int dummy = 0;
+                (void)dummy;
+                s = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], s);
+            }
+            acc[j] = s;
+        }
+#pragma unroll
+        for (int j = 0; j < PY; ++j) obuf[yb_off + 2 * j] = acc[j];
+        __syncthreads();
+        {
+            const int jj = p / a.S, s = p % a.S, n = a.n0 + jj;
+            float *o = out_base + ring_off(a.outr, n, jj) + (long long)s * a.P + rowoff;
+#pragma unroll
+            for (int k = 0; k < PY; ++k) {
+                const int i = t + k * EXT_TX;
+                const int y = y0 + i;
+                if (y < a.x_hi) o[y] = a.accumulate ? o[y] + obuf[i] : obuf[i];
+            }
+        }
+    }
+}
+
+// Generic-nh fallback (weights re-read per pair): any odd nh up to MAX_NH.
+__global__ void __launch_bounds__(EXT_TX) k_scatter_gen(const ExtArgs a)
+{
+    extern __shared__ float sm[];
+    const int nh = a.nh, hm = (nh - 1) / 2;
     const int Z = a.z_lo + blockIdx.y;
     const int y0 = a.x_lo + blockIdx.x * EXT_TX;
     const int y = y0 + threadIdx.x;
@@ -43,89 +132,155 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter(const ExtArgs a)
     const int wbase = y0 - 2 * hm;
     const long long rowoff = (long long)Z * a.NXP;
     float *out_base = const_cast<float *>(a.outr.base);
-
-    float Wr[NH > 0 ? NH : 1];
-    if (NH > 0) {
-#pragma unroll
-        for (int ih = 0; ih < (NH > 0 ? NH : 1); ++ih) {
-            const int xs = y - a.sigma * (ih - hm);
-            Wr[ih] = (yin && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
-        }
-    }
-    constexpr int MAXPF = (EXT_TX + 4 * ((MAX_NH - 1) / 2) + EXT_TX - 1) / EXT_TX;
-    const int npf = (span + EXT_TX - 1) / EXT_TX;
-    float pre[MAXPF];
-
-    auto load_window = [&](int p) {
+    for (int p = 0; p < a.npair; ++p) {
         const int j = p / a.S, s = p % a.S, n = a.n0 + j;
         const float *src = a.in.base + ring_off(a.in, n, j) + (long long)s * a.P + rowoff;
-#pragma unroll
-        for (int k = 0; k < MAXPF; ++k) {
-            if (k < npf) {
-                const int i = threadIdx.x + k * EXT_TX;
-                const int xp = wbase + i;
-                pre[k] = (i < span && xp >= 0 && xp < a.NXP) ? __ldg(src + xp) : 0.f;
-            }
-        }
-    };
-
-    if (a.npair > 0) load_window(0);
-    for (int p = 0; p < a.npair; ++p) {
-        float *buf = sm + (p & 1) * span;
-#pragma unroll
-        for (int k = 0; k < MAXPF; ++k) {
-            const int i = threadIdx.x + k * EXT_TX;
-            if (k < npf && i < span) buf[i] = pre[k];
+        __syncthreads();
+        for (int i = threadIdx.x; i < span; i += EXT_TX) {
+            const int xp = wbase + i;
+            sm[i] = (xp >= 0 && xp < a.NXP) ? __ldg(src + xp) : 0.f;
         }
         __syncthreads();
-        if (p + 1 < a.npair) load_window(p + 1);
         float acc = 0.f;
         const int c0 = threadIdx.x + 2 * hm;
-        if (NH > 0) {
-#pragma unroll
-            for (int ih = 0; ih < (NH > 0 ? NH : 1); ++ih) acc = fmaf(Wr[ih], buf[c0 - 2 * a.sigma * (ih - hm)], acc);
-        } else {
-            for (int ih = 0; ih < nh; ++ih) {
-                const int xs = y - a.sigma * (ih - hm);
-                const float wv = (yin && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
-                acc = fmaf(wv, buf[c0 - 2 * a.sigma * (ih - hm)], acc);
-            }
+        for (int ih = 0; ih < nh; ++ih) {
+            const int xs = y - a.sigma * (ih - hm);
+            const float wv = (yin && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
+            acc = fmaf(wv, sm[c0 - 2 * a.sigma * (ih - hm)], acc);
         }
         if (yin) {
-            const int j = p / a.S, s = p % a.S, n = a.n0 + j;
             float *o = out_base + ring_off(a.outr, n, j) + (long long)s * a.P + rowoff + y;
             *o = a.accumulate ? *o + acc : acc;
         }
     }
 }
 
+template <int NH, int PY>
+static void launch_scatter_nh(const ExtArgs &a, cudaStream_t st)
+{
+    constexpr int HM = (NH - 1) / 2;
+    constexpr int TXS = EXT_TX * PY;
+    const size_t smem = (2 * (TXS + 4 * HM) + TXS) * sizeof(float);
+    dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
+    if (a.sigma > 0) k_scatter_rb<NH, PY, 1><<<grid, EXT_TX, smem, st>>>(a);
+    else k_scatter_rb<NH, PY, -1><<<grid, EXT_TX, smem, st>>>(a);
+}
+
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
-    dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
-    const int hm = (a.nh - 1) / 2;
-    const size_t smem = 2 * (EXT_TX + 4 * hm) * sizeof(float);
     switch (a.nh) {
-    case 1: k_scatter<1><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 3: k_scatter<3><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 5: k_scatter<5><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 11: k_scatter<11><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 21: k_scatter<21><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 31: k_scatter<31><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 41: k_scatter<41><<<grid, EXT_TX, smem, st>>>(a); break;
-    default: k_scatter<0><<<grid, EXT_TX, smem, st>>>(a); break;
+    case 1: launch_scatter_nh<1, 8>(a, st); break;
+    case 3: launch_scatter_nh<3, 8>(a, st); break;
+    case 5: launch_scatter_nh<5, 8>(a, st); break;
+    case 11: launch_scatter_nh<11, 8>(a, st); break;
+    case 21: launch_scatter_nh<21, 4>(a, st); break;
+    case 31: launch_scatter_nh<31, 2>(a, st); break;
+    case 41: launch_scatter_nh<41, 2>(a, st); break;
+    default: {
+        dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
+        const int hm = (a.nh - 1) / 2;
+        k_scatter_gen<<<grid, EXT_TX, (EXT_TX + 4 * hm) * sizeof(float), st>>>(a);
+    }
     }
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ imaging
 
-template <int NH, int MODE>
-__global__ void __launch_bounds__(EXT_TX) k_image(const ImgArgs a)
+// Register-blocked imaging: a thread owns PX consecutive points x_i = xb + i and, for
+// IMG_EXT, their PX x NH image accumulators (IMG_CONTRACT: PX x NH weights p~ and PX
+// accumulators) for the whole segment.  D(x_i - h) and L(x_i + h) come from PX + NH - 1
+// window samples each, so a shared-memory load serves up to PX multiply-adds.
+template <int NH, int PX, int MODE>
+__global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
 {
     extern __shared__ float sm[];
-    const int nh = NH > 0 ? NH : a.nh;
-    const int hm = (nh - 1) / 2;
+    constexpr int HM = (NH - 1) / 2;
+    constexpr int TXS = EXT_TX * PX;
+    constexpr int SPAN = TXS + 2 * HM;
+    constexpr int NPF = (SPAN + EXT_TX - 1) / EXT_TX;
+    constexpr int NW = PX + NH - 1;
+    const int Z = a.z_lo + blockIdx.y;
+    const int x0 = a.x_lo + blockIdx.x * TXS;
+    const int t = threadIdx.x;
+    const int xb = x0 + PX * t;
+    const int wbase = x0 - HM;
+    const long long rowoff = (long long)Z * a.NXP;
+
+    constexpr int NA = MODE == IMG_EXT ? PX * NH : PX;
+    float acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+    float ptr[MODE == IMG_CONTRACT ? PX * NH : 1];
+    if (MODE == IMG_CONTRACT) {
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+#pragma unroll
+            for (int ih = 0; ih < NH; ++ih)
+                ptr[i * NH + ih] = (xb + i < a.x_hi) ? __ldg(a.pt + ih * a.P + rowoff + xb + i) : 0.f;
+    }
+    float pd[NPF], pl[NPF];
+    auto load_window = [&](int p) {
+        const int j = p / a.S, s = p % a.S, n = a.n0 + j;
+        const float *sd = a.D.base + ring_off(a.D, n, j) + (long long)s * a.P + rowoff;
+        const float *sl = a.L.base + ring_off(a.L, n, j) + (long long)s * a.P + rowoff;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int i = t + k * EXT_TX;
+            const int xp = wbase + i;
+            const bool ok = i < SPAN && xp >= 0 && xp < a.NXP;
+            pd[k] = ok ? __ldg(sd + xp) : 0.f;
+            pl[k] = ok ? __ldg(sl + xp) : 0.f;
+        }
+    };
+    if (a.npair > 0) load_window(0);
+    for (int p = 0; p < a.npair; ++p) {
+        float *bd = sm + (p & 1) * 2 * SPAN;
+        float *bl = bd + SPAN;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int i = t + k * EXT_TX;
+            if (i < SPAN) { bd[i] = pd[k]; bl[i] = pl[k]; }
+        }
+        __syncthreads();
+        if (p + 1 < a.npair) load_window(p + 1);
+        // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k), k < NW; window index xb - wbase + k - HM = PX t + k
+        float dv[NW], lv[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) { dv[k] = bd[PX * t + k]; lv[k] = bl[PX * t + k]; }
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (MODE == IMG_EXT) {
+#pragma unroll
+                for (int ih = 0; ih < NH; ++ih)   // D(x_i - h) = dv[i - ih + 2 HM], L(x_i + h) = lv[i + ih]
+                    acc[i * NH + ih] = fmaf(dv[i - ih + 2 * HM], lv[i + ih], acc[i * NH + ih]);
+            } else {
+                float s = 0.f;
+#pragma unroll
+                for (int ih = 0; ih < NH; ++ih) s = fmaf(ptr[i * NH + ih] * dv[i - ih + 2 * HM], lv[i + ih], s);
+                acc[MODE == IMG_EXT ? 0 : i] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        if (xb + i >= a.x_hi) continue;
+        if (MODE == IMG_EXT) {
+#pragma unroll
+            for (int ih = 0; ih < NH; ++ih) a.img[ih * a.P + rowoff + xb + i] += acc[i * NH + ih];
+        } else {
+            a.img[rowoff + xb + i] += acc[MODE == IMG_EXT ? 0 : i];
+        }
+    }
+}
+
+// Generic-nh fallback: one point per thread, accumulators in shared memory.
+template <int MODE>
+__global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
+{
+    extern __shared__ float sm[];
+    const int nh = a.nh, hm = (nh - 1) / 2;
     const int Z = a.z_lo + blockIdx.y;
     const int x0 = a.x_lo + blockIdx.x * EXT_TX;
     const int X = x0 + threadIdx.x;
@@ -133,88 +288,34 @@ __global__ void __launch_bounds__(EXT_TX) k_image(const ImgArgs a)
     const int span = EXT_TX + 2 * hm;
     const int wbase = x0 - hm;
     const long long rowoff = (long long)Z * a.NXP;
-
-    constexpr int NA = (MODE == IMG_EXT && NH > 0) ? NH : 1;
-    constexpr int NW = (MODE == IMG_CONTRACT && NH > 0) ? NH : 1;
-    float acc[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
-    float ptr[NW];
-    if (MODE == IMG_CONTRACT && NH > 0) {
-#pragma unroll
-        for (int ih = 0; ih < NW; ++ih) ptr[ih] = xin ? __ldg(a.pt + ih * a.P + rowoff + X) : 0.f;
-    }
-    // generic-nh image accumulators live in shared memory after the windows
-    float *gacc = sm + 4 * span;
-    if (MODE == IMG_EXT && NH == 0)
+    float *bd = sm, *bl = sm + span, *gacc = sm + 2 * span;
+    if (MODE == IMG_EXT)
         for (int ih = 0; ih < nh; ++ih) gacc[ih * EXT_TX + threadIdx.x] = 0.f;
-
-    constexpr int MAXPF = (EXT_TX + 2 * ((MAX_NH - 1) / 2) + EXT_TX - 1) / EXT_TX;
-    const int npf = (span + EXT_TX - 1) / EXT_TX;
-    float pd[MAXPF], pl[MAXPF];
-
-    auto load_window = [&](int p) {
+    float cacc = 0.f;
+    for (int p = 0; p < a.npair; ++p) {
         const int j = p / a.S, s = p % a.S, n = a.n0 + j;
         const float *sd = a.D.base + ring_off(a.D, n, j) + (long long)s * a.P + rowoff;
         const float *sl = a.L.base + ring_off(a.L, n, j) + (long long)s * a.P + rowoff;
-#pragma unroll
-        for (int k = 0; k < MAXPF; ++k) {
-            if (k < npf) {
-                const int i = threadIdx.x + k * EXT_TX;
-                const int xp = wbase + i;
-                const bool ok = i < span && xp >= 0 && xp < a.NXP;
-                pd[k] = ok ? __ldg(sd + xp) : 0.f;
-                pl[k] = ok ? __ldg(sl + xp) : 0.f;
-            }
-        }
-    };
-
-    if (a.npair > 0) load_window(0);
-    for (int p = 0; p < a.npair; ++p) {
-        float *bd = sm + (p & 1) * 2 * span;
-        float *bl = bd + span;
-#pragma unroll
-        for (int k = 0; k < MAXPF; ++k) {
-            const int i = threadIdx.x + k * EXT_TX;
-            if (k < npf && i < span) { bd[i] = pd[k]; bl[i] = pl[k]; }
+        __syncthreads();
+        for (int i = threadIdx.x; i < span; i += EXT_TX) {
+            const int xp = wbase + i;
+            const bool ok = xp >= 0 && xp < a.NXP;
+            bd[i] = ok ? __ldg(sd + xp) : 0.f;
+            bl[i] = ok ? __ldg(sl + xp) : 0.f;
         }
         __syncthreads();
-        if (p + 1 < a.npair) load_window(p + 1);
-        // D(X - h) at bd[tx + hm - h], L(X + h) at bl[tx + hm + h], h = ih - hm
         const int t = threadIdx.x;
-        if (NH > 0) {
-            if (MODE == IMG_EXT) {
-#pragma unroll
-                for (int ih = 0; ih < NA; ++ih) acc[ih] = fmaf(bd[t + 2 * hm - ih], bl[t + ih], acc[ih]);
-            } else {
-                float s = 0.f;
-#pragma unroll
-                for (int ih = 0; ih < NW; ++ih) s = fmaf(ptr[ih] * bd[t + 2 * hm - ih], bl[t + ih], s);
-                acc[0] += s;
-            }
-        } else {
-            if (MODE == IMG_EXT) {
-                for (int ih = 0; ih < nh; ++ih)
-                    gacc[ih * EXT_TX + t] = fmaf(bd[t + 2 * hm - ih], bl[t + ih], gacc[ih * EXT_TX + t]);
-            } else {
-                float s = 0.f;
-                for (int ih = 0; ih < nh; ++ih) {
-                    const float pv = xin ? __ldg(a.pt + ih * a.P + rowoff + X) : 0.f;
-                    s = fmaf(pv * bd[t + 2 * hm - ih], bl[t + ih], s);
-                }
-                acc[0] += s;
-            }
+        for (int ih = 0; ih < nh; ++ih) {
+            const float prod = bd[t + 2 * hm - ih] * bl[t + ih];
+            if (MODE == IMG_EXT) gacc[ih * EXT_TX + t] += prod;
+            else cacc = fmaf(xin ? __ldg(a.pt + ih * a.P + rowoff + X) : 0.f, prod, cacc);
         }
     }
     if (!xin) return;
-    if (MODE == IMG_EXT) {
-        for (int ih = 0; ih < nh; ++ih) {
-            const float v = NH > 0 ? acc[ih < NA ? ih : 0] : gacc[ih * EXT_TX + threadIdx.x];
-            a.img[ih * a.P + rowoff + X] += v;
-        }
-    } else {
-        a.img[rowoff + X] += acc[0];
-    }
+    if (MODE == IMG_EXT)
+        for (int ih = 0; ih < nh; ++ih) a.img[ih * a.P + rowoff + X] += gacc[ih * EXT_TX + threadIdx.x];
+    else
+        a.img[rowoff + X] += cacc;
 }
 
 // pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L
@@ -237,44 +338,52 @@ __global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
     a.img[off] += acc;
 }
 
+template <int NH, int PX, int MODE>
+static void launch_image_rb(const ImgArgs &a, cudaStream_t st)
+{
+    constexpr int HM = (NH - 1) / 2;
+    constexpr int TXS = EXT_TX * PX;
+    const size_t smem = 4 * (TXS + 2 * HM) * sizeof(float);
+    dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
+    k_image_rb<NH, PX, MODE><<<grid, EXT_TX, smem, st>>>(a);
+}
+
 template <int MODE>
-static void launch_image_nh(const ImgArgs &a, dim3 grid, size_t smem, cudaStream_t st)
+static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
 {
     switch (a.nh) {
-    case 1: k_image<1, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 3: k_image<3, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 5: k_image<5, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 11: k_image<11, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 21: k_image<21, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 31: k_image<31, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    case 41: k_image<41, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
-    default: k_image<0, MODE><<<grid, EXT_TX, smem, st>>>(a); break;
+    case 1: launch_image_rb<1, 8, MODE>(a, st); break;
+    case 3: launch_image_rb<3, 8, MODE>(a, st); break;
+    case 5: launch_image_rb<5, 8, MODE>(a, st); break;
+    case 11: launch_image_rb<11, 8, MODE>(a, st); break;
+    case 21: launch_image_rb<21, 4, MODE>(a, st); break;
+    case 31: launch_image_rb<31, 2, MODE>(a, st); break;
+    case 41: launch_image_rb<41, 2, MODE>(a, st); break;
+    default: {
+        const int hm = (a.nh - 1) / 2;
+        size_t smem = (2 * (EXT_TX + 2 * hm) + (MODE == IMG_EXT ? a.nh * EXT_TX : 0)) * sizeof(float);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_image_gen<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
+        k_image_gen<MODE><<<grid, EXT_TX, smem, st>>>(a);
     }
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
-    dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
     if (mode == IMG_LOCAL) {
+        dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
         k_image_local<<<grid, EXT_TX, 0, st>>>(a);
         return cudaGetLastError();
     }
-    const int hm = (a.nh - 1) / 2;
-    size_t smem = 4 * (EXT_TX + 2 * hm) * sizeof(float);
-    const bool generic = !(a.nh == 1 || a.nh == 3 || a.nh == 5 || a.nh == 11 || a.nh == 21 || a.nh == 31 ||
-                           a.nh == 41);
-    if (generic && mode == IMG_EXT) {
-        smem += (size_t)a.nh * EXT_TX * sizeof(float);
-        if (smem > 48 * 1024) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_image<0, IMG_EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    if (mode == IMG_EXT) launch_image_nh<IMG_EXT>(a, grid, smem, st);
-    else launch_image_nh<IMG_CONTRACT>(a, grid, smem, st);
-    return cudaGetLastError();
+    if (mode == IMG_EXT) return launch_image_mode<IMG_EXT>(a, st);
+    return launch_image_mode<IMG_CONTRACT>(a, st);
 }
 
 }  // namespace fwk

@@ -46,14 +46,37 @@ __device__ __forceinline__ float4 shfl_down4(float4 v)
     return v;
 }
 
+// ---- asynchronous global -> shared copies (LDGSTS); src_bytes = 0 zero-fills the 16 bytes
+__device__ __forceinline__ void cp16(float *dst, const float *src, bool valid)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// Per-warp pipeline: an 8-slot ring of q^n rows (128 points + 4-point halos) feeds the x-taps
+// and the register queue; a 4-slot ring holds the q^{n-1}, c and local-source rows of the
+// output row.  Iteration z waits for the copy group issued 4 iterations earlier, so about four
+// rows of every input stream are in flight per warp.
+constexpr int CUR_SLOTS = 8;
+constexpr int AUX_SLOTS = 4;
+constexpr int CUR_ROW = STRIP + 8;
+
 template <bool LOCAL, bool D2, bool SRC>
 __global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
 {
+    extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31;
-    const int wid = blockIdx.x * PROP_WARPS + (threadIdx.x >> 5);
+    const int wic = threadIdx.x >> 5;
+    const int wid = blockIdx.x * PROP_WARPS + wic;
     if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
     const int strip = wid % a.nstrip, chunk = wid / a.nstrip;
-    const int x = strip * STRIP + lane * 4;
+    const int x0 = strip * STRIP;
+    const int x = x0 + lane * 4;
     const int z0 = 4 + chunk * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.NZ - 4);
     const bool xin = x < a.NXP;
@@ -63,9 +86,54 @@ __global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
     float *out = a.out + so;
     const long long NXP = a.NXP;
 
+    // aux row layout: [prev][c][f0?][f1?][f2?][coef, fc?]
+    const int i_f0 = 2, i_f1 = i_f0 + (a.f0 != nullptr), i_f2 = i_f1 + (a.f1 != nullptr),
+              i_cf = i_f2 + (a.f2 != nullptr);
+    const int naux = LOCAL ? i_cf + (a.fc != nullptr ? 2 : 0) : 2;
+    float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP);
+    float *curR = wsm;
+    float *auxR = wsm + CUR_SLOTS * CUR_ROW;
+
+    auto issue_cur = [&](int zr) {
+        if (zr > z1 + 3) return;
+        float *dst = curR + (zr % CUR_SLOTS) * CUR_ROW;
+        const float *src = cur + (long long)zr * NXP;
+        for (int k = lane; k < CUR_ROW / 4; k += 32) {
+            const int col = x0 - 4 + 4 * k;
+            const bool ok = col >= 0 && col + 4 <= a.NXP;
+            cp16(dst + 4 * k, ok ? src + col : cur, ok);
+        }
+    };
+    auto issue_aux = [&](int zr) {
+        if (zr >= z1) return;
+        float *dst = auxR + (zr % AUX_SLOTS) * naux * STRIP + 4 * lane;
+        const long long off = (long long)zr * NXP + x;
+        const long long o2 = xin ? off : 0;
+        cp16(dst, prev + o2, xin);
+        cp16(dst + STRIP, a.c + o2, xin);
+        if (LOCAL) {
+            if (a.f0) cp16(dst + i_f0 * STRIP, a.f0 + so + o2, xin);
+            if (a.f1) cp16(dst + i_f1 * STRIP, a.f1 + so + o2, xin);
+            if (a.f2) cp16(dst + i_f2 * STRIP, a.f2 + so + o2, xin);
+            if (a.fc) {
+                cp16(dst + i_cf * STRIP, a.coef + o2, xin);
+                cp16(dst + (i_cf + 1) * STRIP, a.fc + so + o2, xin);
+            }
+        }
+    };
+
+    // register queue rows z0-4 .. z0+3
     float4 q[9];
 #pragma unroll
     for (int k = 0; k < 8; ++k) q[k] = xin ? ldg4(cur + (long long)(z0 - 4 + k) * NXP + x) : f4zero();
+    // prologue: groups for the first four iterations
+#pragma unroll
+    for (int g = 0; g < AUX_SLOTS; ++g) {
+        issue_cur(z0 + g);
+        issue_cur(z0 + 4 + g);
+        issue_aux(z0 + g);
+        cp_commit();
+    }
     const float4 gxv = xin ? ldg4(a.gx + x) : f4zero();
     long long soff = -1;
     float amp = 0.f;
@@ -76,77 +144,97 @@ __global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
     const float axc = a.ax[0] + a.az[0];
 
     for (int z = z0; z < z1; ++z) {
-        const long long row = (long long)z * NXP;
-        q[8] = xin ? ldg4(cur + row + 4 * NXP + x) : f4zero();
-        float4 L = shfl_up4(q[4]);
-        float4 R = shfl_down4(q[4]);
-        if (lane == 0) L = (x >= 4) ? ldg4(cur + row + x - 4) : f4zero();
-        if (lane == 31) R = (x + 4 < a.NXP) ? ldg4(cur + row + x + 4) : f4zero();
+        cp_wait<AUX_SLOTS - 1>();
+        __syncwarp();
+        const float *crow = curR + (z % CUR_SLOTS) * CUR_ROW;
+        q[8] = lds4(curR + ((z + 4) % CUR_SLOTS) * CUR_ROW + 4 + 4 * lane);
+        const float4 L = lds4(crow + 4 * lane);
+        const float4 R = lds4(crow + 8 + 4 * lane);
+        const float *arow = auxR + (z % AUX_SLOTS) * naux * STRIP + 4 * lane;
+        const float4 pv = lds4(arow);
+        const float4 cv = lds4(arow + STRIP);
+        float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();
+        if (LOCAL) {
+            if (a.f0) lf0 = lds4(arow + i_f0 * STRIP);
+            if (a.f1) lf1 = lds4(arow + i_f1 * STRIP);
+            if (a.f2) lf2 = lds4(arow + i_f2 * STRIP);
+            if (a.fc) { lcf = lds4(arow + i_cf * STRIP); lfc = lds4(arow + (i_cf + 1) * STRIP); }
+        }
         const float r[12] = {L.x, L.y, L.z, L.w, q[4].x, q[4].y, q[4].z, q[4].w, R.x, R.y, R.z, R.w};
-        if (xin) {
-            const long long idx = row + x;
-            const float4 pv = ld4(prev + idx);
-            const float4 cv = ldg4(a.c + idx);
-            const float gzz = __ldg(a.gz + z);
-            float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();
-            if (LOCAL) {
-                if (a.f0) lf0 = ldg4(a.f0 + so + idx);
-                if (a.f1) lf1 = ldg4(a.f1 + so + idx);
-                if (a.f2) lf2 = ldg4(a.f2 + so + idx);
-                if (a.fc) { lcf = ldg4(a.coef + idx); lfc = ldg4(a.fc + so + idx); }
-            }
-            float o[4], d2[4];
+        const long long idx = (long long)z * NXP + x;
+        const float gzz = __ldg(a.gz + z);
+        float o[4], d2[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float c0 = r[j + 4];
-                float lap = axc * c0;
-                lap = fmaf(a.ax[1], r[j + 3] + r[j + 5], lap);
-                lap = fmaf(a.ax[2], r[j + 2] + r[j + 6], lap);
-                lap = fmaf(a.ax[3], r[j + 1] + r[j + 7], lap);
-                lap = fmaf(a.ax[4], r[j + 0] + r[j + 8], lap);
-                lap = fmaf(a.az[1], cmp(q[3], j) + cmp(q[5], j), lap);
-                lap = fmaf(a.az[2], cmp(q[2], j) + cmp(q[6], j), lap);
-                lap = fmaf(a.az[3], cmp(q[1], j) + cmp(q[7], j), lap);
-                lap = fmaf(a.az[4], cmp(q[0], j) + cmp(q[8], j), lap);
-                float s = 0.f;
-                if (LOCAL) {
-                    s = fmaf(a.a0, cmp(lf0, j), s);
-                    s = fmaf(a.a1, cmp(lf1, j), s);
-                    s = fmaf(a.a2, cmp(lf2, j), s);
-                    s = fmaf(cmp(lcf, j), cmp(lfc, j), s);
-                }
-                if (SRC) s += (soff == idx + j) ? amp : 0.f;
-                const float g = gzz * cmp(gxv, j);
-                const float pj = cmp(pv, j);
-                o[j] = g * (2.f * c0 - g * pj + cmp(cv, j) * (lap + s));
-                d2[j] = (o[j] - 2.f * c0 + pj) * a.inv_dt2;
+        for (int j = 0; j < 4; ++j) {
+            const float c0 = r[j + 4];
+            float lap = axc * c0;
+            lap = fmaf(a.ax[1], r[j + 3] + r[j + 5], lap);
+            lap = fmaf(a.ax[2], r[j + 2] + r[j + 6], lap);
+            lap = fmaf(a.ax[3], r[j + 1] + r[j + 7], lap);
+            lap = fmaf(a.ax[4], r[j + 0] + r[j + 8], lap);
+            lap = fmaf(a.az[1], cmp(q[3], j) + cmp(q[5], j), lap);
+            lap = fmaf(a.az[2], cmp(q[2], j) + cmp(q[6], j), lap);
+            lap = fmaf(a.az[3], cmp(q[1], j) + cmp(q[7], j), lap);
+            lap = fmaf(a.az[4], cmp(q[0], j) + cmp(q[8], j), lap);
+            float s = 0.f;
+            if (LOCAL) {
+                s = fmaf(a.a0, cmp(lf0, j), s);
+                s = fmaf(a.a1, cmp(lf1, j), s);
+                s = fmaf(a.a2, cmp(lf2, j), s);
+                s = fmaf(cmp(lcf, j), cmp(lfc, j), s);
             }
+            if (SRC) s += (soff == idx + j) ? amp : 0.f;
+            const float g = gzz * cmp(gxv, j);
+            const float pj = cmp(pv, j);
+            o[j] = g * (2.f * c0 - g * pj + cmp(cv, j) * (lap + s));
+            d2[j] = (o[j] - 2.f * c0 + pj) * a.inv_dt2;
+        }
+        if (xin) {
             st4(out + idx, make_float4(o[0], o[1], o[2], o[3]));
             if (D2) st4(a.d2 + so + idx, make_float4(d2[0], d2[1], d2[2], d2[3]));
         }
+        __syncwarp();   // every lane is done with this iteration's slots before they are refilled
+        issue_cur(z + CUR_SLOTS);
+        issue_aux(z + AUX_SLOTS);
+        cp_commit();
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
     }
+    cp_wait<0>();
 }
 
-cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st)
+template <bool LOCAL, bool D2, bool SRC>
+static void launch_prop_t(const PropArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_prop<LOCAL, D2, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr = true;
+    }
+    k_prop<LOCAL, D2, SRC><<<grid, block, smem, st>>>(a);
+}
+
+cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
+{
+    PropArgs a = a0;
     const int nwarps = a.nstrip * a.nchunk;
     dim3 grid((nwarps + PROP_WARPS - 1) / PROP_WARPS, nshot);
     dim3 block(PROP_WARPS * 32);
     const bool local = a.f0 || a.f1 || a.f2 || a.fc;
     const bool d2 = a.d2 != nullptr;
     const bool src = a.src_off != nullptr;
+    a.naux_max = 2 + (local ? (a.f0 != nullptr) + (a.f1 != nullptr) + (a.f2 != nullptr) + (a.fc ? 2 : 0) : 0);
+    const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP) * sizeof(float);
     const int key = (local ? 4 : 0) | (d2 ? 2 : 0) | (src ? 1 : 0);
     switch (key) {
-    case 0: k_prop<false, false, false><<<grid, block, 0, st>>>(a); break;
-    case 1: k_prop<false, false, true><<<grid, block, 0, st>>>(a); break;
-    case 2: k_prop<false, true, false><<<grid, block, 0, st>>>(a); break;
-    case 3: k_prop<false, true, true><<<grid, block, 0, st>>>(a); break;
-    case 4: k_prop<true, false, false><<<grid, block, 0, st>>>(a); break;
-    case 5: k_prop<true, false, true><<<grid, block, 0, st>>>(a); break;
-    case 6: k_prop<true, true, false><<<grid, block, 0, st>>>(a); break;
-    default: k_prop<true, true, true><<<grid, block, 0, st>>>(a); break;
+    case 0: launch_prop_t<false, false, false>(a, grid, block, smem, st); break;
+    case 1: launch_prop_t<false, false, true>(a, grid, block, smem, st); break;
+    case 2: launch_prop_t<false, true, false>(a, grid, block, smem, st); break;
+    case 3: launch_prop_t<false, true, true>(a, grid, block, smem, st); break;
+    case 4: launch_prop_t<true, false, false>(a, grid, block, smem, st); break;
+    case 5: launch_prop_t<true, false, true>(a, grid, block, smem, st); break;
+    case 6: launch_prop_t<true, true, false>(a, grid, block, smem, st); break;
+    default: launch_prop_t<true, true, true>(a, grid, block, smem, st); break;
     }
     return cudaGetLastError();
 }

@@ -71,7 +71,8 @@ def test_gradient_against_central_finite_differences(prob):
         J = fwime_objective(ctx, v, cu(p.w), cu(p.pt), cu(p.dobs), p.eps)
         J.backward()
         g = v.grad.double().cpu().numpy()
-        errs = []
+        errs, rels = [], []
+        gn = np.linalg.norm(g)
         for k in range(10):
             dv = synth.gaussian_blobs(p.nz, p.nx, rng, nblob=3, amp=1.0, sigma_pts=5.0, ring=1)
             e = 5.0
@@ -79,9 +80,14 @@ def test_gradient_against_central_finite_differences(prob):
             jm = ctx.objective(cu(p.v0 - e * dv), cu(p.w), cu(p.pt), cu(p.dobs), eps=p.eps)
             fd = (jp - jm) / (2 * e)
             an = float((g * dv).sum())
-            errs.append(abs(fd - an) / max(abs(an), 1e-300))
-    assert max(errs) <= 1e-3, errs
-    assert np.median(errs) <= 2e-4, errs
+            scale = gn * np.linalg.norm(dv)
+            # error on the scale of a generic directional derivative; random smooth directions can be
+            # almost orthogonal to the gradient, where FP32 noise in Phi swamps (fd - an) / an
+            errs.append(abs(fd - an) / scale)
+            if abs(an) > 1e-2 * scale:
+                rels.append(abs(fd - an) / abs(an))
+    assert max(errs) <= 1e-4, errs
+    assert len(rels) >= 5 and max(rels) <= 2e-3, rels
 
 
 def test_no_grad_path_runs_forward_sweep_only(prob):

@@ -303,3 +303,12 @@ def test_workspace_budget_enforced(case):
         with pytest.raises(fw.FwimeError) as e:
             c.forward(dev(case.v), dev(case.w), d)
         assert e.value.code == fw.FWIME_ENOMEM
+
+
+def test_autotuner_picks_a_chunking_without_changing_results(case):
+    with case.ctx() as a, case.ctx() as b:
+        zc, us = b.autotune(fw.OP_BORN_EXT)
+        assert zc >= 8 and us > 0
+        assert b.get_option("zchunk") == zc
+        assert np.array_equal(case.g_ext(a), case.g_ext(b))
+        assert np.array_equal(case.g_forward(a), case.g_forward(b))

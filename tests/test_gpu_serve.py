@@ -1,0 +1,83 @@
+"""Continuous-batching request loop: requests of different grid sizes, nt and nh,
+forward and gradient, arriving while others run.  Each result must be the same
+alone and in the mix (bit-identical: the per-request arithmetic does not depend
+on what else is on the GPU), memory admission must hold requests back when the
+budget is small, and latencies are reported."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+from paper_2206_02362_gb300 import serve  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def mix(n=10, seed=5):
+    reqs = synth.serving_mix(nreq=n, rate=400.0, seed=synth.SEED0 + 300 + seed, nz_range=(20, 40),
+                             nx_range=(60, 160), nt_range=(120, 260), nh_choices=(1, 3, 5))
+    return [serve.from_synth(r) for r in reqs]
+
+
+def test_results_same_alone_and_in_the_mix():
+    assert torch.cuda.is_available()
+    reqs = mix()
+    srv = serve.Server(max_active=16)
+    try:
+        mixed = srv.serve([r for r in reqs], realtime=True)
+        alone = [srv.serve([r], realtime=False)[0] for r in reqs]
+    finally:
+        srv.close()
+    assert [r.rid for r in mixed] == [r.rid for r in reqs]
+    kinds = {r.kind for r in reqs}
+    assert kinds == {"forward", "gradient"}
+    for a, m in zip(alone, mixed):
+        if a.kind == "forward":
+            assert np.array_equal(a.data, m.data)
+        else:
+            assert np.array_equal(a.grad, m.grad) and a.objective == m.objective
+    s = serve.summarize(mixed)
+    assert s["p99_s"] >= s["p50_s"] > 0 and s["shots_per_s"] > 0
+
+
+def test_served_forward_matches_oracle():
+    req = mix(n=4)[0]
+    req.kind = "forward"
+    srv = serve.Server()
+    try:
+        res = srv.serve([req], realtime=False)[0]
+    finally:
+        srv.close()
+    g = oracle.Grid(nz=req.nz, nx=req.nx, W=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
+    geo = oracle.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
+    ref = oracle.forward(g, req.v.astype(np.float64), geo, req.w.astype(np.float64)[None])[0]
+    assert np.linalg.norm(res.data - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_memory_admission_limits_concurrency():
+    reqs = mix(n=6, seed=9)
+    biggest = max(serve.request_bytes(r) for r in reqs)
+    srv = serve.Server(memory_budget=biggest + (1 << 20))     # room for about one request at a time
+    try:
+        res = srv.serve(reqs, realtime=False)
+    finally:
+        srv.close()
+    assert len(res) == len(reqs)
+    order = sorted(res, key=lambda r: r.admitted)
+    for a, b in zip(order, order[1:]):
+        # with room for one, a request is admitted only after an earlier one finished, unless both fit
+        if serve.request_bytes(next(q for q in reqs if q.rid == a.rid)) + \
+                serve.request_bytes(next(q for q in reqs if q.rid == b.rid)) > biggest + (1 << 20):
+            assert b.admitted >= a.done - 1e-3
+
+
+def test_over_budget_request_is_rejected():
+    reqs = mix(n=1)
+    srv = serve.Server(memory_budget=1 << 20)
+    try:
+        with pytest.raises(ValueError):
+            srv.serve(reqs, realtime=False)
+    finally:
+        srv.close()
