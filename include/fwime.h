@@ -185,6 +185,28 @@ int fwime_profile_read(fwime_ctx *ctx, int kernel, double *ms, long long *launch
 
 int fwime_last_error_detail(fwime_ctx *ctx, char *buf, size_t n);
 
+/* ---- Allocation-free forward modelling (the paper has no counterpart) ----
+ * For callers that cannot call cudaMalloc (inside another allocator or memory
+ * pool, with device memory reserved up front, or on a thread that must not
+ * enter the driver's allocator): f(m) of fwime_forward with no context and no
+ * allocation.  Its scratch (padded model, sponge tables, offsets, two
+ * wavefields per shot) is one file-scope device array of
+ * FWIME_STATIC_SCRATCH_BYTES held by every GPU that loads the library until
+ * the process exits.  v[nz][nx], w[nshot][nt] and d[nshot][nt][nrec] are
+ * caller-owned DEVICE pointers; work is enqueued on cuda_stream (NULL = legacy
+ * default stream).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it: make that first call before
+ * any stream capture.  Every call shares the array and leaves its contents
+ * behind (wavefields are cleared at the start of a call); calls whose work
+ * overlaps on the GPU race on it and must be serialised by the caller.
+ * Returns FWIME_ENOMEM, with a message for fwime_static_last_error, when the
+ * problem needs more than FWIME_STATIC_SCRATCH_BYTES (see
+ * fwime_static_scratch_bytes), FWIME_EINVAL for a bad grid or geometry. */
+#define FWIME_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+size_t fwime_static_scratch_bytes(const fwime_grid *g, const fwime_geom *geo);
+int fwime_forward_static(const fwime_grid *g, const fwime_geom *geo, const float *v, const float *w,
+                         float *d, void *cuda_stream);
+int fwime_static_last_error(char *buf, size_t n);
 const char *fwime_strerror(int code);
 void fwime_destroy(fwime_ctx *ctx);
 
