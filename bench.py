@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--segment", type=int, default=0, help="checkpoint/ring segment length (0 = auto)")
     ap.add_argument("--no-grad", action="store_true", help="skip the FWIME-gradient batched-vs-plain section")
+    ap.add_argument("--no-tune", action="store_true", help="skip the stencil autotuner (automatic chunking)")
     ap.add_argument("--grad-shots", type=int, default=120)
     return ap.parse_args()
 
@@ -187,8 +188,9 @@ def gradient_section(fw, torch, dev, nshot):
     g = torch.zeros((wl.nz, wl.nx), device=dev)
     geom = fw.Geometry(wl.src_iz, wl.src_ix, wl.rec_iz, wl.rec_ix)
     out = {"workload": wl.name, "nshot": wl.nshot, "segment": "auto"}
-    with fw.Context(grid, geom) as c:
+    with fw.Context(grid, geom, profile=1) as c:
         c.gradient(v, w, pt, dobs, g, eps=1e-3)              # warm-up (workspace)
+        c.profile_read(reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         c.gradient(v, w, pt, dobs, g, eps=1e-3, sync=False)
@@ -198,6 +200,10 @@ def gradient_section(fw, torch, dev, nshot):
         out["batched_shots_per_s"] = wl.nshot / tb
         out["batched_seconds"] = tb
         out["launches"] = c.launches
+        prof = c.profile_read(reset=True)
+        kms = sum(p["ms"] for p in prof.values())
+        out["time_share"] = {k: round(p["ms"] / kms, 4) for k, p in prof.items()} if kms else None
+        out["family_gbs"] = {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items() if p["ms"] > 0}
     nps = 2
     geom2 = fw.Geometry(wl.src_iz[:nps], wl.src_ix[:nps], wl.rec_iz, wl.rec_ix)
     with fw.Context(grid, geom2, plain=1) as c:
@@ -273,6 +279,9 @@ def main():
     d = torch.zeros((wl.nshot, wl.nt, wl.nrec), device=dev)
     img = torch.zeros((wl.nh, wl.nz, wl.nx), device=dev)
     ctx = fw.Context(grid, geom, profile=1, segment=args.segment)
+    tuned = None
+    if not args.no_tune:
+        tuned = ctx.autotune(fw.OP_BORN_EXT_ADJ)    # stencil chunking measured on this batch (untimed)
     launches = [0]
 
     def step(c, vv, ww, pp, dd, ii):
@@ -342,6 +351,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Marmousi2-shaped stand-in)",
             "config": config(wl, args, world), "roofline": roofline, "gpu_launches": launches[0],
             "clocks": clocks, "shots_per_s": shots_per_s,
+            "autotune": {"stencil_rows_per_warp": tuned[0], "us_per_launch": tuned[1]} if tuned else None,
             "executed_gupd_s": value * 5.0 / 4.0}
 
     # plain path: one shot per launch, host-driven steps, same per-shot work

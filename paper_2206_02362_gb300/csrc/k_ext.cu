@@ -27,6 +27,27 @@ __device__ __forceinline__ long long ring_off(const RingRef &r, int n, int j)
     return (long long)slot * r.slot_stride;
 }
 
+// ---- asynchronous global -> shared copies (LDGSTS); src_bytes = 0 zero-fills the 16 bytes
+__device__ __forceinline__ void cpa16(float *dst, const float *src, bool valid)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Copies the row segment [wal, wal + 4 * nchunk) of `src` (16-byte chunks, zero outside [0, NXP))
+// into `dst`; wal is a multiple of 4.
+__device__ __forceinline__ void copy_window(float *dst, const float *src, int wal, int nchunk, int NXP)
+{
+    for (int k = threadIdx.x; k < nchunk; k += EXT_TX) {
+        const int col = wal + 4 * k;
+        const bool ok = col >= 0 && col + 4 <= NXP;
+        cpa16(dst + 4 * k, ok ? src + col : src, ok);
+    }
+}
+
 // ------------------------------------------------------------------ scatter
 
 // Register-blocked scatter: a thread owns PY outputs y_j = ybase + 2j (j < PY), so the D
@@ -34,89 +55,105 @@ __device__ __forceinline__ long long ring_off(const RingRef &r, int n, int j)
 // ybase + 2m: one shared-memory load per position serves up to PY multiply-adds.  The
 // thread's PY x NH weights stay in registers for the whole segment.  Outputs are staged
 // through shared memory and stored coalesced.
+// Vector loads from shared memory: VW = 4 (16-byte, LDS.128) or 2 (8-byte, LDS.64) consecutive floats.
+template <int VW, int N>
+__device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
+{
+    static_assert(N % VW == 0, "window length must be a multiple of the vector width");
+    if (VW == 4) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+            const float4 v = reinterpret_cast<const float4 *>(src)[k];
+            dst[4 * k] = v.x; dst[4 * k + 1] = v.y; dst[4 * k + 2] = v.z; dst[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const float2 v = reinterpret_cast<const float2 *>(src)[k];
+            dst[2 * k] = v.x; dst[2 * k + 1] = v.y;
+        }
+    }
+}
+
+// Register-blocked scatter: a thread owns PY consecutive outputs y_j = yb + j; the D samples
+// they need, y_j - 2 sigma h, lie in the 4 HM + PY consecutive positions [yb - 2HM, yb + PY + 2HM),
+// read with conflict-free vector loads (the column range is aligned so that the CTA's window
+// starts on a 16-byte boundary).  The PY x NH weights stay in registers for the whole segment.
+// The (step, shot) pairs stream through an EXT_STAGES-deep cp.async ring, one barrier per pair.
 template <int NH, int PY, int SIGMA>
 __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
+    float *sm = reinterpret_cast<float *>(sm4);
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PY;               // outputs per CTA
-    constexpr int SPAN = TXS + 4 * HM;             // D window
-    constexpr int NPF = (SPAN + EXT_TX - 1) / EXT_TX;
-    constexpr int NM = NH + PY - 1;
+    constexpr int SPAN = TXS + 4 * HM;             // D window, starting at y0 - 2 HM (16-byte aligned)
+    constexpr int NCH = (SPAN + 3) / 4;
+    constexpr int STG = 4 * NCH + 4;
+    constexpr int NS = EXT_STAGES;
+    constexpr int NM = PY + 4 * HM;                // samples per thread
+    constexpr int VW = (PY % 4 == 0) ? 4 : 2;
+    constexpr int NMV = (NM + VW - 1) / VW * VW;
     const int Z = a.z_lo + blockIdx.y;
     const int y0 = a.x_lo + blockIdx.x * TXS;
     const int t = threadIdx.x;
-    const int yb_off = 2 * PY * (t >> 1) + (t & 1);     // offset of this thread's first output
-    const int ybase = y0 + yb_off;
+    const int yb = y0 + PY * t;
     const long long rowoff = (long long)Z * a.NXP;
-    const int wbase = y0 - 2 * HM;
-    float *win = sm;                                   // 2 x SPAN
-    float *obuf = sm + 2 * SPAN;                       // TXS staged outputs
+    const int wal = y0 - 2 * HM;                   // multiple of 4 by the launcher's choice of x_lo
     float *out_base = const_cast<float *>(a.outr.base);
 
     float Wr[PY][NH];
 #pragma unroll
     for (int j = 0; j < PY; ++j) {
-        const int y = ybase + 2 * j;
+        const int y = yb + j;
 #pragma unroll
         for (int ih = 0; ih < NH; ++ih) {
             const int xs = y - SIGMA * (ih - HM);
             Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
         }
     }
-    float pre[NPF];
-    auto load_window = [&](int p) {
-        const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-        const float *src = a.in.base + ring_off(a.in, n, j) + (long long)s * a.P + rowoff;
-#pragma unroll
-        for (int k = 0; k < NPF; ++k) {
-            const int i = t + k * EXT_TX;
-            const int xp = wbase + i;
-            pre[k] = (i < SPAN && xp >= 0 && xp < a.NXP) ? __ldg(src + xp) : 0.f;
+    auto issue = [&](int p) {
+        if (p < a.npair) {
+            const int j = p / a.S, s = p % a.S, n = a.n0 + j;
+            const float *src = a.in.base + ring_off(a.in, n, j) + (long long)s * a.P + rowoff;
+            copy_window(sm + (p % NS) * STG, src, wal, NCH, a.NXP);
         }
+        cpa_commit();
     };
-    if (a.npair > 0) load_window(0);
+#pragma unroll
+    for (int q = 0; q < NS - 1; ++q) issue(q);
     for (int p = 0; p < a.npair; ++p) {
-        float *buf = win + (p & 1) * SPAN;
-#pragma unroll
-        for (int k = 0; k < NPF; ++k) {
-            const int i = t + k * EXT_TX;
-            if (i < SPAN) buf[i] = pre[k];
-        }
-        __syncthreads();
-        if (p + 1 < a.npair) load_window(p + 1);
-        // dv[m] = D(ybase + 2(m - HM)), m = 0 .. NM-1; window index (ybase - wbase) + 2(m - HM)
-        float dv[NM];
-        const float *bb = buf + yb_off;                 // = buf + (ybase - wbase) - 2 HM
-#pragma unroll
-        for (int m = 0; m < NM; ++m) dv[m] = bb[2 * m];
+        cpa_wait<NS - 2>();
+        __syncthreads();                 // pair p landed for every thread; pair p-1 fully consumed
+        issue(p + NS - 1);               // refills the stage of pair p-1
+        float dv[NMV];                   // dv[k] = D(yb - 2 HM + k): stage index PY t + k
+        lds_vec<VW>(dv, sm + (p % NS) * STG + PY * t);
         float acc[PY];
 #pragma unroll
         for (int j = 0; j < PY; ++j) {
-            float s = 0.f;
+            float sacc = 0.f;
 #pragma unroll
-            for (int ih = 0; ih < NH; ++ih) {
-                // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
-                constexpr int dummy = 0;
-                (void)dummy;
-                s = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], s);
-            }
-            acc[j] = s;
+            for (int ih = 0; ih < NH; ++ih)   // D(y_j - 2 SIGMA h) = dv[j - 2 SIGMA (ih - HM) + 2 HM]
+                sacc = fmaf(Wr[j][ih], dv[j - 2 * SIGMA * (ih - HM) + 2 * HM], sacc);
+            acc[j] = sacc;
         }
+        const int jj = p / a.S, s = p % a.S, n = a.n0 + jj;
+        float *o = out_base + ring_off(a.outr, n, jj) + (long long)s * a.P + rowoff + yb;
 #pragma unroll
-        for (int j = 0; j < PY; ++j) obuf[yb_off + 2 * j] = acc[j];
-        __syncthreads();
-        {
-            const int jj = p / a.S, s = p % a.S, n = a.n0 + jj;
-            float *o = out_base + ring_off(a.outr, n, jj) + (long long)s * a.P + rowoff;
-#pragma unroll
-            for (int k = 0; k < PY; ++k) {
-                const int i = t + k * EXT_TX;
-                const int y = y0 + i;
-                if (y < a.x_hi) o[y] = a.accumulate ? o[y] + obuf[i] : obuf[i];
+        for (int j = 0; j < PY; j += 2) {
+            if (yb + j + 1 < a.x_hi) {
+                float2 v = make_float2(acc[j], acc[j + 1]);
+                if (a.accumulate) {
+                    const float2 old = *reinterpret_cast<const float2 *>(o + j);
+                    v.x += old.x; v.y += old.y;
+                }
+                *reinterpret_cast<float2 *>(o + j) = v;
+            } else if (yb + j < a.x_hi) {
+                o[j] = a.accumulate ? o[j] + acc[j] : acc[j];
             }
         }
     }
+    cpa_wait<0>();
 }
 
 // Generic-nh fallback (weights re-read per pair): any odd nh up to MAX_NH.
@@ -160,8 +197,15 @@ static void launch_scatter_nh(const ExtArgs &a, cudaStream_t st)
 {
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PY;
-    const size_t smem = (2 * (TXS + 4 * HM) + TXS) * sizeof(float);
+    constexpr int STG = 4 * ((TXS + 4 * HM + 3) / 4) + 4;
+    const size_t smem = EXT_STAGES * STG * sizeof(float);
     dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
+    static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    if (!attr) {
+        cudaFuncSetAttribute(k_scatter_rb<NH, PY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_scatter_rb<NH, PY, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
     if (a.sigma > 0) k_scatter_rb<NH, PY, 1><<<grid, EXT_TX, smem, st>>>(a);
     else k_scatter_rb<NH, PY, -1><<<grid, EXT_TX, smem, st>>>(a);
 }
@@ -195,17 +239,23 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
 template <int NH, int PX, int MODE>
 __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
+    float *sm = reinterpret_cast<float *>(sm4);
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PX;
     constexpr int SPAN = TXS + 2 * HM;
-    constexpr int NPF = (SPAN + EXT_TX - 1) / EXT_TX;
+    constexpr int NCH = (SPAN + 3) / 4;
+    constexpr int WIN = 4 * NCH + 4;
+    constexpr int STG = 2 * WIN;                   // D window, then L window
+    constexpr int NS = EXT_STAGES;
     constexpr int NW = PX + NH - 1;
+    constexpr int VW = (PX % 4 == 0) ? 4 : 2;
+    constexpr int NWV = (NW + VW - 1) / VW * VW;
     const int Z = a.z_lo + blockIdx.y;
     const int x0 = a.x_lo + blockIdx.x * TXS;
     const int t = threadIdx.x;
     const int xb = x0 + PX * t;
-    const int wbase = x0 - HM;
+    const int wal = x0 - HM;                       // multiple of 4 by the launcher's choice of x_lo
     const long long rowoff = (long long)Z * a.NXP;
 
     constexpr int NA = MODE == IMG_EXT ? PX * NH : PX;
@@ -220,35 +270,26 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
             for (int ih = 0; ih < NH; ++ih)
                 ptr[i * NH + ih] = (xb + i < a.x_hi) ? __ldg(a.pt + ih * a.P + rowoff + xb + i) : 0.f;
     }
-    float pd[NPF], pl[NPF];
-    auto load_window = [&](int p) {
-        const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-        const float *sd = a.D.base + ring_off(a.D, n, j) + (long long)s * a.P + rowoff;
-        const float *sl = a.L.base + ring_off(a.L, n, j) + (long long)s * a.P + rowoff;
-#pragma unroll
-        for (int k = 0; k < NPF; ++k) {
-            const int i = t + k * EXT_TX;
-            const int xp = wbase + i;
-            const bool ok = i < SPAN && xp >= 0 && xp < a.NXP;
-            pd[k] = ok ? __ldg(sd + xp) : 0.f;
-            pl[k] = ok ? __ldg(sl + xp) : 0.f;
+    auto issue = [&](int p) {
+        if (p < a.npair) {
+            const int j = p / a.S, s = p % a.S, n = a.n0 + j;
+            float *st = sm + (p % NS) * STG;
+            copy_window(st, a.D.base + ring_off(a.D, n, j) + (long long)s * a.P + rowoff, wal, NCH, a.NXP);
+            copy_window(st + WIN, a.L.base + ring_off(a.L, n, j) + (long long)s * a.P + rowoff, wal, NCH, a.NXP);
         }
+        cpa_commit();
     };
-    if (a.npair > 0) load_window(0);
+#pragma unroll
+    for (int q = 0; q < NS - 1; ++q) issue(q);
     for (int p = 0; p < a.npair; ++p) {
-        float *bd = sm + (p & 1) * 2 * SPAN;
-        float *bl = bd + SPAN;
-#pragma unroll
-        for (int k = 0; k < NPF; ++k) {
-            const int i = t + k * EXT_TX;
-            if (i < SPAN) { bd[i] = pd[k]; bl[i] = pl[k]; }
-        }
+        cpa_wait<NS - 2>();
         __syncthreads();
-        if (p + 1 < a.npair) load_window(p + 1);
-        // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k), k < NW; window index xb - wbase + k - HM = PX t + k
-        float dv[NW], lv[NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) { dv[k] = bd[PX * t + k]; lv[k] = bl[PX * t + k]; }
+        issue(p + NS - 1);
+        // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k): stage index PX t + k (conflict-free vector loads)
+        const float *bd = sm + (p % NS) * STG + PX * t;
+        float dv[NWV], lv[NWV];
+        lds_vec<VW>(dv, bd);
+        lds_vec<VW>(lv, bd + WIN);
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             if (MODE == IMG_EXT) {
@@ -263,6 +304,7 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
             }
         }
     }
+    cpa_wait<0>();
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
         if (xb + i >= a.x_hi) continue;
@@ -318,24 +360,37 @@ __global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
         a.img[rowoff + X] += cacc;
 }
 
-// pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L
+// pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L.  Four pairs are
+// processed per iteration with independent partial sums, so each thread keeps its 8-16 loads of
+// four pairs in flight (coalesced: consecutive threads, consecutive points).
+__device__ __forceinline__ float local_term(const ImgArgs &a, int p, long long off)
+{
+    const int j = p / a.S, s = p % a.S, n = a.n0 + j;
+    const long long so = (long long)s * a.P + off;
+    const float l = __ldg(a.L.base + ring_off(a.L, n, j) + so);
+    float t = a.alpha * l;
+    if (a.M2.base) t += __ldg(a.M2.base + ring_off(a.M2, n, j) + so);
+    float r = __ldg(a.D.base + ring_off(a.D, n, j) + so) * t;
+    if (a.Ds.base) r = fmaf(__ldg(a.Ds.base + ring_off(a.Ds, n, j) + so), l, r);
+    return r;
+}
+
 __global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
 {
     const int Z = a.z_lo + blockIdx.y;
     const int X = a.x_lo + blockIdx.x * EXT_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const long long off = (long long)Z * a.NXP + X;
-    float acc = 0.f;
-    for (int p = 0; p < a.npair; ++p) {
-        const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-        const long long so = (long long)s * a.P + off;
-        const float l = __ldg(a.L.base + ring_off(a.L, n, j) + so);
-        float t = a.alpha * l;
-        if (a.M2.base) t += __ldg(a.M2.base + ring_off(a.M2, n, j) + so);
-        acc = fmaf(__ldg(a.D.base + ring_off(a.D, n, j) + so), t, acc);
-        if (a.Ds.base) acc = fmaf(__ldg(a.Ds.base + ring_off(a.Ds, n, j) + so), l, acc);
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    int p = 0;
+    for (; p + 4 <= a.npair; p += 4) {
+        acc0 += local_term(a, p, off);
+        acc1 += local_term(a, p + 1, off);
+        acc2 += local_term(a, p + 2, off);
+        acc3 += local_term(a, p + 3, off);
     }
-    a.img[off] += acc;
+    for (; p < a.npair; ++p) acc0 += local_term(a, p, off);
+    a.img[off] += (acc0 + acc1) + (acc2 + acc3);
 }
 
 template <int NH, int PX, int MODE>
@@ -343,8 +398,14 @@ static void launch_image_rb(const ImgArgs &a, cudaStream_t st)
 {
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PX;
-    const size_t smem = 4 * (TXS + 2 * HM) * sizeof(float);
+    constexpr int STG = 2 * (4 * ((TXS + 2 * HM + 3) / 4) + 4);
+    const size_t smem = EXT_STAGES * STG * sizeof(float);
     dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
+    static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    if (!attr) {
+        cudaFuncSetAttribute(k_image_rb<NH, PX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
     k_image_rb<NH, PX, MODE><<<grid, EXT_TX, smem, st>>>(a);
 }
 
