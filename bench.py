@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--segment", type=int, default=0, help="checkpoint/ring segment length (0 = auto)")
     ap.add_argument("--no-grad", action="store_true", help="skip the FWIME-gradient batched-vs-plain section")
     ap.add_argument("--no-tune", action="store_true", help="skip the stencil autotuner (automatic chunking)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix section")
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--grad-shots", type=int, default=120)
     return ap.parse_args()
 
@@ -173,6 +176,39 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def serving_section(nreq: int, rate: float):
+    """Serving mix: Poisson arrivals at `rate`/s of forward and FWIME-gradient shot requests on grids
+    200-600 x 400-2000 at 10 m, nt 2000-6000, nh in {1, 11, 31}, served with memory admission and
+    overlap (continuous batching); p50/p99 latency and shots/s.  The plain comparison serves the
+    same requests one at a time, one shot per launch."""
+    from paper_2206_02362_gb300 import serve
+    reqs = [serve.from_synth(r) for r in synth.serving_mix(nreq=nreq, rate=rate)]
+    srv = serve.Server(max_active=64)
+    try:
+        warm = [serve.from_synth(r) for r in synth.serving_mix(nreq=4, rate=rate, seed=synth.SEED0 + 99)]
+        srv.serve(warm, realtime=False)
+        t0 = time.perf_counter()
+        res = srv.serve(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    out = {"workload": f"serving mix, {nreq} requests, Poisson {rate}/s", **serve.summarize(res, wall)}
+    out["kinds"] = {k: sum(1 for r in reqs if r.kind == k) for k in ("forward", "gradient")}
+    # plain: the same requests alone, one after the other, one shot per launch (a subset, scaled)
+    sub = reqs[: max(4, nreq // 8)]
+    plain = serve.Server(max_active=1, plain=True)
+    try:
+        t0 = time.perf_counter()
+        plain.serve(sub, realtime=False)
+        tp = time.perf_counter() - t0
+    finally:
+        plain.close()
+    out["plain_shots_per_s"] = len(sub) / tp
+    out["plain_sample"] = f"first {len(sub)} requests served alone, one shot per launch"
+    out["served_vs_plain"] = out["shots_per_s"] / out["plain_shots_per_s"]
+    return out
+
 
 def gradient_section(fw, torch, dev, nshot):
     """FWIME gradient (objective + B* r + T* r, checkpointed) on the North-Sea-shaped workload,
@@ -403,6 +439,9 @@ def main():
     # FWIME gradient (Eqs. 7-9) on the North-Sea-shaped workload: batched vs plain shots/s
     if not args.no_grad and rank == 0:
         line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots)
+    # serving mix: continuous batching with memory admission, p50/p99 (Poisson arrivals)
+    if not args.no_serve and rank == 0:
+        line["serving"] = serving_section(args.serve_requests, args.serve_rate)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -1134,7 +1134,24 @@ int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_o
     TRY(zero(x, r.w.f[0], sizeof(float) * S * x->P));
     TRY(zero(x, r.w.f[1], sizeof(float) * S * x->P));
     const int rows = x->NZ - 8;
-    const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+    // candidates: a fixed ladder plus the chunkings that make the work a whole number of waves of
+    // resident warps (a partly filled last wave idles most of the GPU for its duration)
+    std::vector<int> cand = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+    int bps = 0, nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && prop_occupancy(&bps) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && bps > 0) {
+        const long long resident = (long long)bps * nsm * PROP_WARPS;
+        const long long per_chunk = (long long)((x->NXP + STRIP - 1) / STRIP) * S;   // warps per chunk row
+        for (int waves = 1; waves <= 12; ++waves) {
+            const long long nchunk = (waves * resident) / per_chunk;
+            if (nchunk < 1) continue;
+            const int zc = (int)((rows + nchunk - 1) / nchunk);
+            if (zc >= 4 && zc <= 512) cand.push_back(zc);
+        }
+    }
+    cudaGetLastError();
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1143,7 +1160,7 @@ int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_o
     int best = 0;
     float best_us = 1e30f;
     for (int zc : cand) {
-        if (zc > rows && zc != cand[0]) break;
+        if (zc > rows && zc != cand.front()) break;
         x->opt_zchunk = zc;
         init_run(x, r, S);
         for (int it = 0; it < 2; ++it) TRY(prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0));

@@ -100,6 +100,7 @@ struct ImgArgs {
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
+cudaError_t prop_occupancy(int *blocks_per_sm);
 cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st);
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);

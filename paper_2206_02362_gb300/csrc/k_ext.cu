@@ -27,6 +27,27 @@ __device__ __forceinline__ long long ring_off(const RingRef &r, int n, int j)
     return (long long)slot * r.slot_stride;
 }
 
+// Walks the (step, shot) pairs of a segment in order p = 0, 1, ... (shot fastest) without
+// integer division: pointer to the pair's field row in ring r.
+struct RingIt {
+    const float *base;
+    long long slot_stride, P;
+    int S, mod, s, slot;
+    __device__ __forceinline__ void init(const RingRef &r, int n0, int S_, long long P_, long long rowoff)
+    {
+        base = r.base + rowoff; slot_stride = r.slot_stride; P = P_; S = S_; mod = r.mod; s = 0;
+        slot = r.mod > 0 ? (n0 + r.shift) % r.mod : r.shift;
+    }
+    __device__ __forceinline__ const float *ptr() const { return base + (long long)slot * slot_stride + (long long)s * P; }
+    __device__ __forceinline__ void next()
+    {
+        if (++s == S) {
+            s = 0;
+            if (++slot == mod) slot = 0;   // mod == 0 (direct rings) never wraps
+        }
+    }
+};
+
 // ---- asynchronous global -> shared copies (LDGSTS); src_bytes = 0 zero-fills the 16 bytes
 __device__ __forceinline__ void cpa16(float *dst, const float *src, bool valid)
 {
@@ -100,7 +121,6 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
     const int yb = y0 + PY * t;
     const long long rowoff = (long long)Z * a.NXP;
     const int wal = y0 - 2 * HM;                   // multiple of 4 by the launcher's choice of x_lo
-    float *out_base = const_cast<float *>(a.outr.base);
 
     float Wr[PY][NH];
 #pragma unroll
@@ -112,12 +132,16 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
             Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
         }
     }
+    RingIt itin, itout;
+    itin.init(a.in, a.n0, a.S, a.P, rowoff);
+    itout.init(a.outr, a.n0, a.S, a.P, rowoff + yb);
+    int stage_in = 0, stage_c = 0;
     auto issue = [&](int p) {
         if (p < a.npair) {
-            const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-            const float *src = a.in.base + ring_off(a.in, n, j) + (long long)s * a.P + rowoff;
-            copy_window(sm + (p % NS) * STG, src, wal, NCH, a.NXP);
+            copy_window(sm + stage_in * STG, itin.ptr(), wal, NCH, a.NXP);
+            itin.next();
         }
+        stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
         cpa_commit();
     };
 #pragma unroll
@@ -126,8 +150,10 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
         cpa_wait<NS - 2>();
         __syncthreads();                 // pair p landed for every thread; pair p-1 fully consumed
         issue(p + NS - 1);               // refills the stage of pair p-1
+        const float *stg = sm + stage_c * STG;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
         float dv[NMV];                   // dv[k] = D(yb - 2 HM + k): stage index PY t + k
-        lds_vec<VW>(dv, sm + (p % NS) * STG + PY * t);
+        lds_vec<VW>(dv, stg + PY * t);
         float acc[PY];
 #pragma unroll
         for (int j = 0; j < PY; ++j) {
@@ -137,8 +163,8 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
                 sacc = fmaf(Wr[j][ih], dv[j - 2 * SIGMA * (ih - HM) + 2 * HM], sacc);
             acc[j] = sacc;
         }
-        const int jj = p / a.S, s = p % a.S, n = a.n0 + jj;
-        float *o = out_base + ring_off(a.outr, n, jj) + (long long)s * a.P + rowoff + yb;
+        float *o = const_cast<float *>(itout.ptr());
+        itout.next();
 #pragma unroll
         for (int j = 0; j < PY; j += 2) {
             if (yb + j + 1 < a.x_hi) {
@@ -270,13 +296,19 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
             for (int ih = 0; ih < NH; ++ih)
                 ptr[i * NH + ih] = (xb + i < a.x_hi) ? __ldg(a.pt + ih * a.P + rowoff + xb + i) : 0.f;
     }
+    RingIt itd, itl;
+    itd.init(a.D, a.n0, a.S, a.P, rowoff);
+    itl.init(a.L, a.n0, a.S, a.P, rowoff);
+    int stage_in = 0, stage_c = 0;
     auto issue = [&](int p) {
         if (p < a.npair) {
-            const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-            float *st = sm + (p % NS) * STG;
-            copy_window(st, a.D.base + ring_off(a.D, n, j) + (long long)s * a.P + rowoff, wal, NCH, a.NXP);
-            copy_window(st + WIN, a.L.base + ring_off(a.L, n, j) + (long long)s * a.P + rowoff, wal, NCH, a.NXP);
+            float *st = sm + stage_in * STG;
+            copy_window(st, itd.ptr(), wal, NCH, a.NXP);
+            copy_window(st + WIN, itl.ptr(), wal, NCH, a.NXP);
+            itd.next();
+            itl.next();
         }
+        stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
         cpa_commit();
     };
 #pragma unroll
@@ -286,7 +318,8 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
         __syncthreads();
         issue(p + NS - 1);
         // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k): stage index PX t + k (conflict-free vector loads)
-        const float *bd = sm + (p % NS) * STG + PX * t;
+        const float *bd = sm + stage_c * STG + PX * t;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
         float dv[NWV], lv[NWV];
         lds_vec<VW>(dv, bd);
         lds_vec<VW>(lv, bd + WIN);
@@ -360,37 +393,37 @@ __global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
         a.img[rowoff + X] += cacc;
 }
 
-// pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L.  Four pairs are
-// processed per iteration with independent partial sums, so each thread keeps its 8-16 loads of
-// four pairs in flight (coalesced: consecutive threads, consecutive points).
-__device__ __forceinline__ float local_term(const ImgArgs &a, int p, long long off)
-{
-    const int j = p / a.S, s = p % a.S, n = a.n0 + j;
-    const long long so = (long long)s * a.P + off;
-    const float l = __ldg(a.L.base + ring_off(a.L, n, j) + so);
-    float t = a.alpha * l;
-    if (a.M2.base) t += __ldg(a.M2.base + ring_off(a.M2, n, j) + so);
-    float r = __ldg(a.D.base + ring_off(a.D, n, j) + so) * t;
-    if (a.Ds.base) r = fmaf(__ldg(a.Ds.base + ring_off(a.Ds, n, j) + so), l, r);
-    return r;
-}
-
+// pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L, four independent
+// pairs in flight per thread (coalesced: consecutive threads, consecutive points).
 __global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
 {
     const int Z = a.z_lo + blockIdx.y;
     const int X = a.x_lo + blockIdx.x * EXT_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const long long off = (long long)Z * a.NXP + X;
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-    int p = 0;
-    for (; p + 4 <= a.npair; p += 4) {
-        acc0 += local_term(a, p, off);
-        acc1 += local_term(a, p + 1, off);
-        acc2 += local_term(a, p + 2, off);
-        acc3 += local_term(a, p + 3, off);
+    RingIt itd, itl, itm, its;
+    itd.init(a.D, a.n0, a.S, a.P, off);
+    itl.init(a.L, a.n0, a.S, a.P, off);
+    if (a.M2.base) itm.init(a.M2, a.n0, a.S, a.P, off);
+    if (a.Ds.base) its.init(a.Ds, a.n0, a.S, a.P, off);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p = 0; p < a.npair; p += 4) {
+        // four independent pairs per iteration: their loads are all in flight together
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (p + u < a.npair) {
+                const float l = __ldg(itl.ptr());
+                float tt = a.alpha * l;
+                if (a.M2.base) { tt += __ldg(itm.ptr()); itm.next(); }
+                float r = __ldg(itd.ptr()) * tt;
+                if (a.Ds.base) { r = fmaf(__ldg(its.ptr()), l, r); its.next(); }
+                acc[u] += r;
+                itd.next();
+                itl.next();
+            }
+        }
     }
-    for (; p < a.npair; ++p) acc0 += local_term(a, p, off);
-    a.img[off] += (acc0 + acc1) + (acc2 + acc3);
+    a.img[off] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 template <int NH, int PX, int MODE>

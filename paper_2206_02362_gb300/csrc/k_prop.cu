@@ -214,6 +214,14 @@ static void launch_prop_t(const PropArgs &a, dim3 grid, dim3 block, size_t smem,
     k_prop<LOCAL, D2, SRC><<<grid, block, smem, st>>>(a);
 }
 
+// Resident CTAs per SM of the plain (no local source) variant with the smem it launches with.
+cudaError_t prop_occupancy(int *blocks_per_sm)
+{
+    const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * 2 * STRIP) * sizeof(float);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_prop<false, false, false>, PROP_WARPS * 32,
+                                                         smem);
+}
+
 cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
 {
     PropArgs a = a0;

@@ -98,7 +98,8 @@ def request_bytes(req: ShotRequest) -> int:
 class Server:
     """Memory-admitted, stream-overlapped request loop on one CUDA device."""
 
-    def __init__(self, memory_budget: int | None = None, max_active: int = 64, workers: int = 8, device: int = 0):
+    def __init__(self, memory_budget: int | None = None, max_active: int = 64, workers: int = 8, device: int = 0,
+                 plain: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -108,6 +109,7 @@ class Server:
             memory_budget = int(0.8 * free)
         self.budget = memory_budget
         self.max_active = max_active
+        self.plain = plain              # one shot per launch, host-driven steps (the comparison path)
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
 
     # ---------------------------------------------------------------- one request
@@ -133,7 +135,7 @@ class Server:
                     .to(self.device, non_blocking=True)
                 t["g"] = torch.empty((req.nz, req.nx), device=self.device)
                 host_out = torch.empty((req.nz, req.nx), pin_memory=True)
-        ctx = fw.Context(grid, geom, stream=stream, shots_per_batch=1)
+        ctx = fw.Context(grid, geom, stream=stream, shots_per_batch=1, plain=int(self.plain))
         act = _Active(req, ctx, stream, torch.cuda.Event(), t, host_out, nbytes, now)
 
         def enqueue():
