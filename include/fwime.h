@@ -165,6 +165,17 @@ int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *
 int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                     const float *dobs, float eps, double *objective);
 
+/* f(m) for a group of contexts at once (Eq. 1; the Computational-aspects
+ * section's shots are independent): ctxs[i] has its own grid, record length
+ * and shots, with model v[i], wavelets w[i] and output d[i] (device pointers,
+ * layouts as fwime_forward).  Each time step of all members runs as ONE
+ * kernel launch (plus one recording launch): shots of uneven grid sizes share
+ * the launch, members drop out as their nt ends.  All members must use the
+ * same stream and fit all their shots in one batch (else FWIME_ENOMEM); at most
+ * 4096 members.  Results equal n separate fwime_forward calls bit for bit. */
+int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, const float *const *w,
+                        float *const *d);
+
 /* Autotuner of the stencil kernel's tiling: plans the workspace of operator
  * `op` (so the batch size is the one the operator will use), then times the
  * time-step kernel on that batch for candidate rows-per-warp chunkings with

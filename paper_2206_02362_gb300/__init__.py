@@ -34,7 +34,8 @@ KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_autotune", "fwime_sync",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_autotune", "fwime_forward_group",
+                 "fwime_sync",
                  "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
 
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    lib.fwime_forward_group.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp)]
     lib.fwime_sync.argtypes = [vp]
     lib.fwime_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ip]
@@ -172,6 +175,21 @@ def _ptr(t) -> int:
     if t.dtype.__str__() != "torch.float32" or not t.is_contiguous():
         raise TypeError("tensors must be contiguous float32")
     return t.data_ptr()
+
+
+def forward_group(contexts, vs, ws, ds, sync: bool = True):
+    """f(m) for several contexts (different grids, nt, shots) with one launch per time step for all
+    of them (fwime_forward_group).  vs/ws/ds: per-context device tensors as for Context.forward."""
+    n = len(contexts)
+    arr = lambda xs: (ctypes.c_void_p * n)(*xs)  # noqa: E731
+    rc = load().fwime_forward_group(arr([c._h.value for c in contexts]), n, arr([_ptr(t) for t in vs]),
+                                    arr([_ptr(t) for t in ws]), arr([_ptr(t) for t in ds]))
+    if rc != FWIME_OK:
+        raise FwimeError(rc, "fwime_forward_group", contexts[0].detail())
+    if sync:
+        for c in contexts:
+            c.sync()
+    return ds
 
 
 class Context:

@@ -41,8 +41,19 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every translation unit for sm_103a and link libfwime.so; returns its path."""
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, defines=(), build_dir=None) -> str:
+    """Compile every translation unit for sm_103a and link libfwime.so; returns its path.
+
+    `defines` (e.g. ["FWIME_PROP_AUX_SLOTS=6"]) and `build_dir` build a variant of the library
+    into another directory (tuning experiments); the default build is the one the package loads."""
+    global BUILD, LIB
+    if build_dir is not None:
+        saved = BUILD, LIB
+        BUILD, LIB = build_dir, os.path.join(build_dir, "libfwime.so")
+        try:
+            return build(force, verbose, ptxas_info, [f"-D{d}" for d in defines] if defines else ())
+        finally:
+            BUILD, LIB = saved
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, "fwime_kernels.cuh"), os.path.join(ROOT, "include", "fwime.h")]
     objs = []
@@ -52,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s, *headers, __file__]):
-            extra = ["-Xptxas", "-v"] if ptxas_info else []
+            extra = (["-Xptxas", "-v"] if ptxas_info else []) + list(defines)
             jobs.append([nvcc(), *_flags(extra), "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

@@ -311,7 +311,7 @@ static int plan(fwime_ctx *x, int op, WS &w)
     case FWIME_OP_TOMO: w.W = take(nh * P); w.W2 = take(nh * P); w.coef = take(P); break;
     case FWIME_OP_TOMO_ADJ:
     case FWIME_OP_GRADIENT:
-    case FWIME_OP_OBJECTIVE: w.W = take(nh * P); w.ptp = take(nh * P); w.acc1 = take(P); w.acc2 = take(P); break;
+    case FWIME_OP_OBJECTIVE: w.W = take(nh * P); w.acc1 = take(P); w.acc2 = take(nh * P); break;
     default: break;
     }
     const size_t SP = (size_t)w.S * P;
@@ -705,15 +705,11 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
     const long long SP = (long long)S * x->P;
     const size_t nhP = (size_t)x->g.nh * x->P;
     TRY(zero(x, r.w.W, sizeof(float) * nhP));
-    TRY(zero(x, r.w.ptp, sizeof(float) * nhP));
     TRY(zero(x, r.w.acc1, sizeof(float) * x->P));
-    TRY(zero(x, r.w.acc2, sizeof(float) * x->P));
+    TRY(zero(x, r.w.acc2, sizeof(float) * nhP));   // extended image of the residual, contracted with p~ at the end
     const double nm = (double)x->g.nz * x->g.nx;
     LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
            launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
-                              x->st));
-    LAUNCH(FWIME_K_OTHER, 8.0 * x->g.nh * nm,
-           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.ptp, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 2,
                               x->st));
     float *D0r = r.w.ring[0], *Er = r.w.ring[1], *Dsr = r.w.ring[2];
     float *Mu = r.w.ring[3], *Zr = r.w.ring[4], *Mu2 = r.w.ring[5];
@@ -799,14 +795,14 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
             }
             TRY(image(r, Sb, n0, kk, IMG_LOCAL, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(Mu2, SP, R, 1),
                       ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc1));
-            TRY(image(r, Sb, n0, kk, IMG_CONTRACT, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1),
-                      ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, r.w.ptp, r.w.acc2));
+            TRY(image(r, Sb, n0, kk, IMG_EXT, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1),
+                      ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, nullptr, r.w.acc2));
         }
     }
     if (!objective_only)
         LAUNCH(FWIME_K_OTHER, 20.0 * nm,
                launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
-                               accumulate, x->st));
+                               accumulate, x->st, pt, x->g.nh));
     if (grad) {
         LAUNCH(FWIME_K_OTHER, 4.0 * x->g.nh * nm,
                launch_dso(pt, x->g.nh, (long long)x->g.nz * x->g.nx, x->d_part, nred, x->st));
@@ -1118,6 +1114,83 @@ int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt
     x->user_J = objective;
     Call c{FWIME_OP_GRADIENT, v, w, pt, dobs, grad, 0, eps};
     return call_op(x, c, K_EXT, K_DATA, K_MODEL);
+}
+
+int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, const float *const *w, float *const *d)
+{
+    if (!ctxs || !v || !w || !d || n < 1 || n > 4096) return FWIME_EINVAL;
+    fwime_ctx *x = ctxs[0];
+    if (!x) return FWIME_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !v[i] || !w[i] || !d[i]) return fail(x, FWIME_EINVAL, "null member %d", i);
+        if (ctxs[i]->st != x->st) return fail(x, FWIME_EINVAL, "group members must share one stream");
+        if (ctxs[i]->capturing || ctxs[i]->opt_host_io) return fail(x, FWIME_EINVAL, "member %d: capture/host I/O", i);
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(x, FWIME_EINVAL, "member %d repeats member %d", i, j);
+    }
+    x->launches = 0;
+    std::vector<Run> runs(n);
+    for (int i = 0; i < n; ++i) {
+        fwime_ctx *m = ctxs[i];
+        TRY(plan(m, FWIME_OP_FORWARD, runs[i].w));
+        if (runs[i].w.S < m->nshot)
+            return fail(x, FWIME_ENOMEM, "group member %d: %d shots do not fit one batch", i, m->nshot);
+        init_run(m, runs[i], m->nshot);
+        TRY(prep_model(m, runs[i], v[i]));
+        TRY(zero(m, runs[i].w.f[0], sizeof(float) * m->nshot * m->P));
+        TRY(zero(m, runs[i].w.f[1], sizeof(float) * m->nshot * m->P));
+        TRY(zero(m, d[i], sizeof(float) * (size_t)m->nshot * m->g.nt * m->nrec));
+    }
+    // members in decreasing nt: the ones still running at a step are a prefix
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->g.nt > ctxs[b]->g.nt; });
+    std::vector<GroupMember> gm(n);
+    std::vector<GroupRec> gr(n);
+    std::vector<int> cta_end(n), rec_end(n);
+    int ctas = 0, recs = 0;
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        fwime_ctx *m = ctxs[i];
+        Run &r = runs[i];
+        PropArgs a = r.base;
+        a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx; a.d2 = nullptr;
+        a.src_off = m->d_src_off; a.src_amp = w[i]; a.src_stride = m->g.nt;
+        a.f0 = a.f1 = a.f2 = a.coef = a.fc = nullptr;
+        a.naux_max = 2;
+        gm[k].a[0] = a; gm[k].a[0].cur = r.w.f[0]; gm[k].a[0].prev = r.w.f[1]; gm[k].a[0].out = r.w.f[1];
+        gm[k].a[1] = a; gm[k].a[1].cur = r.w.f[1]; gm[k].a[1].prev = r.w.f[0]; gm[k].a[1].out = r.w.f[0];
+        gm[k].ctas_per_shot = (r.nstrip * r.nchunk + PROP_WARPS - 1) / PROP_WARPS;
+        gm[k].cta_begin = ctas;
+        ctas += gm[k].ctas_per_shot * m->nshot;
+        cta_end[k] = ctas;
+        gr[k].rec_off = m->d_rec_off; gr[k].fA = r.w.f[0]; gr[k].fB = r.w.f[1]; gr[k].d = d[i]; gr[k].P = m->P;
+        gr[k].nrec = m->nrec; gr[k].nshot = m->nshot; gr[k].nt = m->g.nt; gr[k].rec_begin = recs;
+        recs += m->nshot * m->nrec;
+        rec_end[k] = recs;
+    }
+    void *dev = nullptr;
+    const size_t bytes = n * (sizeof(GroupMember) + sizeof(GroupRec));
+    CK(cudaMallocAsync(&dev, bytes, x->st));
+    std::vector<char> host(bytes);
+    std::memcpy(host.data(), gm.data(), n * sizeof(GroupMember));
+    std::memcpy(host.data() + n * sizeof(GroupMember), gr.data(), n * sizeof(GroupRec));
+    CK(cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, x->st));
+    CK(cudaStreamSynchronize(x->st));   // the host copy of the tables is a local
+    const GroupMember *dgm = reinterpret_cast<const GroupMember *>(dev);
+    const GroupRec *dgr = reinterpret_cast<const GroupRec *>(reinterpret_cast<char *>(dev) + n * sizeof(GroupMember));
+    const int maxnt = ctxs[order[0]]->g.nt;
+    int nactive = n;
+    for (int step = 0; step + 1 < maxnt; ++step) {
+        while (nactive > 0 && ctxs[order[nactive - 1]]->g.nt - 1 <= step) --nactive;
+        double pts = 0.0;
+        for (int k = 0; k < nactive; ++k) pts += (double)ctxs[order[k]]->nshot * ctxs[order[k]]->NZ * ctxs[order[k]]->NX;
+        LAUNCH(FWIME_K_PROP, 12.0 * pts, launch_prop_group(dgm, nactive, cta_end[nactive - 1], dgr, 0, step, x->st, false));
+        LAUNCH(FWIME_K_POINTS, 8.0 * rec_end[nactive - 1],
+               launch_prop_group(dgm, nactive, 0, dgr, rec_end[nactive - 1], step, x->st, true));
+    }
+    CK(cudaFreeAsync(dev, x->st));
+    return FWIME_OK;
 }
 
 int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_out)

@@ -47,6 +47,20 @@ struct PropArgs {
     int naux_max;                  // rows per aux stage (set by launch_prop)
 };
 
+// grouped forward: one member = one shot batch on its own grid
+struct GroupMember {
+    PropArgs a[2];                 // even / odd steps (cur and prev swap); src_amp = wavelet base
+    int cta_begin;                 // first CTA of this member in the launch
+    int ctas_per_shot;
+};
+struct GroupRec {
+    const int *rec_off;
+    const float *fA, *fB;          // the member's two wavefield buffers
+    float *d;                      // data [nshot][nt][nrec]
+    long long P;
+    int nrec, nshot, nt, rec_begin;
+};
+
 struct PointsArgs {
     int nrec;
     long long P;
@@ -101,6 +115,8 @@ struct ImgArgs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
 cudaError_t prop_occupancy(int *blocks_per_sm);
+cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const GroupRec *g, int nrec_threads,
+                              int step, cudaStream_t st, bool record);
 cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st);
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
@@ -122,7 +138,7 @@ cudaError_t launch_ext_weights(const float *pt, const float *bpad, const float *
                                int nh, int nz, int nx, int o, int NXP, long long P, int mode, cudaStream_t st);
 cudaError_t launch_finalize(const float *acc1, const float *acc2, const float *bpad, const float *v, float *out,
                             int nplanes, int nz, int nx, int o, int NXP, long long P, int mode, int accumulate,
-                            cudaStream_t st);
+                            cudaStream_t st, const float *pt = nullptr, int nh = 0);
 cudaError_t launch_residual(const float *pred, const float *dobs, float *r, long long n, double *partials,
                             int nblocks, cudaStream_t st);
 cudaError_t launch_sum_partials(const double *partials, int n, double *out, int accumulate, double scale,

@@ -91,10 +91,11 @@ cudaError_t launch_ext_weights(const float *pt, const float *bpad, const float *
 }
 
 // Model-space outputs on the physical grid:
-//   mode 0: out[k] (=,+=) b * acc1[k]                        (B*, B~*: image planes k)
-//   mode 1: out    (=,+=) b * acc1 - 3 b / v * acc2         (T*, gradient)
+//   mode 0: out[k] (=,+=) b * acc1[k]                                  (B*, B~*: image planes k)
+//   mode 1: out    (=,+=) b * acc1 - 3 b / v * sum_h p~[h] acc2[h]        (T*, gradient; acc2 holds the
+//                                                                         extended image planes)
 __global__ void k_finalize(const float *acc1, const float *acc2, const float *bpad, const float *v, float *out, int nz,
-                           int nx, int o, int NXP, long long P, int mode, int accumulate)
+                           int nx, int o, int NXP, long long P, int mode, int accumulate, const float *pt, int nh)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x, iz = blockIdx.y, k = blockIdx.z;
     if (ix >= nx) return;
@@ -102,17 +103,21 @@ __global__ void k_finalize(const float *acc1, const float *acc2, const float *bp
     const long long p = (long long)(iz + o) * NXP + ix + o;
     const float b = bpad[p];
     float val = b * acc1[(long long)k * P + p];
-    if (mode == 1) val -= 3.f * b / v[pp] * acc2[p];
+    if (mode == 1) {
+        float c = 0.f;
+        for (int ih = 0; ih < nh; ++ih) c = fmaf(pt[(long long)ih * nz * nx + pp], acc2[(long long)ih * P + p], c);
+        val -= 3.f * b / v[pp] * c;
+    }
     float *dst = out + (long long)k * nz * nx + pp;
     *dst = accumulate ? *dst + val : val;
 }
 
 cudaError_t launch_finalize(const float *acc1, const float *acc2, const float *bpad, const float *v, float *out,
                             int nplanes, int nz, int nx, int o, int NXP, long long P, int mode, int accumulate,
-                            cudaStream_t st)
+                            cudaStream_t st, const float *pt, int nh)
 {
     dim3 grid((nx + 127) / 128, nz, nplanes);
-    k_finalize<<<grid, 128, 0, st>>>(acc1, acc2, bpad, v, out, nz, nx, o, NXP, P, mode, accumulate);
+    k_finalize<<<grid, 128, 0, st>>>(acc1, acc2, bpad, v, out, nz, nx, o, NXP, P, mode, accumulate, pt, nh);
     return cudaGetLastError();
 }
 

@@ -62,25 +62,33 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 // and the register queue; a 4-slot ring holds the q^{n-1}, c and local-source rows of the
 // output row.  Iteration z waits for the copy group issued 4 iterations earlier, so about four
 // rows of every input stream are in flight per warp.
-constexpr int CUR_SLOTS = 8;
-constexpr int AUX_SLOTS = 4;
+#ifndef FWIME_PROP_CUR_SLOTS
+#define FWIME_PROP_CUR_SLOTS 8
+#endif
+#ifndef FWIME_PROP_AUX_SLOTS
+#define FWIME_PROP_AUX_SLOTS 4
+#endif
+#ifndef FWIME_PROP_MIN_BLOCKS
+#define FWIME_PROP_MIN_BLOCKS 1
+#endif
+constexpr int CUR_SLOTS = FWIME_PROP_CUR_SLOTS;   // q^n rows in flight: the queue reads row z+4 of slots
+constexpr int AUX_SLOTS = FWIME_PROP_AUX_SLOTS;   // pipeline depth of the q^{n-1}, c, local-source rows
 constexpr int CUR_ROW = STRIP + 8;
+static_assert(CUR_SLOTS >= AUX_SLOTS + 4, "the q^n ring must hold rows z .. z+4+depth");
 
+// The time step of one warp's work item (strip, chunk) of shot `shot`; wsm is the warp's shared
+// memory (CUR_SLOTS x CUR_ROW + AUX_SLOTS x naux_max x STRIP floats).
 template <bool LOCAL, bool D2, bool SRC>
-__global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
+__device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, const int shot, float *wsm)
 {
-    extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31;
-    const int wic = threadIdx.x >> 5;
-    const int wid = blockIdx.x * PROP_WARPS + wic;
-    if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
     const int strip = wid % a.nstrip, chunk = wid / a.nstrip;
     const int x0 = strip * STRIP;
     const int x = x0 + lane * 4;
     const int z0 = 4 + chunk * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.NZ - 4);
     const bool xin = x < a.NXP;
-    const long long so = (long long)blockIdx.y * a.P;
+    const long long so = (long long)shot * a.P;
     const float *__restrict__ cur = a.cur + so;
     const float *prev = a.prev + so;
     float *out = a.out + so;
@@ -90,25 +98,25 @@ __global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
     const int i_f0 = 2, i_f1 = i_f0 + (a.f0 != nullptr), i_f2 = i_f1 + (a.f1 != nullptr),
               i_cf = i_f2 + (a.f2 != nullptr);
     const int naux = LOCAL ? i_cf + (a.fc != nullptr ? 2 : 0) : 2;
-    float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP);
     float *curR = wsm;
     float *auxR = wsm + CUR_SLOTS * CUR_ROW;
 
+    // copy bounds do not change along the march: hoisted out of the loop
+    const int c0 = x0 - 4 + 4 * lane, c1 = x0 - 4 + 4 * (lane + 32);
+    const bool ok0 = c0 >= 0 && c0 + 4 <= a.NXP;
+    const bool ok1 = lane < CUR_ROW / 4 - 32 && c1 + 4 <= a.NXP;
     auto issue_cur = [&](int zr) {
         if (zr > z1 + 3) return;
-        float *dst = curR + (zr % CUR_SLOTS) * CUR_ROW;
+        float *dst = curR + ((unsigned)zr % CUR_SLOTS) * CUR_ROW;
         const float *src = cur + (long long)zr * NXP;
-        for (int k = lane; k < CUR_ROW / 4; k += 32) {
-            const int col = x0 - 4 + 4 * k;
-            const bool ok = col >= 0 && col + 4 <= a.NXP;
-            cp16(dst + 4 * k, ok ? src + col : cur, ok);
-        }
+        cp16(dst + 4 * lane, ok0 ? src + c0 : cur, ok0);
+        if (lane < CUR_ROW / 4 - 32) cp16(dst + 4 * (lane + 32), ok1 ? src + c1 : cur, ok1);
     };
+    const long long o_x = xin ? x : 0;
     auto issue_aux = [&](int zr) {
         if (zr >= z1) return;
-        float *dst = auxR + (zr % AUX_SLOTS) * naux * STRIP + 4 * lane;
-        const long long off = (long long)zr * NXP + x;
-        const long long o2 = xin ? off : 0;
+        float *dst = auxR + ((unsigned)zr % AUX_SLOTS) * naux * STRIP + 4 * lane;
+        const long long o2 = xin ? (long long)zr * NXP + o_x : 0;
         cp16(dst, prev + o2, xin);
         cp16(dst + STRIP, a.c + o2, xin);
         if (LOCAL) {
@@ -126,81 +134,167 @@ __global__ void __launch_bounds__(PROP_WARPS * 32) k_prop(const PropArgs a)
     float4 q[9];
 #pragma unroll
     for (int k = 0; k < 8; ++k) q[k] = xin ? ldg4(cur + (long long)(z0 - 4 + k) * NXP + x) : f4zero();
-    // prologue: groups for the first four iterations
+    // prologue: one group per iteration of look-ahead (rows z0 .. z0+3 feed the first x-taps)
 #pragma unroll
     for (int g = 0; g < AUX_SLOTS; ++g) {
-        issue_cur(z0 + g);
+        if (g < 4) issue_cur(z0 + g);
         issue_cur(z0 + 4 + g);
         issue_aux(z0 + g);
         cp_commit();
     }
+    for (int g = AUX_SLOTS; g < 4; ++g) issue_cur(z0 + g);   // (only when the depth is below 4)
     const float4 gxv = xin ? ldg4(a.gx + x) : f4zero();
     long long soff = -1;
     float amp = 0.f;
     if (SRC) {
-        soff = a.src_off[blockIdx.y];
-        amp = a.src_amp[(long long)blockIdx.y * a.src_stride] * a.src_scale;
+        soff = a.src_off[shot];
+        amp = a.src_amp[(long long)shot * a.src_stride] * a.src_scale;
     }
     const float axc = a.ax[0] + a.az[0];
 
-    for (int z = z0; z < z1; ++z) {
-        cp_wait<AUX_SLOTS - 1>();
-        __syncwarp();
-        const float *crow = curR + (z % CUR_SLOTS) * CUR_ROW;
-        q[8] = lds4(curR + ((z + 4) % CUR_SLOTS) * CUR_ROW + 4 + 4 * lane);
-        const float4 L = lds4(crow + 4 * lane);
-        const float4 R = lds4(crow + 8 + 4 * lane);
-        const float *arow = auxR + (z % AUX_SLOTS) * naux * STRIP + 4 * lane;
-        const float4 pv = lds4(arow);
-        const float4 cv = lds4(arow + STRIP);
-        float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();
-        if (LOCAL) {
-            if (a.f0) lf0 = lds4(arow + i_f0 * STRIP);
-            if (a.f1) lf1 = lds4(arow + i_f1 * STRIP);
-            if (a.f2) lf2 = lds4(arow + i_f2 * STRIP);
-            if (a.fc) { lcf = lds4(arow + i_cf * STRIP); lfc = lds4(arow + (i_cf + 1) * STRIP); }
-        }
-        const float r[12] = {L.x, L.y, L.z, L.w, q[4].x, q[4].y, q[4].z, q[4].w, R.x, R.y, R.z, R.w};
-        const long long idx = (long long)z * NXP + x;
-        const float gzz = __ldg(a.gz + z);
-        float o[4], d2[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float c0 = r[j + 4];
-            float lap = axc * c0;
-            lap = fmaf(a.ax[1], r[j + 3] + r[j + 5], lap);
-            lap = fmaf(a.ax[2], r[j + 2] + r[j + 6], lap);
-            lap = fmaf(a.ax[3], r[j + 1] + r[j + 7], lap);
-            lap = fmaf(a.ax[4], r[j + 0] + r[j + 8], lap);
-            lap = fmaf(a.az[1], cmp(q[3], j) + cmp(q[5], j), lap);
-            lap = fmaf(a.az[2], cmp(q[2], j) + cmp(q[6], j), lap);
-            lap = fmaf(a.az[3], cmp(q[1], j) + cmp(q[7], j), lap);
-            lap = fmaf(a.az[4], cmp(q[0], j) + cmp(q[8], j), lap);
-            float s = 0.f;
-            if (LOCAL) {
-                s = fmaf(a.a0, cmp(lf0, j), s);
-                s = fmaf(a.a1, cmp(lf1, j), s);
-                s = fmaf(a.a2, cmp(lf2, j), s);
-                s = fmaf(cmp(lcf, j), cmp(lfc, j), s);
-            }
-            if (SRC) s += (soff == idx + j) ? amp : 0.f;
-            const float g = gzz * cmp(gxv, j);
-            const float pj = cmp(pv, j);
-            o[j] = g * (2.f * c0 - g * pj + cmp(cv, j) * (lap + s));
-            d2[j] = (o[j] - 2.f * c0 + pj) * a.inv_dt2;
-        }
-        if (xin) {
-            st4(out + idx, make_float4(o[0], o[1], o[2], o[3]));
-            if (D2) st4(a.d2 + so + idx, make_float4(d2[0], d2[1], d2[2], d2[3]));
-        }
-        __syncwarp();   // every lane is done with this iteration's slots before they are refilled
-        issue_cur(z + CUR_SLOTS);
-        issue_aux(z + AUX_SLOTS);
-        cp_commit();
+    // One output row zz; the queue's logical row k (zz-4+k) lives in q[(k + R) % 9], so nine
+    // consecutive rows rotate the queue through the registers without moving any of them.
+#define FWIME_PROP_ROW(R)                                                                                    \
+    {                                                                                                        \
+        const int zz = z + (R);                                                                              \
+        cp_wait<AUX_SLOTS - 1>();                                                                            \
+        __syncwarp();                                                                                        \
+        const float *crow = curR + ((unsigned)zz % CUR_SLOTS) * CUR_ROW;                                     \
+        q[(8 + (R)) % 9] = lds4(curR + ((unsigned)(zz + 4) % CUR_SLOTS) * CUR_ROW + 4 + 4 * lane);           \
+        const float4 L = lds4(crow + 4 * lane);                                                              \
+        const float4 Rr = lds4(crow + 8 + 4 * lane);                                                         \
+        const float *arow = auxR + ((unsigned)zz % AUX_SLOTS) * naux * STRIP + 4 * lane;                     \
+        const float4 pv = lds4(arow);                                                                        \
+        const float4 cv = lds4(arow + STRIP);                                                                \
+        float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();               \
+        if (LOCAL) {                                                                                         \
+            if (a.f0) lf0 = lds4(arow + i_f0 * STRIP);                                                       \
+            if (a.f1) lf1 = lds4(arow + i_f1 * STRIP);                                                       \
+            if (a.f2) lf2 = lds4(arow + i_f2 * STRIP);                                                       \
+            if (a.fc) { lcf = lds4(arow + i_cf * STRIP); lfc = lds4(arow + (i_cf + 1) * STRIP); }            \
+        }                                                                                                    \
+        const float4 Q0 = q[(0 + (R)) % 9], Q1 = q[(1 + (R)) % 9], Q2 = q[(2 + (R)) % 9],                    \
+                     Q3 = q[(3 + (R)) % 9], Q4 = q[(4 + (R)) % 9], Q5 = q[(5 + (R)) % 9],                    \
+                     Q6 = q[(6 + (R)) % 9], Q7 = q[(7 + (R)) % 9], Q8 = q[(8 + (R)) % 9];                    \
+        const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};           \
+        const long long idx = (long long)zz * NXP + x;                                                       \
+        const float gzz = __ldg(a.gz + zz);                                                                  \
+        float o[4], d2[4];                                                                                   \
+        _Pragma("unroll") for (int j = 0; j < 4; ++j) {                                                      \
+            const float c0v = rr[j + 4];                                                                     \
+            float lap = axc * c0v;                                                                           \
+            lap = fmaf(a.ax[1], rr[j + 3] + rr[j + 5], lap);                                                 \
+            lap = fmaf(a.ax[2], rr[j + 2] + rr[j + 6], lap);                                                 \
+            lap = fmaf(a.ax[3], rr[j + 1] + rr[j + 7], lap);                                                 \
+            lap = fmaf(a.ax[4], rr[j + 0] + rr[j + 8], lap);                                                 \
+            lap = fmaf(a.az[1], cmp(Q3, j) + cmp(Q5, j), lap);                                               \
+            lap = fmaf(a.az[2], cmp(Q2, j) + cmp(Q6, j), lap);                                               \
+            lap = fmaf(a.az[3], cmp(Q1, j) + cmp(Q7, j), lap);                                               \
+            lap = fmaf(a.az[4], cmp(Q0, j) + cmp(Q8, j), lap);                                               \
+            float sv = 0.f;                                                                                  \
+            if (LOCAL) {                                                                                     \
+                sv = fmaf(a.a0, cmp(lf0, j), sv);                                                            \
+                sv = fmaf(a.a1, cmp(lf1, j), sv);                                                            \
+                sv = fmaf(a.a2, cmp(lf2, j), sv);                                                            \
+                sv = fmaf(cmp(lcf, j), cmp(lfc, j), sv);                                                     \
+            }                                                                                                \
+            if (SRC) sv += (soff == idx + j) ? amp : 0.f;                                                    \
+            const float g = gzz * cmp(gxv, j);                                                               \
+            const float pj = cmp(pv, j);                                                                     \
+            o[j] = g * (2.f * c0v - g * pj + cmp(cv, j) * (lap + sv));                                       \
+            d2[j] = (o[j] - 2.f * c0v + pj) * a.inv_dt2;                                                     \
+        }                                                                                                    \
+        if (xin) {                                                                                           \
+            st4(out + idx, make_float4(o[0], o[1], o[2], o[3]));                                             \
+            if (D2) st4(a.d2 + so + idx, make_float4(d2[0], d2[1], d2[2], d2[3]));                           \
+        }                                                                                                    \
+        __syncwarp(); /* every lane is done with this row's slots before they are refilled */              \
+        issue_cur(zz + 4 + AUX_SLOTS);                                                                       \
+        issue_aux(zz + AUX_SLOTS);                                                                           \
+        cp_commit();                                                                                         \
+    }
+
+    int z = z0;
+    for (; z + 9 <= z1; z += 9) {
+        FWIME_PROP_ROW(0) FWIME_PROP_ROW(1) FWIME_PROP_ROW(2) FWIME_PROP_ROW(3) FWIME_PROP_ROW(4)
+        FWIME_PROP_ROW(5) FWIME_PROP_ROW(6) FWIME_PROP_ROW(7) FWIME_PROP_ROW(8)
+    }
+    for (; z < z1; ++z) {   // the last (z1 - z0) mod 9 rows: shift the queue by one register per row
+        FWIME_PROP_ROW(0)
 #pragma unroll
         for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
     }
+#undef FWIME_PROP_ROW
     cp_wait<0>();
+}
+
+template <bool LOCAL, bool D2, bool SRC>
+__global__ void __launch_bounds__(PROP_WARPS * 32, LOCAL ? FWIME_PROP_MIN_BLOCKS : 4) k_prop(const PropArgs a)
+{
+    extern __shared__ float4 smem4[];
+    const int wic = threadIdx.x >> 5;
+    const int wid = blockIdx.x * PROP_WARPS + wic;
+    if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
+    float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP);
+    prop_body<LOCAL, D2, SRC>(a, wid, blockIdx.y, wsm);
+}
+
+// ------------------------------------------------------------- grouped forward
+// One launch advances one time step of every member of a group of shot batches on grids of
+// different sizes (and different record lengths): CTA b belongs to the member whose cta_begin is
+// the largest <= b.  Members are sorted by decreasing nt, so the members still running at a step
+// are a prefix and the grid covers exactly their CTAs.
+__global__ void __launch_bounds__(PROP_WARPS * 32, 4) k_prop_group(const GroupMember *__restrict__ m, int nactive, int step)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ PropArgs sa;
+    int lo = 0, hi = nactive - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m[mid].cta_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    if (threadIdx.x == 0) {
+        sa = m[lo].a[step & 1];
+        sa.src_amp += step;
+    }
+    __syncthreads();
+    const int local = (int)blockIdx.x - m[lo].cta_begin;
+    const int cps = m[lo].ctas_per_shot;
+    const int shot = local / cps;
+    const int wic = threadIdx.x >> 5;
+    const int wid = (local - shot * cps) * PROP_WARPS + wic;
+    if (wid >= sa.nstrip * sa.nchunk) return;   // warp-uniform
+    float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * 2 * STRIP);
+    prop_body<false, false, true>(sa, wid, shot, wsm);
+}
+
+// after step n the new field q^{n+1} of a member is in buffer B for even n, A for odd n
+__global__ void k_points_group(const GroupRec *__restrict__ g, int nactive, int step)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int lo = 0, hi = nactive - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g[mid].rec_begin <= i) lo = mid; else hi = mid - 1;
+    }
+    const GroupRec &r = g[lo];
+    const int local = i - r.rec_begin;
+    if (local >= r.nshot * r.nrec) return;
+    const int s = local / r.nrec, k = local - s * r.nrec;
+    const float *f = (step & 1) ? r.fA : r.fB;
+    r.d[(long long)s * r.nt * r.nrec + (long long)(step + 1) * r.nrec + k] = f[(long long)s * r.P + r.rec_off[k]];
+}
+
+cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const GroupRec *g, int nrec_threads,
+                              int step, cudaStream_t st, bool record)
+{
+    const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * 2 * STRIP) * sizeof(float);
+    if (!record) {
+        k_prop_group<<<ctas, PROP_WARPS * 32, smem, st>>>(m, nactive, step);
+    } else {
+        k_points_group<<<(nrec_threads + 127) / 128, 128, 0, st>>>(g, nactive, step);
+    }
+    return cudaGetLastError();
 }
 
 template <bool LOCAL, bool D2, bool SRC>

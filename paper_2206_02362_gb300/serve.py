@@ -99,7 +99,7 @@ class Server:
     """Memory-admitted, stream-overlapped request loop on one CUDA device."""
 
     def __init__(self, memory_budget: int | None = None, max_active: int = 64, workers: int = 8, device: int = 0,
-                 plain: bool = False):
+                 plain: bool = False, group_forward: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -110,6 +110,9 @@ class Server:
         self.budget = memory_budget
         self.max_active = max_active
         self.plain = plain              # one shot per launch, host-driven steps (the comparison path)
+        # forward requests admitted together run as one group: one launch per time step for all of
+        # them, whatever their grid sizes and record lengths (fwime_forward_group)
+        self.group_forward = group_forward and not plain
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
 
     # ---------------------------------------------------------------- one request
@@ -151,6 +154,38 @@ class Server:
         act.future = self.pool.submit(enqueue)
         return act
 
+    def _admit_forward_group(self, reqs: list, sizes: dict, now: float) -> list:
+        import paper_2206_02362_gb300 as fw
+        torch = self.torch
+        stream = torch.cuda.Stream(device=self.device)
+        acts, ctxs, vs, ws, ds = [], [], [], [], []
+        event = torch.cuda.Event()
+        with torch.cuda.stream(stream):
+            for req in reqs:
+                grid = fw.Grid(nz=req.nz, nx=req.nx, sponge=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
+                geom = fw.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
+                t = {"v": torch.from_numpy(np.ascontiguousarray(req.v, dtype=np.float32)).pin_memory()
+                     .to(self.device, non_blocking=True),
+                     "w": torch.from_numpy(np.ascontiguousarray(req.w, dtype=np.float32)[None]).pin_memory()
+                     .to(self.device, non_blocking=True),
+                     "d": torch.empty((1, req.nt, len(req.rec_iz)), device=self.device)}
+                host_out = torch.empty((req.nt, len(req.rec_iz)), pin_memory=True)
+                ctx = fw.Context(grid, geom, stream=stream, shots_per_batch=1)
+                acts.append(_Active(req, ctx, stream, event, t, host_out, sizes[req.rid], now))
+                ctxs.append(ctx); vs.append(t["v"]); ws.append(t["w"]); ds.append(t["d"])
+
+        def enqueue():
+            with torch.cuda.stream(stream):
+                fw.forward_group(ctxs, vs, ws, ds, sync=False)
+                for a in acts:
+                    a.host_out.copy_(a.tensors["d"][0], non_blocking=True)
+                event.record(stream)
+
+        fut = self.pool.submit(enqueue)
+        for a in acts:
+            a.future = fut
+        return acts
+
     def _finish(self, act: _Active, now: float) -> ShotResult:
         act.ctx.sync()                       # already complete; reads the status word and the objective
         r = ShotResult(act.req.rid, act.req.kind, act.req.arrival, act.admitted, now)
@@ -183,10 +218,19 @@ class Server:
                     req.arrival = now
                 queue.append(req)
             # admission: FIFO, as memory and slots free up
-            while queue and len(active) < self.max_active and used + sizes[queue[0].rid] <= self.budget:
+            admitted = []
+            while queue and len(active) + len(admitted) < self.max_active and \
+                    used + sizes[queue[0].rid] <= self.budget:
                 req = queue.popleft()
-                active.append(self._admit(req, sizes[req.rid], time.perf_counter() - t0))
+                admitted.append(req)
                 used += sizes[req.rid]
+            fwd = [r for r in admitted if r.kind == "forward"] if self.group_forward else []
+            grouped = {r.rid for r in fwd} if len(fwd) > 1 else set()
+            if grouped:
+                active.extend(self._admit_forward_group(fwd, sizes, time.perf_counter() - t0))
+            for req in admitted:
+                if req.rid not in grouped:
+                    active.append(self._admit(req, sizes[req.rid], time.perf_counter() - t0))
             # completion
             still = []
             for act in active:

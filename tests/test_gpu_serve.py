@@ -28,8 +28,14 @@ def test_results_same_alone_and_in_the_mix():
     try:
         mixed = srv.serve([r for r in reqs], realtime=True)
         alone = [srv.serve([r], realtime=False)[0] for r in reqs]
+        burst = srv.serve([r for r in reqs], realtime=False)   # all admitted at once: forwards grouped
     finally:
         srv.close()
+    for a, b in zip(alone, burst):
+        if a.kind == "forward":
+            assert np.array_equal(a.data, b.data)
+        else:
+            assert np.array_equal(a.grad, b.grad) and a.objective == b.objective
     assert [r.rid for r in mixed] == [r.rid for r in reqs]
     kinds = {r.kind for r in reqs}
     assert kinds == {"forward", "gradient"}
