@@ -144,27 +144,17 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
         stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
         cpa_commit();
     };
-#pragma unroll
-    for (int q = 0; q < NS - 1; ++q) issue(q);
-    for (int p = 0; p < a.npair; ++p) {
-        cpa_wait<NS - 2>();
-        __syncthreads();                 // pair p landed for every thread; pair p-1 fully consumed
-        issue(p + NS - 1);               // refills the stage of pair p-1
-        const float *stg = sm + stage_c * STG;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+    auto compute = [&](const float *stg, float *o) {
         float dv[NMV];                   // dv[k] = D(yb - 2 HM + k): stage index PY t + k
         lds_vec<VW>(dv, stg + PY * t);
         float acc[PY];
 #pragma unroll
-        for (int j = 0; j < PY; ++j) {
-            float sacc = 0.f;
+        for (int j = 0; j < PY; ++j) acc[j] = 0.f;
 #pragma unroll
-            for (int ih = 0; ih < NH; ++ih)   // D(y_j - 2 SIGMA h) = dv[j - 2 SIGMA (ih - HM) + 2 HM]
-                sacc = fmaf(Wr[j][ih], dv[j - 2 * SIGMA * (ih - HM) + 2 * HM], sacc);
-            acc[j] = sacc;
-        }
-        float *o = const_cast<float *>(itout.ptr());
-        itout.next();
+        for (int ih = 0; ih < NH; ++ih)      // offsets outer: the PY sums are independent chains
+#pragma unroll
+            for (int j = 0; j < PY; ++j)     // D(y_j - 2 SIGMA h) = dv[j - 2 SIGMA (ih - HM) + 2 HM]
+                acc[j] = fmaf(Wr[j][ih], dv[j - 2 * SIGMA * (ih - HM) + 2 * HM], acc[j]);
 #pragma unroll
         for (int j = 0; j < PY; j += 2) {
             if (yb + j + 1 < a.x_hi) {
@@ -177,6 +167,29 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
             } else if (yb + j < a.x_hi) {
                 o[j] = a.accumulate ? o[j] + acc[j] : acc[j];
             }
+        }
+    };
+    // two pairs per barrier.  The prologue fills NS - 2 stages; iteration p waits for pairs p and
+    // p+1 (at most NS - 4 younger groups pending), then refills the stages of pairs p-2 and p-1,
+    // which every thread finished in the previous iteration (the barrier orders it).
+#pragma unroll
+    for (int q = 0; q < NS - 2; ++q) issue(q);
+    for (int p = 0; p < a.npair; p += 2) {
+        cpa_wait<NS - 4>();
+        __syncthreads();
+        issue(p + NS - 2);
+        issue(p + NS - 1);
+        const float *st0 = sm + stage_c * STG;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+        const float *st1 = sm + stage_c * STG;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+        float *o0 = const_cast<float *>(itout.ptr());
+        itout.next();
+        compute(st0, o0);
+        if (p + 1 < a.npair) {
+            float *o1 = const_cast<float *>(itout.ptr());
+            itout.next();
+            compute(st1, o1);
         }
     }
     cpa_wait<0>();
@@ -311,15 +324,9 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
         stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
         cpa_commit();
     };
-#pragma unroll
-    for (int q = 0; q < NS - 1; ++q) issue(q);
-    for (int p = 0; p < a.npair; ++p) {
-        cpa_wait<NS - 2>();
-        __syncthreads();
-        issue(p + NS - 1);
+    auto compute = [&](const float *stg) {
         // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k): stage index PX t + k (conflict-free vector loads)
-        const float *bd = sm + stage_c * STG + PX * t;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+        const float *bd = stg + PX * t;
         float dv[NWV], lv[NWV];
         lds_vec<VW>(dv, bd);
         lds_vec<VW>(lv, bd + WIN);
@@ -336,6 +343,21 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
                 acc[MODE == IMG_EXT ? 0 : i] += s;
             }
         }
+    };
+    // two pairs per barrier (same stage accounting as the scatter kernel)
+#pragma unroll
+    for (int q = 0; q < NS - 2; ++q) issue(q);
+    for (int p = 0; p < a.npair; p += 2) {
+        cpa_wait<NS - 4>();
+        __syncthreads();
+        issue(p + NS - 2);
+        issue(p + NS - 1);
+        const float *st0 = sm + stage_c * STG;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+        const float *st1 = sm + stage_c * STG;
+        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
+        compute(st0);
+        if (p + 1 < a.npair) compute(st1);
     }
     cpa_wait<0>();
 #pragma unroll
