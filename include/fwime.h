@@ -165,6 +165,18 @@ int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *
 int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                     const float *dobs, float eps, double *objective);
 
+/* Variable projection step (Theory section, Eqs. 2-5): approximately minimises
+ *   Phi_eps,m(p~) = 1/2 ||B~(m) p~ - dres||^2 + eps^2/2 ||D p~||^2
+ * with `niter` iterations of linear conjugate gradients on the normal
+ * equations (B~* B~ + eps^2 D* D) p~ = B~* dres, starting from and overwriting
+ * pt[nh][nz][nx].  dres[nshot][nt][nrec] = d_obs - f(m); both device pointers.
+ * history (host, niter+1 doubles, may be NULL) receives Phi_eps,m at every
+ * iterate, written at the next fwime_sync.  Each iteration applies B~ and B~*
+ * once (4 propagations + the background recomputation); the scalars stay on
+ * the device.  D = diag(|ih - (nh-1)/2| + 1) as in fwime_gradient. */
+int fwime_vp_solve(fwime_ctx *ctx, const float *v, const float *w, const float *dres, float eps, int niter,
+                   float *pt, double *history);
+
 /* f(m) for a group of contexts at once (Eq. 1; the Computational-aspects
  * section's shots are independent): ctxs[i] has its own grid, record length
  * and shots, with model v[i], wavelets w[i] and output d[i] (device pointers,

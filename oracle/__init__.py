@@ -8,8 +8,9 @@ CUDA path in ``paper_2206_02362_gb300``.
 Operators (Barnier et al., Theory section): ``forward`` = f(m) (Eq. 1),
 ``born``/``born_adj`` = B, B* (Eq. 8), ``born_ext``/``born_ext_adj`` = B~, B~*
 (Eqs. 1-2, subsurface-offset extension), ``tomo``/``tomo_adj`` = T, T* (Eq. 9),
-``gradient`` = (Phi at fixed p~, B* r + T* r) (Eqs. 1, 7-9), ``cost_fwime`` =
-Eq. 11.  Primitives (``lap``, ``step``, ``step_T``, ``prop``, ``prop_T``,
+``gradient`` = (Phi at fixed p~, B* r + T* r) (Eqs. 1, 7-9), ``vp_solve`` =
+linear conjugate gradients for the variable projection step (Eqs. 2-5),
+``cost_fwime`` = Eq. 11.  Primitives (``lap``, ``step``, ``step_T``, ``prop``, ``prop_T``,
 ``d2t``, ``d2t_T``, ``scatter``, ``scatter_TD``, ``scatter_TW``) are exposed
 for dot-product pins.
 
@@ -293,3 +294,48 @@ def cost_vp(n_vp: int, c_ext: float) -> float:
 def cost_fwime(n_vp: int, c_ext: float) -> float:
     """Eq. 11: C_FWIME = 6 + 4 N_vp (1 + C_ext)."""
     return float(_L().og_cost_fwime(int(n_vp), float(c_ext)))
+
+
+def dso_weights(g: Grid):
+    """Diagonal of D on p~[nh][nz][nx]: |ih - (nh-1)/2| + 1 per offset plane (the reading used by dso_penalty)."""
+    hm = (g.nh - 1) // 2
+    return (np.abs(np.arange(g.nh) - hm) + 1.0)[:, None, None]
+
+
+def vp_objective(g: Grid, v, geo: Geometry, w, dres, pt, eps: float) -> float:
+    """Phi_eps,m(p~) = 1/2 ||B~(m) p~ - dres||^2 + eps^2/2 ||D p~||^2 with dres = d_obs - f(m) (Eq. 2)."""
+    r = born_ext(g, v, geo, w, pt) - np.asarray(dres, dtype=np.float64)
+    return 0.5 * float(np.sum(r * r)) + 0.5 * eps * eps * float(np.sum((dso_weights(g) * pt) ** 2))
+
+
+def vp_solve(g: Grid, v, geo: Geometry, w, dres, pt0, eps: float, niter: int):
+    """Variable projection step (Eqs. 2-5): niter iterations of linear conjugate gradients on the normal
+    equations H p~ = B~* dres, H = B~* B~ + eps^2 D* D, started at pt0.  Textbook CG (Hestenes-Stiefel):
+    r = b - H p, d = r; per iteration alpha = r.r / d.Hd, p += alpha d, r -= alpha Hd,
+    beta = r'.r' / r.r, d = r' + beta d.  Returns (p~, [Phi at p_0, ..., p_niter]) with every Phi
+    evaluated directly from its definition."""
+    v = np.asarray(v, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    dres = np.asarray(dres, dtype=np.float64)
+    D2 = dso_weights(g) ** 2 * (eps * eps)
+
+    def H(q):
+        return born_ext_adj(g, v, geo, w, born_ext(g, v, geo, w, q)) + D2 * q
+
+    p = np.array(pt0, dtype=np.float64)
+    r = born_ext_adj(g, v, geo, w, dres) - H(p)
+    d = r.copy()
+    rr = float(np.sum(r * r))
+    hist = [vp_objective(g, v, geo, w, dres, p, eps)]
+    for _ in range(niter):
+        Hd = H(d)
+        dHd = float(np.sum(d * Hd))
+        alpha = rr / dHd if dHd > 0 else 0.0
+        p = p + alpha * d
+        r = r - alpha * Hd
+        rr_new = float(np.sum(r * r))
+        beta = rr_new / rr if rr > 0 else 0.0
+        d = r + beta * d
+        rr = rr_new
+        hist.append(vp_objective(g, v, geo, w, dres, p, eps))
+    return p, hist

@@ -34,9 +34,8 @@ KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_autotune", "fwime_forward_group",
-                 "fwime_sync",
-                 "fwime_profile_read",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_vp_solve",
+                 "fwime_autotune", "fwime_forward_group", "fwime_sync", "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
 
 
@@ -90,6 +89,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_tomo_adj.argtypes = [vp, fp, fp, fp, fp, fp, ip]
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_vp_solve.argtypes = [vp, fp, fp, fp, ctypes.c_float, ip, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.fwime_forward_group.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
@@ -304,6 +304,16 @@ class Context:
         self._done(self._lib.fwime_gradient(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs), ctypes.c_float(eps),
                                             _ptr(grad), ctypes.byref(self._J)), "fwime_gradient", sync)
         return float(self._J.value)
+
+    def vp_solve(self, v, w, dres, pt, eps=0.0, niter=10, sync=True):
+        """Variable projection (Eqs. 2-5): niter CG iterations on (B~*B~ + eps^2 D*D) p~ = B~* dres, in place on
+        pt.  Returns the objective Phi_eps,m at every iterate (niter + 1 values): a list when sync, else the
+        ctypes array that the next sync() fills."""
+        hist = (ctypes.c_double * (niter + 1))()
+        self._vp_hist = hist
+        self._done(self._lib.fwime_vp_solve(self._h, _ptr(v), _ptr(w), _ptr(dres), ctypes.c_float(eps), int(niter),
+                                            _ptr(pt), hist), "fwime_vp_solve", sync)
+        return list(hist) if sync else hist
 
     def autotune(self, op: int) -> tuple[int, float]:
         """Times the stencil kernel on this operator's batch for candidate chunkings; keeps the fastest.

@@ -65,6 +65,8 @@ struct fwime_ctx {
     void *small = nullptr;          // one stream-ordered block: J, partials, status, offsets
     std::vector<int> h_off;         // host copy of the offsets (source of the async upload)
     double *user_J = nullptr;
+    double *vp_hist_dev = nullptr, *vp_hist_user = nullptr;   // VP objective history (device, caller's host)
+    int vp_hist_n = 0;
     // workspace arena
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -1011,6 +1013,7 @@ void fwime_destroy(fwime_ctx *x)
     for (auto e : x->ev) cudaEventDestroy(e);
     if (x->ws) cudaFreeAsync(x->ws, x->st);
     if (x->small) cudaFreeAsync(x->small, x->st);
+    if (x->vp_hist_dev) cudaFreeAsync(x->vp_hist_dev, x->st);
     cudaGetLastError();
     delete x;
 }
@@ -1114,6 +1117,76 @@ int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt
     x->user_J = objective;
     Call c{FWIME_OP_GRADIENT, v, w, pt, dobs, grad, 0, eps};
     return call_op(x, c, K_EXT, K_DATA, K_MODEL);
+}
+
+int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dres, float eps, int niter, float *pt,
+                   double *history)
+{
+    if (!x) return FWIME_EINVAL;
+    if (!v || !w || !dres || !pt || niter < 0 || !(eps >= 0.f)) return fail(x, FWIME_EINVAL, "vp_solve arguments");
+    if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "vp_solve takes device pointers, no capture");
+    x->launches = 0;
+    const size_t nm = (size_t)x->g.nh * x->g.nz * x->g.nx, nd = (size_t)x->nshot * x->g.nt * x->nrec;
+    const long long PP = (long long)x->g.nz * x->g.nx;
+    float *r = nullptr, *pdir = nullptr, *hp = nullptr, *dtmp = nullptr;
+    double *sc = nullptr, *hist = nullptr;
+    const int nred = 1024;
+    const float eps2 = eps * eps;
+    auto dot = [&](const float *a, const float *b, size_t n, double *out, double scale, int acc) -> int {
+        LAUNCH(FWIME_K_OTHER, 8.0 * n, launch_dot(a, b, (long long)n, x->d_part, nred, out, acc, scale, x->st));
+        return FWIME_OK;
+    };
+    // H q = B~* B~ q + eps^2 D^2 q  (Eq. 3)
+    auto apply_H = [&](const float *q, float *out) -> int {
+        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT, v, w, q, nullptr, dtmp, 0, 0.f}));
+        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, out, 0, 0.f}));
+        LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_dso_add(q, out, x->g.nh, PP, eps2, x->st));
+        return FWIME_OK;
+    };
+    auto solve = [&]() -> int {
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&r), nm * sizeof(float), x->st));
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&pdir), nm * sizeof(float), x->st));
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&hp), nm * sizeof(float), x->st));
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&dtmp), nd * sizeof(float), x->st));
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&sc), 8 * sizeof(double), x->st));
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&hist), (niter + 1) * sizeof(double), x->st));
+        const double consts[8] = {0, 0, 0, 0, 0, 0, 1.0, -1.0};   // sc[6] = 1, sc[7] = -1
+        CK(cudaMemcpyAsync(sc, consts, sizeof(consts), cudaMemcpyHostToDevice, x->st));
+        // r0 = B~* (dres - B~ p0) - eps^2 D^2 p0,  Phi(p0) = 1/2 ||B~ p0 - dres||^2 + eps^2/2 ||D p0||^2
+        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT, v, w, pt, nullptr, dtmp, 0, 0.f}));
+        LAUNCH(FWIME_K_OTHER, 12.0 * nd, launch_axpby_dev(dtmp, dres, (long long)nd, sc, 6, 1.f, 7, x->st));   // dres - B~ p0
+        TRY(dot(dtmp, dtmp, nd, sc + 5, 0.5, 0));
+        LAUNCH(FWIME_K_OTHER, 4.0 * nm, launch_dso(pt, x->g.nh, PP, x->d_part, nred, x->st));
+        LAUNCH(FWIME_K_OTHER, 8.0, launch_sum_partials(x->d_part, nred, sc + 5, 1, 0.5 * (double)eps2, x->st));
+        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, r, 0, 0.f}));
+        LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_dso_add(pt, r, x->g.nh, PP, -eps2, x->st));
+        CK(cudaMemcpyAsync(pdir, r, nm * sizeof(float), cudaMemcpyDeviceToDevice, x->st));
+        TRY(dot(r, r, nm, sc + 0, 1.0, 0));
+        CK(cudaMemcpyAsync(hist, sc + 5, sizeof(double), cudaMemcpyDeviceToDevice, x->st));
+        for (int k = 0; k < niter; ++k) {
+            TRY(apply_H(pdir, hp));
+            TRY(dot(pdir, hp, nm, sc + 1, 1.0, 0));                              // p.Hp
+            LAUNCH(FWIME_K_OTHER, 8.0, launch_cg_scalars(sc, 0, hist, k + 1, x->st));   // alpha; Phi -= alpha rr / 2
+            LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_axpby_dev(pt, pdir, (long long)nm, sc, 2, 1.f, -1, x->st));   // p~ += alpha p
+            LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_axpby_dev(r, hp, (long long)nm, sc, 2, -1.f, -1, x->st));     // r -= alpha Hp
+            TRY(dot(r, r, nm, sc + 4, 1.0, 0));
+            LAUNCH(FWIME_K_OTHER, 8.0, launch_cg_scalars(sc, 1, nullptr, 0, x->st));     // beta = rr_new / rr
+            LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_axpby_dev(pdir, r, (long long)nm, sc, 6, 1.f, 3, x->st));   // p = r + beta p
+        }
+        return FWIME_OK;
+    };
+    const int rc = solve();
+    for (void *q : {(void *)r, (void *)pdir, (void *)hp, (void *)dtmp, (void *)sc})
+        if (q) cudaFreeAsync(q, x->st);
+    if (rc != FWIME_OK) {
+        if (hist) cudaFreeAsync(hist, x->st);
+        return rc;
+    }
+    if (x->vp_hist_dev) CK(cudaFreeAsync(x->vp_hist_dev, x->st));   // an earlier solve's history, never synced
+    x->vp_hist_dev = hist;
+    x->vp_hist_user = history;
+    x->vp_hist_n = niter + 1;
+    return FWIME_OK;
 }
 
 int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, const float *const *w, float *const *d)
@@ -1279,6 +1352,12 @@ int fwime_sync(fwime_ctx *x)
     if (x->user_J) {
         *x->user_J = *x->h_J;
         x->user_J = nullptr;
+    }
+    if (x->vp_hist_dev) {
+        if (x->vp_hist_user)
+            CK(cudaMemcpy(x->vp_hist_user, x->vp_hist_dev, x->vp_hist_n * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaFreeAsync(x->vp_hist_dev, x->st));
+        x->vp_hist_dev = x->vp_hist_user = nullptr;
     }
     if (st & ST_CFL) return fail(x, FWIME_ECFL, "velocity violates the CFL bound or is not positive");
     return FWIME_OK;

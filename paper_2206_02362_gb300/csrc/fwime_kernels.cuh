@@ -145,5 +145,12 @@ cudaError_t launch_sum_partials(const double *partials, int n, double *out, int 
                                 cudaStream_t st);
 cudaError_t launch_dso(const float *pt, int nh, long long PP, double *partials, int nblocks, cudaStream_t st);
 cudaError_t launch_copy_fields(float *dst, const float *src, long long n, cudaStream_t st);
+// VP conjugate gradients (device scalars)
+cudaError_t launch_dot(const float *x, const float *y, long long n, double *partials, int nblocks, double *out,
+                       int accumulate, double scale, cudaStream_t st);
+cudaError_t launch_dso_add(const float *p, float *hp, int nh, long long PP, float eps2, cudaStream_t st);
+cudaError_t launch_axpby_dev(float *y, const float *x, long long n, const double *sc, int ia, float sa, int ib,
+                             cudaStream_t st);
+cudaError_t launch_cg_scalars(double *sc, int mode, double *history, int k, cudaStream_t st);
 
 }  // namespace fwk

@@ -209,3 +209,92 @@ cudaError_t launch_copy_fields(float *dst, const float *src, long long n, cudaSt
 }
 
 }  // namespace fwk
+
+// ------------------------------------------------------------ VP conjugate gradients
+// Vector kernels of the linear conjugate-gradient solve of the variable projection step
+// (Theory section, Eqs. 2-5).  Scalars live in device memory (sc[]) so an iteration never
+// waits on the host.  Layout of sc: 0 rr, 1 pHp, 2 alpha, 3 beta, 4 rr_new, 5 phi.
+
+namespace {
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[256];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    return red[0];
+}
+}  // namespace
+
+// partials[b] = sum over this block's share of x . y (FP64, fixed order)
+__global__ void k_dot(const float *x, const float *y, long long n, double *partials)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)x[i] * (double)y[i];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Hp += eps^2 D^2 p with D = diag(|ih - hm| + 1), planes of PP points
+__global__ void k_dso_add(const float *p, float *hp, int nh, long long PP, float eps2)
+{
+    const long long n = (long long)nh * PP;
+    const int hm = (nh - 1) / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float wd = (float)(abs((int)(i / PP) - hm) + 1);
+        hp[i] = fmaf(eps2 * wd * wd, p[i], hp[i]);
+    }
+}
+
+// y = a x + b y with a, b read from device scalars (sign applied): ya = +/- sc[ia], yb = sc[ib] or 1
+__global__ void k_axpby_dev(float *y, const float *x, long long n, const double *sc, int ia, float sa, int ib)
+{
+    const float a = sa * (float)sc[ia];
+    const float b = ib >= 0 ? (float)sc[ib] : 1.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(a, x[i], b * y[i]);
+}
+
+// scalar updates: mode 0 (after pHp): alpha = rr / pHp, phi -= alpha rr / 2, store the history entry;
+// mode 1 (after rr_new): beta = rr_new / rr, rr = rr_new
+__global__ void k_cg_scalars(double *sc, int mode, double *history, int k)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == 0) {
+        sc[2] = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;
+        sc[5] -= 0.5 * sc[2] * sc[0];
+        if (history) history[k] = sc[5];
+    } else {
+        sc[3] = sc[0] > 0.0 ? sc[4] / sc[0] : 0.0;
+        sc[0] = sc[4];
+    }
+}
+
+namespace fwk {
+cudaError_t launch_dot(const float *x, const float *y, long long n, double *partials, int nblocks, double *out,
+                       int accumulate, double scale, cudaStream_t st)
+{
+    k_dot<<<nblocks, 256, 0, st>>>(x, y, n, partials);
+    return launch_sum_partials(partials, nblocks, out, accumulate, scale, st);
+}
+cudaError_t launch_dso_add(const float *p, float *hp, int nh, long long PP, float eps2, cudaStream_t st)
+{
+    k_dso_add<<<1216, 256, 0, st>>>(p, hp, nh, PP, eps2);
+    return cudaGetLastError();
+}
+cudaError_t launch_axpby_dev(float *y, const float *x, long long n, const double *sc, int ia, float sa, int ib,
+                             cudaStream_t st)
+{
+    k_axpby_dev<<<1216, 256, 0, st>>>(y, x, n, sc, ia, sa, ib);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_scalars(double *sc, int mode, double *history, int k, cudaStream_t st)
+{
+    k_cg_scalars<<<1, 32, 0, st>>>(sc, mode, history, k);
+    return cudaGetLastError();
+}
+}  // namespace fwk
