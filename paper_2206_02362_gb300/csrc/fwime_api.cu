@@ -1209,7 +1209,9 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
         if (runs[i].w.S < m->nshot)
             return fail(x, FWIME_ENOMEM, "group member %d: %d shots do not fit one batch", i, m->nshot);
         init_run(m, runs[i], m->nshot);
+        const long long before = m->launches;
         TRY(prep_model(m, runs[i], v[i]));
+        if (m != x) x->launches += m->launches - before;   // the group's count includes every member's prep
         TRY(zero(m, runs[i].w.f[0], sizeof(float) * m->nshot * m->P));
         TRY(zero(m, runs[i].w.f[1], sizeof(float) * m->nshot * m->P));
         TRY(zero(m, d[i], sizeof(float) * (size_t)m->nshot * m->g.nt * m->nrec));

@@ -39,7 +39,8 @@ def test_group_forward_matches_separate_calls_and_oracle():
             ctxs.append(c); vs.append(vd); ws.append(wd); refs.append(ref)
             ds.append(torch.full_like(ref, 3.0))
         fw.forward_group(ctxs, vs, ws, ds)
-        assert ctxs[0].launches == 2 * (max(g.nt for g, *_ in specs) - 1)
+        # one model preparation per member, then a stencil and a recording launch per time step
+        assert ctxs[0].launches == len(specs) + 2 * (max(g.nt for g, *_ in specs) - 1)
     for (grid, geom, v, w), d, ref in zip(specs, ds, refs):
         assert torch.equal(d, ref)
         og = oracle.Grid(nz=grid.nz, nx=grid.nx, W=grid.sponge, nt=grid.nt, dt=grid.dt, dx=grid.dx)
