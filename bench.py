@@ -290,8 +290,8 @@ def ncu_traffic():
     if not m or not t or m.group(1) != h:
         return None
     return {"dram_bytes_per_launch": float(t.group(1)),
-            "variant_algorithmic_bytes": float(a.group(1)) if a else None,
-            "variant": "k_prop<LOCAL> (one local source field), 32-shot capture scaled to 100 shots",
+            "algorithmic_bytes_per_launch": float(a.group(1)) if a else None,
+            "captured": "every k_prop launch of one timed bench step (full size, 100 shots, nt 200), 1-pass ncu",
             "source": "profiles/k_prop_marmousi2_ncu.md"}
 
 
@@ -381,7 +381,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": "k_prop (wave-equation time step, forward and adjoint)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic,
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic_source": traffic,
                 "launches": pk["launches"], "avg_launch_us": 1e3 * pk["ms"] / max(pk["launches"], 1),
                 "algorithmic_bytes_per_launch": pk["bytes"] / max(pk["launches"], 1),
                 "time_share": {k: round(p["ms"] / kern_ms, 4) for k, p in prof.items()} if kern_ms else None,

@@ -447,10 +447,7 @@ static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, R
     ExtArgs a{};
     a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz;
-    ext_cols(x, a.x_lo, a.x_hi);
-    // start the range where the kernel's window (x_lo - 2 hm) falls on a 16-byte boundary; the
-    // extra leading columns have zero weights and receive zero
-    a.x_lo -= (((a.x_lo - 2 * a.hm) % 4) + 4) % 4;
+    ext_cols(x, a.x_lo, a.x_hi);   // the launcher may start a few columns earlier (zero weights there)
     a.sigma = sigma; a.W = W; a.in = in; a.outr = out; a.accumulate = accumulate;
     const double pts = (double)x->g.nz * (a.x_hi - a.x_lo);
     LAUNCH(FWIME_K_SCATTER, pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0)) + 4.0 * x->g.nh),
@@ -464,10 +461,7 @@ static int image(Run &r, int Sb, int n0, int kk, int mode, RingRef D, RingRef L,
     fwime_ctx *x = r.x;
     ImgArgs a{};
     a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
-    a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;
-    // start the range where the kernel's windows (x_lo - hm) fall on a 16-byte boundary; the extra
-    // leading columns lie outside the physical grid and are never read back
-    a.x_lo -= (((a.x_lo - a.hm) % 4) + 4) % 4;
+    a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;   // the physical columns
     a.D = D; a.L = L; a.M2 = M2; a.Ds = Ds; a.alpha = alpha; a.pt = pt; a.img = img;
     const double pts = (double)x->g.nz * x->g.nx;
     const double per = 8.0 + (M2.base ? 4 : 0) + (Ds.base ? 4 : 0);

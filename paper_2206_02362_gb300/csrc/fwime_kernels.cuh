@@ -19,7 +19,10 @@ constexpr int STRIP = 128;      // x-points per warp in the stencil kernel (32 l
 constexpr int PROP_WARPS = 4;   // warps per CTA in the stencil kernel
 constexpr int EXT_TX = 128;     // x-points per CTA in the scatter / imaging kernels
 constexpr int MAX_NH = 201;     // largest supported number of subsurface offsets
-constexpr int EXT_STAGES = 6;   // cp.async pipeline depth of the scatter / imaging kernels (even, >= 4)
+#ifndef FWIME_EXT_STAGES
+#define FWIME_EXT_STAGES 6
+#endif
+constexpr int EXT_STAGES = FWIME_EXT_STAGES;   // cp.async pipeline depth of the imaging kernels (even, >= 4)
 
 // status bits latched by kernels
 constexpr int ST_CFL = 1;

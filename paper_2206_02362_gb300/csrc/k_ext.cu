@@ -6,17 +6,20 @@
 //   scatter    e(y)   = sum_h W(y-h, h) D(y-2h)          (sigma = +1)
 //   transpose  z(u)   = sum_h W(u+h, h) L(u+2h)          (sigma = -1)
 //   image      I(x,h) += sum_{shots,steps} D(x-h) L(x+h)
-//   contract   G(x)   += sum_h p~(x,h) sum D(x-h) L(x+h)
+//   contract   G(x)   += sum_h p~(x,h) sum D(x-h) L(x+h)  (generic kernel only)
 //   local      G(x)   += sum D (alpha L + M2) + Ds L
 //
 // The weights W = b p~ (nh values per point) are shared by every shot and
 // every time step, so these kernels run once per segment of K time steps over
-// all K x S (step, shot) pairs of a batch: a CTA owns one row and 128 columns,
-// keeps its nh weights (or nh image accumulators) in registers for the whole
-// segment, and streams the pairs' D/L rows through a double-buffered
-// shared-memory window (global loads of pair p+1 are issued before the
-// arithmetic of pair p).  Weight and image traffic is then 1/(K S) of a
-// per-step formulation.
+// all K x S (step, shot) pairs of a batch, keeping the weights (scatter) or the
+// image accumulators (imaging) in registers for the whole segment, while the
+// pairs' rows stream through cp.async rings in shared memory.  Weight and image
+// traffic is then 1/(K S) of a per-step formulation.  Both default kernels copy
+// rows de-interleaved into their even and odd samples: the products of offset h
+// pair samples of one parity (y and y - 2h; x - h and x + h), so a lane that
+// owns samples of one parity reuses every loaded sample for several offsets.
+#include <utility>
+
 #include "fwime_kernels.cuh"
 
 namespace fwk {
@@ -57,6 +60,49 @@ __device__ __forceinline__ void cpa16(float *dst, const float *src, bool valid)
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// 4-byte asynchronous copy (cp.async.ca); src_bytes = 0 zero-fills.  Used to de-interleave a row
+// into its even and odd samples while it is copied into shared memory.
+__device__ __forceinline__ void cpa4(unsigned dst, const float *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+// unconditional 4-byte copies dst + C SSTEP <- src + C GSTEP bytes for C in the sequence (immediate
+// offsets: one instruction per copy)
+template <int SOFF, int GOFF>
+__device__ __forceinline__ void cpa4_imm(unsigned dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], 4;\n" ::"r"(dst), "l"(src), "n"(SOFF), "n"(GOFF)
+                 : "memory");
+}
+template <int SSTEP, int GSTEP, int... C>
+__device__ __forceinline__ void cpa4_run(unsigned dst, const float *src, std::integer_sequence<int, C...>)
+{
+    (cpa4_imm<SSTEP * C, GSTEP * C>(dst, src), ...);
+}
+
+// Row pointer of the (step, shot) pairs of a segment in order (shot fastest), advanced by one
+// addition per pair and a multiply only when the time slot changes.
+struct PairRow {
+    const float *base, *row;
+    long long slot_stride, P;
+    int S, mod, s, slot;
+    __device__ __forceinline__ void init(const RingRef &r, int n0, int S_, long long P_, long long rowoff)
+    {
+        base = r.base + rowoff; slot_stride = r.slot_stride; P = P_; S = S_; mod = r.mod; s = 0;
+        slot = r.mod > 0 ? (n0 + r.shift) % r.mod : r.shift;
+        row = base + (long long)slot * slot_stride;
+    }
+    __device__ __forceinline__ void next()
+    {
+        if (++s == S) {
+            s = 0;
+            if (++slot == mod) slot = 0;   // mod == 0 (direct rings) never wraps
+            row = base + (long long)slot * slot_stride;
+        } else {
+            row += P;
+        }
+    }
+};
 
 // Copies the row segment [wal, wal + 4 * nchunk) of `src` (16-byte chunks, zero outside [0, NXP))
 // into `dst`; wal is a multiple of 4.
@@ -96,6 +142,172 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
     }
 }
 
+// ---------------------------------------------------------- scatter, parity-split (default path)
+//
+// e(y) = sum_h W(y - sigma h, h) D(y - 2 sigma h) reads D only at samples of y's parity.  A lane
+// owns A outputs of one parity, y_j = yf + 2j, whose A x NH products need only A + 2 HM samples of
+// that parity: rows are copied into shared memory split into their even and odd samples (4-byte
+// cp.async), and every sample a lane loads serves up to A multiply-adds with the A x NH weights it
+// keeps in registers for the whole segment.  Lanes 0-15 take the even outputs of the warp's 32 A
+// columns, lanes 16-31 the odd ones; one shuffle across the two halves reassembles A consecutive
+// outputs per lane for vector stores.  Each warp streams its own window through its own cp.async
+// ring, synchronised with __syncwarp only.
+#ifndef FWIME_SC_WARPS
+#define FWIME_SC_WARPS 4
+#endif
+#ifndef FWIME_SC_STAGES
+#define FWIME_SC_STAGES 8
+#endif
+#ifndef FWIME_SC_MINB
+#define FWIME_SC_MINB 1
+#endif
+#ifndef FWIME_IMG_MINB
+#define FWIME_IMG_MINB 1
+#endif
+#ifndef FWIME_SC_A21
+#define FWIME_SC_A21 4
+#endif
+constexpr int SC_WARPS = FWIME_SC_WARPS;     // warps per CTA (independent pipelines)
+constexpr int SC_STAGES = FWIME_SC_STAGES;   // cp.async ring depth per warp
+
+template <int NH, int A>
+struct ScatterShape {
+    static constexpr int HM = (NH - 1) / 2;
+    static constexpr int WOUT = 32 * A;                      // outputs per warp
+    static constexpr int SPAN = WOUT + 4 * HM;               // window [yw - 2 HM, yw + WOUT + 2 HM)
+    static constexpr int HALF = SPAN / 2;                    // samples of one parity
+    static constexpr int OFF = (HALF + 31) / 32 * 32 + 16;   // odd samples, 16 banks after the even ones
+    static constexpr int STG = 2 * OFF;                      // floats per stage
+    static constexpr int NCP = (SPAN + 31) / 32;             // 4-byte copies per lane and pair
+    static constexpr int VW = A % 4 == 0 ? 4 : 2;
+    static constexpr int NWIN = A + 2 * HM;                  // samples a lane reads
+    static constexpr int NWV = (NWIN + VW - 1) / VW * VW;
+    static constexpr size_t SMEM = (size_t)SC_WARPS * SC_STAGES * STG * sizeof(float);
+    // copies past SPAN land below OFF (even) or 2 OFF (odd); reads stay below HALF + 4 <= OFF
+    static_assert(OFF >= HALF + 16 && 15 * A + NWV <= OFF, "parity array overflow");
+};
+
+template <int NH, int A, int SIGMA>
+__global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(const ExtArgs a, int nwx)
+{
+    using Sh = ScatterShape<NH, A>;
+    constexpr int HM = Sh::HM, NS = SC_STAGES;
+    extern __shared__ float4 sm4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wsm = reinterpret_cast<float *>(sm4) + warp * NS * Sh::STG;
+    // warps are numbered over (row, column block) so that no warp of a CTA idles at a row's end
+    const int gw = blockIdx.x * SC_WARPS + warp;
+    if (gw >= nwx * (a.z_hi - a.z_lo)) return;     // whole warp; no block-wide barrier follows
+    const int Z = a.z_lo + gw / nwx;
+    const int yw = a.x_lo + (gw % nwx) * Sh::WOUT;  // multiple of 4
+    const int par = lane >> 4, tp = lane & 15;
+    const int yf = yw + par + 2 * A * tp;          // this lane's outputs yf + 2j, j < A
+    const long long rowoff = (long long)Z * a.NXP;
+    const int wal = yw - 2 * HM;                   // even
+
+    float Wr[A][NH];
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+        const int y = yf + 2 * j;
+#pragma unroll
+        for (int ih = 0; ih < NH; ++ih) {
+            const int xs = y - SIGMA * (ih - HM);
+            Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
+        }
+    }
+    // the lane copies window samples n = lane + 32 c (column wal + n) into its parity's array
+    const unsigned sm0 =
+        static_cast<unsigned>(__cvta_generic_to_shared(wsm)) + 4u * ((lane & 1) * Sh::OFF + (lane >> 1));
+    const int col0 = wal + lane;
+    const bool interior = wal >= 0 && wal + 32 * Sh::NCP <= a.NXP;
+    PairRow pin, pout;
+    pin.init(a.in, a.n0, a.S, a.P, rowoff);
+    pout.init(a.outr, a.n0, a.S, a.P, rowoff);
+    unsigned st_in = 0;
+    int st_c = 0;
+    auto issue = [&](int p) {
+        if (p < a.npair) {
+            const unsigned d = sm0 + st_in;
+            if (interior) {
+                cpa4_run<64, 128>(d, pin.row + col0, std::make_integer_sequence<int, Sh::NCP>{});
+            } else {
+#pragma unroll
+                for (int c = 0; c < Sh::NCP; ++c) {
+                    const int col = col0 + 32 * c;
+                    const bool ok = col >= 0 && col < a.NXP;
+                    cpa4(d + 64u * c, pin.row + (ok ? col : 0), ok);
+                }
+            }
+            pin.next();
+        }
+        st_in = st_in + 4u * Sh::STG == 4u * NS * Sh::STG ? 0u : st_in + 4u * Sh::STG;
+        cpa_commit();
+    };
+#pragma unroll 1
+    for (int q = 0; q < NS - 1; ++q) issue(q);
+    const int ys = yw + 2 * A * tp + A * par;      // first of the A consecutive outputs this lane stores
+    const float *lsm = wsm + par * Sh::OFF + A * tp;
+#pragma unroll 1
+    for (int p = 0; p < a.npair; ++p) {
+        cpa_wait<NS - 2>();                        // pair p has landed (this lane's copies) ...
+        __syncwarp();                              // ... and every lane's; all finished pair p - 1
+        issue(p + NS - 1);                         // refills the stage of pair p - 1
+        float dv[Sh::NWV];                         // dv[k] = D(yf - 2 HM + 2k)
+        lds_vec<Sh::VW>(dv, lsm + st_c);
+        st_c = st_c + Sh::STG == NS * Sh::STG ? 0 : st_c + Sh::STG;
+        // two partial sums per output (even / odd offsets): 2 A independent chains.  Offsets are
+        // visited in the order of their samples, so the first products wait only for the first load.
+        float acc[2][A];
+#pragma unroll
+        for (int j = 0; j < A; ++j) acc[0][j] = acc[1][j] = 0.f;
+#pragma unroll
+        for (int m = 0; m < NH; ++m) {
+            const int ih = SIGMA > 0 ? NH - 1 - m : m;
+#pragma unroll
+            for (int j = 0; j < A; ++j)            // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
+                acc[m & 1][j] = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], acc[m & 1][j]);
+        }
+        float e[A];
+#pragma unroll
+        for (int j = 0; j < A; ++j) e[j] = acc[0][j] + acc[1][j];
+        float v[A];
+        if constexpr (A == 4) {
+            const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[0] : e[2], 16);
+            const float r1 = __shfl_xor_sync(0xffffffffu, par ? e[1] : e[3], 16);
+            v[0] = par ? r0 : e[0]; v[1] = par ? e[2] : r0;
+            v[2] = par ? r1 : e[1]; v[3] = par ? e[3] : r1;
+        } else {
+            const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[0] : e[1], 16);
+            v[0] = par ? r0 : e[0]; v[1] = par ? e[1] : r0;
+        }
+        float *o = const_cast<float *>(pout.row) + ys;
+        pout.next();
+        if (ys + A <= a.x_hi) {
+            if constexpr (A == 4) {
+                float4 w4 = make_float4(v[0], v[1], v[2], v[3]);
+                if (a.accumulate) {
+                    const float4 old = *reinterpret_cast<const float4 *>(o);
+                    w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+                }
+                *reinterpret_cast<float4 *>(o) = w4;
+            } else {
+                float2 w2 = make_float2(v[0], v[1]);
+                if (a.accumulate) {
+                    const float2 old = *reinterpret_cast<const float2 *>(o);
+                    w2.x += old.x; w2.y += old.y;
+                }
+                *reinterpret_cast<float2 *>(o) = w2;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < A; ++k)
+                if (ys + k < a.x_hi) o[k] = a.accumulate ? o[k] + v[k] : v[k];
+        }
+    }
+    cpa_wait<0>();
+}
+
+#if FWIME_EXT_RB
 // Register-blocked scatter: a thread owns PY consecutive outputs y_j = yb + j; the D samples
 // they need, y_j - 2 sigma h, lie in the 4 HM + PY consecutive positions [yb - 2HM, yb + PY + 2HM),
 // read with conflict-free vector loads (the column range is aligned so that the CTA's window
@@ -195,6 +407,8 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
     cpa_wait<0>();
 }
 
+#endif  // FWIME_EXT_RB
+
 // Generic-nh fallback (weights re-read per pair): any odd nh up to MAX_NH.
 __global__ void __launch_bounds__(EXT_TX) k_scatter_gen(const ExtArgs a)
 {
@@ -231,13 +445,15 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_gen(const ExtArgs a)
     }
 }
 
+#if FWIME_EXT_RB
 template <int NH, int PY>
-static void launch_scatter_nh(const ExtArgs &a, cudaStream_t st)
+static void launch_scatter_nh(ExtArgs a, cudaStream_t st)
 {
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PY;
     constexpr int STG = 4 * ((TXS + 4 * HM + 3) / 4) + 4;
     const size_t smem = EXT_STAGES * STG * sizeof(float);
+    a.x_lo -= (((a.x_lo - 2 * HM) % 4) + 4) % 4;   // window start on a 16-byte boundary
     dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
     static bool attr = false;      // once per instantiation, before any launch (and any capture)
     if (!attr) {
@@ -248,18 +464,39 @@ static void launch_scatter_nh(const ExtArgs &a, cudaStream_t st)
     if (a.sigma > 0) k_scatter_rb<NH, PY, 1><<<grid, EXT_TX, smem, st>>>(a);
     else k_scatter_rb<NH, PY, -1><<<grid, EXT_TX, smem, st>>>(a);
 }
+#define FWIME_SCATTER(NH, PY, A) launch_scatter_nh<NH, PY>(a, st)
+#else
+template <int NH, int A>
+static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
+{
+    using Sh = ScatterShape<NH, A>;
+    a.x_lo -= a.x_lo % 4;          // outputs start on a 16-byte boundary (leading columns get zero weights)
+    const int nwx = (a.x_hi - a.x_lo + Sh::WOUT - 1) / Sh::WOUT;        // warps per row
+    const long long nw = (long long)nwx * (a.z_hi - a.z_lo);
+    dim3 grid((unsigned)((nw + SC_WARPS - 1) / SC_WARPS));
+    static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    if (!attr) {
+        cudaFuncSetAttribute(k_scatter_ps<NH, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        cudaFuncSetAttribute(k_scatter_ps<NH, A, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        attr = true;
+    }
+    if (a.sigma > 0) k_scatter_ps<NH, A, 1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
+    else k_scatter_ps<NH, A, -1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
+}
+#define FWIME_SCATTER(NH, PY, A) launch_scatter_ps<NH, A>(a, st)
+#endif
 
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     switch (a.nh) {
-    case 1: launch_scatter_nh<1, 8>(a, st); break;
-    case 3: launch_scatter_nh<3, 8>(a, st); break;
-    case 5: launch_scatter_nh<5, 8>(a, st); break;
-    case 11: launch_scatter_nh<11, 8>(a, st); break;
-    case 21: launch_scatter_nh<21, 4>(a, st); break;
-    case 31: launch_scatter_nh<31, 2>(a, st); break;
-    case 41: launch_scatter_nh<41, 2>(a, st); break;
+    case 1: FWIME_SCATTER(1, 8, 4); break;
+    case 3: FWIME_SCATTER(3, 8, 4); break;
+    case 5: FWIME_SCATTER(5, 8, 4); break;
+    case 11: FWIME_SCATTER(11, 8, 4); break;
+    case 21: FWIME_SCATTER(21, 4, FWIME_SC_A21); break;
+    case 31: FWIME_SCATTER(31, 2, 4); break;
+    case 41: FWIME_SCATTER(41, 2, 2); break;
     default: {
         dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
         const int hm = (a.nh - 1) / 2;
@@ -268,9 +505,291 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
     }
     return cudaGetLastError();
 }
+#undef FWIME_SCATTER
 
 // ------------------------------------------------------------------ imaging
 
+// ---------------------------------------------------------- imaging, parity-split blocks (default path)
+//
+// I(x, h) += D(x - h) L(x + h).  With u = x - h and w = x + h (same parity) the products of one
+// (step, shot) pair are D(u) L(w) over the band |w - u| <= 2 HM; in the index of one parity,
+// u = ub + par + 2 ut and w = ub + par + 2 wt, the band is |wt - ut| <= HM.  A lane owns 8
+// consecutive ut and a window of 4 nl consecutive wt starting lo after its first ut (a task may
+// have two windows): 8 + 4 nl loaded samples serve up to 32 nl multiply-adds, products outside the
+// band being dropped at compile time.  The windows of the NT tasks (one warp each) tile the band
+// exactly, so every (x, h) is accumulated by exactly one lane of one CTA (a CTA covers 256
+// consecutive u and every offset).  Rows are copied de-interleaved by parity (4-byte cp.async);
+// the 16-byte chunks of a parity array are stored alternately in two halves so that the lanes'
+// vector loads, 8 floats apart, hit distinct banks, and so do the copies.
+struct ImgTask {
+    int lo1, nl1, lo2, nl2;        // windows [lo, lo + 4 nl) of wt - (the lane's first ut); nl2 = 0: none
+};
+
+__host__ __device__ constexpr int img_ntask(int nh)
+{
+    return nh <= 5 ? 1 : nh == 11 ? 2 : nh == 21 ? 3 : nh == 31 ? 4 : 5;
+}
+__host__ __device__ constexpr ImgTask img_task(int nh, int k)
+{
+    return nh == 1 ? ImgTask{0, 2, 0, 0}
+         : nh <= 5 ? ImgTask{-4, 4, 0, 0}
+         : nh == 11 ? (k == 0 ? ImgTask{0, 2, 0, 0} : ImgTask{-8, 2, 8, 2})
+         : nh == 21 ? (k == 0 ? ImgTask{-16, 4, 0, 0} : k == 1 ? ImgTask{0, 2, 0, 0} : ImgTask{8, 4, 0, 0})
+         : nh == 31 ? (k == 0 ? ImgTask{-8, 2, 0, 0} : k == 1 ? ImgTask{0, 2, 0, 0}
+                       : k == 2 ? ImgTask{8, 2, 0, 0} : ImgTask{-16, 2, 16, 2})
+         : (k == 0 ? ImgTask{-24, 4, 0, 0} : k == 1 ? ImgTask{-8, 2, 0, 0} : k == 2 ? ImgTask{0, 2, 0, 0}
+            : k == 3 ? ImgTask{8, 2, 0, 0} : ImgTask{16, 4, 0, 0});
+}
+// every wt - ut offset the band needs, -HM .. 7 + HM, lies in exactly one window; none overlap
+__host__ __device__ constexpr bool img_tasks_tile(int nh)
+{
+    const int hm = (nh - 1) / 2;
+    for (int o = -64; o < 72; ++o) {
+        int n = 0;
+        for (int k = 0; k < img_ntask(nh); ++k) {
+            const ImgTask t = img_task(nh, k);
+            n += (o >= t.lo1 && o < t.lo1 + 4 * t.nl1) + (t.nl2 > 0 && o >= t.lo2 && o < t.lo2 + 4 * t.nl2);
+        }
+        if (n > 1 || (o >= -hm && o <= 7 + hm && n != 1)) return false;
+    }
+    return true;
+}
+static_assert(img_tasks_tile(1) && img_tasks_tile(3) && img_tasks_tile(5) && img_tasks_tile(11) &&
+              img_tasks_tile(21) && img_tasks_tile(31) && img_tasks_tile(41), "imaging tasks must tile the band");
+
+__host__ __device__ constexpr int img_hc(int len)     // chunk pairs of a parity array (== 2 mod 8: no conflicts)
+{
+    int h = 2 * ((len + 15) / 16);
+    while (h % 8 != 2) ++h;
+    return h;
+}
+
+template <int NH>
+struct ImgShape {
+    static constexpr int HM = (NH - 1) / 2;
+    static constexpr int NT = img_ntask(NH);
+    static constexpr int TX = 32 * NT;
+    static constexpr int lo_min()
+    {
+        int m = 1 << 20;
+        for (int k = 0; k < NT; ++k) {
+            const ImgTask t = img_task(NH, k);
+            m = t.lo1 < m ? t.lo1 : m;
+            if (t.nl2 > 0) m = t.lo2 < m ? t.lo2 : m;
+        }
+        return m;
+    }
+    static constexpr int hi_max()
+    {
+        int m = -(1 << 20);
+        for (int k = 0; k < NT; ++k) {
+            const ImgTask t = img_task(NH, k);
+            m = t.lo1 + 4 * t.nl1 > m ? t.lo1 + 4 * t.nl1 : m;
+            if (t.nl2 > 0) m = t.lo2 + 4 * t.nl2 > m ? t.lo2 + 4 * t.nl2 : m;
+        }
+        return m;
+    }
+    static constexpr int LO = lo_min();
+    static constexpr int UT = 128;                           // ut per parity per CTA (16 lanes x 8)
+    static constexpr int LD = UT;                            // D samples per parity
+    static constexpr int LL = UT - 8 + hi_max() - LO;        // L samples per parity: wt in [LO, UT - 8 + hi)
+    static constexpr int HCD = img_hc(LD), HCL = img_hc(LL);
+    static constexpr int OFFD = (8 * HCD + 31) / 32 * 32 + 16, OFFL = (8 * HCL + 31) / 32 * 32 + 16;
+    static constexpr int REGD = OFFD + 8 * HCD;              // D region (floats); the L region follows
+    static constexpr int STG = (REGD + OFFL + 8 * HCL + 3) / 4 * 4;
+    static constexpr int NCD = (2 * LD + TX - 1) / TX, NCL = (2 * LL + TX - 1) / TX;
+    static constexpr size_t SMEM = (size_t)EXT_STAGES * STG * sizeof(float);
+    static_assert(REGD % 8 == 0 && LO % 4 == 0, "alignment");
+};
+
+// one task's share of a pair: products of the lane's 8 D samples with its L window(s)
+template <int NH, int K>
+struct ImgTaskBody {
+    static constexpr ImgTask T = img_task(NH, K);
+    static constexpr int HM = (NH - 1) / 2;
+    static constexpr int W1 = 4 * T.nl1, W2 = T.nl2 > 0 ? 4 * T.nl2 : 1;
+    float acc1[8][W1], acc2[8][W2];
+
+    __device__ __forceinline__ static constexpr bool in1(int i, int j) { return (T.lo1 + j - i) <= HM && (T.lo1 + j - i) >= -HM; }
+    __device__ __forceinline__ static constexpr bool in2(int i, int j)
+    {
+        return T.nl2 > 0 && (T.lo2 + j - i) <= HM && (T.lo2 + j - i) >= -HM;
+    }
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = 0; j < W1; ++j) acc1[i][j] = 0.f;
+#pragma unroll
+            for (int j = 0; j < W2; ++j) acc2[i][j] = 0.f;
+        }
+    }
+    // loads the lane's L window [8 b + LOW, 8 b + LOW + 4 NL) of wt: chunks c0 + q of the L region
+    // (which starts at wt = LO), chunk c at slot (c & 1) hcl + (c >> 1)
+    template <int LOW, int NL>
+    __device__ __forceinline__ static void load_window(float (&lv)[4 * NL], const float *sl, int b, int hcl)
+    {
+        constexpr int c0 = (LOW - ImgShape<NH>::LO) / 4;
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int c = c0 + q;
+            const float4 v = *reinterpret_cast<const float4 *>(sl + 4 * ((c & 1) * hcl + b + (c >> 1)));
+            lv[4 * q] = v.x; lv[4 * q + 1] = v.y; lv[4 * q + 2] = v.z; lv[4 * q + 3] = v.w;
+        }
+    }
+    __device__ __forceinline__ void pair(const float *sd, const float *sl, int b)
+    {
+        using Sh = ImgShape<NH>;
+        float dv[8];
+        {
+            const float4 d0 = *reinterpret_cast<const float4 *>(sd + 4 * b);
+            const float4 d1 = *reinterpret_cast<const float4 *>(sd + 4 * (Sh::HCD + b));
+            dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
+            dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
+        }
+        float l1[W1];
+        load_window<T.lo1, T.nl1>(l1, sl, b, Sh::HCL);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < W1; ++j)
+                if (in1(i, j)) acc1[i][j] = fmaf(dv[i], l1[j], acc1[i][j]);
+        if constexpr (T.nl2 > 0) {
+            float l2[W2];
+            load_window<T.lo2, (T.nl2 > 0 ? T.nl2 : 1)>(l2, sl, b, Sh::HCL);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < W2; ++j)
+                    if (in2(i, j)) acc2[i][j] = fmaf(dv[i], l2[j], acc2[i][j]);
+        }
+    }
+    // adds the accumulators into img at x = x1 + i + o, h = o - i (o = lo + j), x1 = the lane's
+    // first u + its first ut offset; only physical columns [x_lo, x_hi)
+    __device__ __forceinline__ void store(const ImgArgs &a, long long rowoff, int x1)
+    {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = 0; j < W1; ++j) {
+                if (in1(i, j)) {
+                    const int x = x1 + i + T.lo1 + j;
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo1 + j - i + HM) * a.P + rowoff + x] += acc1[i][j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < W2; ++j) {
+                if (in2(i, j)) {
+                    const int x = x1 + i + T.lo2 + j;
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo2 + j - i + HM) * a.P + rowoff + x] += acc2[i][j];
+                }
+            }
+        }
+    }
+};
+
+// block-wide barrier that warps may reach from different code (each warp runs its own task's
+// instantiation of the same pipeline): the non-.aligned form of bar.sync
+__device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;\n" ::: "memory"); }
+
+template <int NH, int K>
+__device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *sm, int lane)
+{
+    using Sh = ImgShape<NH>;
+    constexpr int NS = EXT_STAGES;
+    const int Z = a.z_lo + blockIdx.y;
+    const long long rowoff = (long long)Z * a.NXP;
+    const int ub = u_lo + 256 * blockIdx.x;         // even
+    const int t = threadIdx.x;
+    const int par = lane >> 4, b = lane & 15;
+    // copy plan: thread t copies window samples n = t + TX c; sample n of a window goes to parity n & 1,
+    // index k = n >> 1, chunk k >> 2 stored at slot (chunk & 1) HC + (chunk >> 1)
+    const int cw = (t & 1), ch = (t >> 3) & 1, cp = (t >> 4), ce = (t >> 1) & 3;
+    const unsigned sbase = static_cast<unsigned>(__cvta_generic_to_shared(sm));
+    const unsigned dD = sbase + 4u * (cw * Sh::OFFD + 4 * (ch * Sh::HCD + cp) + ce);
+    const unsigned dL = sbase + 4u * (Sh::REGD + cw * Sh::OFFL + 4 * (ch * Sh::HCL + cp) + ce);
+    constexpr unsigned CSTEP = 4u * 8u * Sh::NT;     // bytes between copies c and c + 1 (TX / 16 chunk pairs)
+    const int colD = ub + t, colL = ub + 2 * Sh::LO + t;
+    // all copied columns, [ub + 2 LO, ub + 2 LO + 2 LL) (which contains the D window), inside the row
+    const bool interior = ub + 2 * Sh::LO >= 0 && ub + 2 * Sh::LO + 2 * Sh::LL <= a.NXP;
+    PairRow pd, pl;
+    pd.init(a.D, a.n0, a.S, a.P, rowoff);
+    pl.init(a.L, a.n0, a.S, a.P, rowoff);
+    int st_in = 0, st_c = 0;
+    constexpr int FD = 2 * Sh::LD / Sh::TX, RD = 2 * Sh::LD - FD * Sh::TX;   // full copy rounds, remainder
+    constexpr int FL = 2 * Sh::LL / Sh::TX, RL = 2 * Sh::LL - FL * Sh::TX;
+    auto issue = [&](int p) {
+        if (p < a.npair) {
+            const unsigned so = 4u * st_in * Sh::STG;
+            if (interior) {
+                const float *sd = pd.row + colD, *sl = pl.row + colL;
+                cpa4_run<CSTEP, 4 * Sh::TX>(dD + so, sd, std::make_integer_sequence<int, FD>{});
+                if (RD > 0 && t < RD) cpa4_imm<CSTEP * FD, 4 * Sh::TX * FD>(dD + so, sd);
+                cpa4_run<CSTEP, 4 * Sh::TX>(dL + so, sl, std::make_integer_sequence<int, FL>{});
+                if (RL > 0 && t < RL) cpa4_imm<CSTEP * FL, 4 * Sh::TX * FL>(dL + so, sl);
+            } else {
+#pragma unroll
+                for (int c = 0; c < Sh::NCD; ++c) {
+                    if (t + Sh::TX * c < 2 * Sh::LD) {
+                        const int col = colD + Sh::TX * c;
+                        const bool ok = col >= 0 && col < a.NXP;
+                        cpa4(dD + so + CSTEP * c, pd.row + (ok ? col : 0), ok);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < Sh::NCL; ++c) {
+                    if (t + Sh::TX * c < 2 * Sh::LL) {
+                        const int col = colL + Sh::TX * c;
+                        const bool ok = col >= 0 && col < a.NXP;
+                        cpa4(dL + so + CSTEP * c, pl.row + (ok ? col : 0), ok);
+                    }
+                }
+            }
+            pd.next();
+            pl.next();
+        }
+        st_in = st_in + 1 == NS ? 0 : st_in + 1;
+        cpa_commit();
+    };
+    ImgTaskBody<NH, K> body;
+    body.zero();
+    // two pairs per barrier: the prologue fills NS - 2 stages; iteration p waits for pairs p and p + 1,
+    // then refills the stages of pairs p - 2 and p - 1, which every warp finished before the barrier
+#pragma unroll 1
+    for (int q = 0; q < NS - 2; ++q) issue(q);
+    for (int p = 0; p < a.npair; p += 2) {
+        cpa_wait<NS - 4>();
+        cta_barrier();
+        issue(p + NS - 2);
+        issue(p + NS - 1);
+        const float *s0 = sm + st_c * Sh::STG;
+        st_c = st_c + 1 == NS ? 0 : st_c + 1;
+        const float *s1 = sm + st_c * Sh::STG;
+        st_c = st_c + 1 == NS ? 0 : st_c + 1;
+        body.pair(s0 + par * Sh::OFFD, s0 + Sh::REGD + par * Sh::OFFL, b);
+        if (p + 1 < a.npair) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
+    }
+    cpa_wait<0>();
+    // u of the lane's first sample: ub + par + 16 b; x = (u + w) / 2 = ub + par + 16 b + i + o
+    body.store(a, rowoff, ub + par + 16 * b);
+}
+
+template <int NH>
+__global__ void __launch_bounds__(ImgShape<NH>::TX, FWIME_IMG_MINB) k_image_ps(const ImgArgs a, int u_lo)
+{
+    extern __shared__ float4 sm4[];
+    float *sm = reinterpret_cast<float *>(sm4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp-uniform dispatch: every warp runs the same pipeline (barriers included) with its own task
+    if (warp == 0) img_task_run<NH, 0>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 1) if (warp == 1) img_task_run<NH, 1 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 2) if (warp == 2) img_task_run<NH, 2 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 3) if (warp == 3) img_task_run<NH, 3 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 4) if (warp == 4) img_task_run<NH, 4 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+}
+
+#if FWIME_EXT_RB
 // Register-blocked imaging: a thread owns PX consecutive points x_i = xb + i and, for
 // IMG_EXT, their PX x NH image accumulators (IMG_CONTRACT: PX x NH weights p~ and PX
 // accumulators) for the whole segment.  D(x_i - h) and L(x_i + h) come from PX + NH - 1
@@ -372,6 +891,8 @@ __global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
     }
 }
 
+#endif  // FWIME_EXT_RB
+
 // Generic-nh fallback: one point per thread, accumulators in shared memory.
 template <int MODE>
 __global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
@@ -448,13 +969,29 @@ __global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
     a.img[off] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+template <int MODE>
+static cudaError_t launch_image_gen(const ImgArgs &a, cudaStream_t st)
+{
+    const int hm = (a.nh - 1) / 2;
+    size_t smem = (2 * (EXT_TX + 2 * hm) + (MODE == IMG_EXT ? a.nh * EXT_TX : 0)) * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_image_gen<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
+    k_image_gen<MODE><<<grid, EXT_TX, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#if FWIME_EXT_RB
 template <int NH, int PX, int MODE>
-static void launch_image_rb(const ImgArgs &a, cudaStream_t st)
+static void launch_image_rb(ImgArgs a, cudaStream_t st)
 {
     constexpr int HM = (NH - 1) / 2;
     constexpr int TXS = EXT_TX * PX;
     constexpr int STG = 2 * (4 * ((TXS + 2 * HM + 3) / 4) + 4);
     const size_t smem = EXT_STAGES * STG * sizeof(float);
+    a.x_lo -= (((a.x_lo - HM) % 4) + 4) % 4;   // windows start on a 16-byte boundary
     dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
     static bool attr = false;      // once per instantiation, before any launch (and any capture)
     if (!attr) {
@@ -475,20 +1012,43 @@ static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
     case 21: launch_image_rb<21, 4, MODE>(a, st); break;
     case 31: launch_image_rb<31, 2, MODE>(a, st); break;
     case 41: launch_image_rb<41, 2, MODE>(a, st); break;
-    default: {
-        const int hm = (a.nh - 1) / 2;
-        size_t smem = (2 * (EXT_TX + 2 * hm) + (MODE == IMG_EXT ? a.nh * EXT_TX : 0)) * sizeof(float);
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_image_gen<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
-        k_image_gen<MODE><<<grid, EXT_TX, smem, st>>>(a);
-    }
+    default: return launch_image_gen<MODE>(a, st);
     }
     return cudaGetLastError();
 }
+#else
+template <int NH>
+static void launch_image_ps(const ImgArgs &a, cudaStream_t st)
+{
+    using Sh = ImgShape<NH>;
+    int u_lo = a.x_lo - Sh::HM;    // first u = x - h of the physical columns, made even
+    u_lo -= ((u_lo % 2) + 2) % 2;
+    dim3 grid((a.x_hi + Sh::HM - u_lo + 255) / 256, a.z_hi - a.z_lo);
+    static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    if (!attr) {
+        cudaFuncSetAttribute(k_image_ps<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        attr = true;
+    }
+    k_image_ps<NH><<<grid, Sh::TX, Sh::SMEM, st>>>(a, u_lo);
+}
+
+template <int MODE>
+static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
+{
+    if (MODE != IMG_EXT) return launch_image_gen<MODE>(a, st);
+    switch (a.nh) {
+    case 1: launch_image_ps<1>(a, st); break;
+    case 3: launch_image_ps<3>(a, st); break;
+    case 5: launch_image_ps<5>(a, st); break;
+    case 11: launch_image_ps<11>(a, st); break;
+    case 21: launch_image_ps<21>(a, st); break;
+    case 31: launch_image_ps<31>(a, st); break;
+    case 41: launch_image_ps<41>(a, st); break;
+    default: return launch_image_gen<MODE>(a, st);
+    }
+    return cudaGetLastError();
+}
+#endif
 
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st)
 {
