@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--grad-shots", type=int, default=120)
+    ap.add_argument("--no-reuse", action="store_true",
+                    help="B~* runs its own checkpointing sweep instead of starting from the background states "
+                         "kept by the B~ of the same step")
     return ap.parse_args()
 
 
@@ -324,16 +327,20 @@ def main():
     pt = torch.from_numpy(pt_h).to(dev)
     d = torch.zeros((wl.nshot, wl.nt, wl.nrec), device=dev)
     img = torch.zeros((wl.nh, wl.nz, wl.nx), device=dev)
-    ctx = fw.Context(grid, geom, profile=1, segment=args.segment)
+    reuse = 0 if args.no_reuse else 1
+    ctx = fw.Context(grid, geom, profile=1, segment=args.segment, reuse_background=reuse)
     tuned = None
     if not args.no_tune:
         tuned = ctx.autotune(fw.OP_BORN_EXT_ADJ)    # stencil chunking measured on this batch (untimed)
     launches = [0]
 
+    reused = [0]
+
     def step(c, vv, ww, pp, dd, ii):
         c.born_ext(vv, ww, pp, dd, sync=False)
         n = c.launches
         c.born_ext_adj(vv, ww, dd, ii, sync=False)
+        reused[0] = c.get_option("background_reused")
         launches[0] += n + c.launches
         if world > 1:
             allreduce_model(ii)        # images summed over the shots of all ranks
@@ -399,13 +406,33 @@ def main():
             "config": config(wl, args, world), "roofline": roofline, "gpu_launches": launches[0],
             "clocks": clocks, "shots_per_s": shots_per_s,
             "autotune": {"stencil_rows_per_warp": tuned[0], "us_per_launch": tuned[1]} if tuned else None,
-            "executed_gupd_s": value * 5.0 / 4.0}
+            "executed_gupd_s": value * (4.0 if reused[0] else 5.0) / 4.0,
+            "background_reuse": {"used": bool(reused[0]),
+                                 "note": "B~* starts from the background states kept by the B~ of the same step "
+                                         "(4 propagations per step instead of 5); --no-reuse disables it"}}
+
+    # the same step without the background reuse (B~* with its own checkpointing sweep), one step
+    if reuse and world == 1:
+        ctx.set_option("reuse_background", 0)
+        step(ctx, v, w, pt, d, img)
+        ctx.sync()
+        torch.cuda.synchronize()
+        e0.record()
+        step(ctx, v, w, pt, d, img)
+        e1.record()
+        ctx.sync()
+        torch.cuda.synchronize()
+        ms_nr = e0.elapsed_time(e1)
+        line["no_reuse"] = {"ms_per_step": ms_nr, "value": updates_per_step(wl) / (ms_nr * 1e-3) / 1e9,
+                            "unit": UNIT, "steps": 1}
+        ctx.set_option("reuse_background", 1)
+        ctx.profile_read(reset=True)
 
     # plain path: one shot per launch, host-driven steps, same per-shot work
     if not args.no_plain and rank == 0:
         nps = 2
         geom2 = fw.Geometry(wl.src_iz[:nps], wl.src_ix[:nps], wl.rec_iz, wl.rec_ix)
-        with fw.Context(grid, geom2, plain=1) as cp:
+        with fw.Context(grid, geom2, plain=1, reuse_background=reuse) as cp:
             d2 = torch.zeros((nps, wl.nt, wl.nrec), device=dev)
             step(cp, v, w[:nps].contiguous(), pt, d2, img)
             cp.sync()

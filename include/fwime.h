@@ -90,7 +90,14 @@ enum {
     FWIME_OPT_ZCHUNK = 6,          /* rows per warp in the stencil kernel; 0 = auto */
     FWIME_OPT_LAUNCHES = 7,        /* read-only: kernels launched by the last operator call */
     FWIME_OPT_WORKSPACE = 8,       /* read-only: bytes of device workspace held */
-    FWIME_OPT_PROFILE = 9          /* 1 = bracket every kernel launch with CUDA events (no graphs) */
+    FWIME_OPT_PROFILE = 9,         /* 1 = bracket every kernel launch with CUDA events (no graphs) */
+    FWIME_OPT_REUSE_BACKGROUND = 10, /* 1 = B / B~ keep the background wavefield's segment-start states of
+                                       every shot (when they fit in device memory) and a following B* / B~*
+                                       with the SAME v and w pointers starts from them instead of its own
+                                       checkpointing sweep (one propagation fewer).  The caller guarantees
+                                       that v and w are not modified in between; any other operator call
+                                       drops the states.  0 (default) frees them. */
+    FWIME_OPT_BACKGROUND_REUSED = 11 /* read-only: 1 if the last call started from those states */
 };
 
 /* Kernel families, for fwime_profile_read. */
@@ -176,6 +183,17 @@ int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float 
  * the device.  D = diag(|ih - (nh-1)/2| + 1) as in fwime_gradient. */
 int fwime_vp_solve(fwime_ctx *ctx, const float *v, const float *w, const float *dres, float eps, int niter,
                    float *pt, double *history);
+
+/* Linear spline re-parametrisation S of the model (Theory section, Eq. 1: m lives on a coarse spline
+ * grid and the wave equation sees v = S m; gradients map back with S*, Eqs. 7-9).  Nodes zs[nzs] x xs[nxs]
+ * are host arrays in metres, strictly increasing (they may extend past the grid); the physical grid
+ * point (iz, ix) sits at (iz dz, ix dx).  Between nodes k and k+1 a point takes the weights 1 - a and a,
+ * a = (c - node_k) / (node_k+1 - node_k); beyond the end nodes it takes the end node's value (bilinear
+ * in 2-D).  adjoint = 0: out[nz][nx] (=, or += when accumulate) = S in[nzs][nxs];
+ * adjoint = 1: out[nzs][nxs] (=, or +=) = S* in[nz][nx].  in and out are device pointers;
+ * FWIME_EINVAL for unsorted or non-finite nodes. */
+int fwime_spline(fwime_ctx *ctx, int nzs, const float *zs, int nxs, const float *xs, const float *in, float *out,
+                 int adjoint, int accumulate);
 
 /* f(m) for a group of contexts at once (Eq. 1; the Computational-aspects
  * section's shots are independent): ctxs[i] has its own grid, record length

@@ -10,6 +10,7 @@ Operators (Barnier et al., Theory section): ``forward`` = f(m) (Eq. 1),
 (Eqs. 1-2, subsurface-offset extension), ``tomo``/``tomo_adj`` = T, T* (Eq. 9),
 ``gradient`` = (Phi at fixed p~, B* r + T* r) (Eqs. 1, 7-9), ``vp_solve`` =
 linear conjugate gradients for the variable projection step (Eqs. 2-5),
+``spline``/``spline_adj`` = the linear spline re-parametrisation S, S* (Eq. 1),
 ``cost_fwime`` = Eq. 11.  Primitives (``lap``, ``step``, ``step_T``, ``prop``, ``prop_T``,
 ``d2t``, ``d2t_T``, ``scatter``, ``scatter_TD``, ``scatter_TW``) are exposed
 for dot-product pins.
@@ -339,3 +340,37 @@ def vp_solve(g: Grid, v, geo: Geometry, w, dres, pt0, eps: float, niter: int):
         rr = rr_new
         hist.append(vp_objective(g, v, geo, w, dres, p, eps))
     return p, hist
+
+
+def spline_matrix(nodes, coords):
+    """Dense [len(coords)][len(nodes)] matrix of the 1-D linear spline (hat) functions on the strictly
+    increasing `nodes`, evaluated at `coords`: a point between nodes k and k+1 takes 1-a and a,
+    a = (c - node_k) / (node_k+1 - node_k); points beyond the end nodes take the end node's value."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    A = np.zeros((len(coords), len(nodes)))
+    for i, c in enumerate(np.asarray(coords, dtype=np.float64)):
+        if len(nodes) == 1 or c <= nodes[0]:
+            A[i, 0] = 1.0
+        elif c >= nodes[-1]:
+            A[i, -1] = 1.0
+        else:
+            k = int(np.searchsorted(nodes, c, side="right")) - 1
+            a = (c - nodes[k]) / (nodes[k + 1] - nodes[k])
+            A[i, k] = 1.0 - a
+            A[i, k + 1] = a
+    return A
+
+
+def spline(zs, xs, nz, nx, dz, dx, m):
+    """S m (Theory section, Eq. 1: v = S m): the model on the spline grid of node coordinates zs x xs
+    (metres) interpolated bilinearly onto the physical grid [nz][nx] at spacing dz, dx."""
+    Az = spline_matrix(zs, np.arange(nz) * dz)
+    Ax = spline_matrix(xs, np.arange(nx) * dx)
+    return Az @ np.asarray(m, dtype=np.float64) @ Ax.T
+
+
+def spline_adj(zs, xs, nz, nx, dz, dx, g):
+    """S* g: a field on the physical grid mapped to the spline nodes (the transpose of `spline`)."""
+    Az = spline_matrix(zs, np.arange(nz) * dz)
+    Ax = spline_matrix(xs, np.arange(nx) * dx)
+    return Az.T @ np.asarray(g, dtype=np.float64) @ Ax

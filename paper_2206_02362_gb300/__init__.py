@@ -27,6 +27,8 @@ FWIME_OK, FWIME_EINVAL, FWIME_ENOMEM, FWIME_ECFL, FWIME_ECUDA, FWIME_ETIMEOUT, F
 OPT_SHOTS_PER_BATCH, OPT_SEGMENT, OPT_PLAIN, OPT_GRAPH, OPT_HOST_IO, OPT_ZCHUNK, OPT_LAUNCHES, OPT_WORKSPACE = \
     1, 2, 3, 4, 5, 6, 7, 8
 OPT_PROFILE = 9
+OPT_REUSE_BACKGROUND = 10
+OPT_BACKGROUND_REUSED = 11
 K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
 KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 (OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
@@ -34,7 +36,7 @@ KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_vp_solve",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_vp_solve", "fwime_spline",
                  "fwime_autotune", "fwime_forward_group", "fwime_sync", "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
 
@@ -90,6 +92,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_vp_solve.argtypes = [vp, fp, fp, fp, ctypes.c_float, ip, fp, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_spline.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float), ip, ctypes.POINTER(ctypes.c_float), fp, fp,
+                                 ip, ip]
     lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.fwime_forward_group.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
@@ -220,14 +224,16 @@ class Context:
             self.set_option(k, v)
 
     _OPTS = {"shots_per_batch": OPT_SHOTS_PER_BATCH, "segment": OPT_SEGMENT, "plain": OPT_PLAIN,
-             "graph": OPT_GRAPH, "host_io": OPT_HOST_IO, "zchunk": OPT_ZCHUNK, "profile": OPT_PROFILE}
+             "graph": OPT_GRAPH, "host_io": OPT_HOST_IO, "zchunk": OPT_ZCHUNK, "profile": OPT_PROFILE,
+             "reuse_background": OPT_REUSE_BACKGROUND}
 
     def set_option(self, name, value):
         opt = self._OPTS[name] if isinstance(name, str) else int(name)
         self._check(self._lib.fwime_set_option(self._h, opt, int(value)), "fwime_set_option")
 
     def get_option(self, name) -> int:
-        opt = {**self._OPTS, "launches": OPT_LAUNCHES, "workspace": OPT_WORKSPACE}[name] \
+        opt = {**self._OPTS, "launches": OPT_LAUNCHES, "workspace": OPT_WORKSPACE,
+               "background_reused": OPT_BACKGROUND_REUSED}[name] \
             if isinstance(name, str) else int(name)
         v = ctypes.c_longlong(0)
         self._check(self._lib.fwime_get_option(self._h, opt, ctypes.byref(v)), "fwime_get_option")
@@ -314,6 +320,17 @@ class Context:
         self._done(self._lib.fwime_vp_solve(self._h, _ptr(v), _ptr(w), _ptr(dres), ctypes.c_float(eps), int(niter),
                                             _ptr(pt), hist), "fwime_vp_solve", sync)
         return list(hist) if sync else hist
+
+    def spline(self, zs, xs, inp, out, adjoint=False, accumulate=False, sync=True):
+        """Linear spline re-parametrisation (Eq. 1): out = S inp (model on the nodes zs x xs, metres, to the
+        physical grid) or, with adjoint, out = S* inp (grid to nodes)."""
+        z = np.ascontiguousarray(zs, dtype=np.float32)
+        x = np.ascontiguousarray(xs, dtype=np.float32)
+        P = ctypes.POINTER(ctypes.c_float)
+        self._done(self._lib.fwime_spline(self._h, len(z), z.ctypes.data_as(P), len(x), x.ctypes.data_as(P),
+                                          _ptr(inp), _ptr(out), int(bool(adjoint)), int(bool(accumulate))),
+                   "fwime_spline", sync)
+        return out
 
     def autotune(self, op: int) -> tuple[int, float]:
         """Times the stencil kernel on this operator's batch for candidate chunkings; keeps the fastest.

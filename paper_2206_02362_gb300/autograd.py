@@ -33,3 +33,27 @@ class FwimeObjective(torch.autograd.Function):
 def fwime_objective(context, v, w, pt, dobs, eps: float = 0.0):
     """Phi_eps(v) at fixed p~ as a differentiable scalar (float64)."""
     return FwimeObjective.apply(v, context, w, pt, dobs, float(eps))
+
+
+class SplineParam(torch.autograd.Function):
+    """v = S m: the model on a coarse spline grid interpolated onto the finite-difference grid (Eq. 1);
+    backward applies S*, so a gradient on the FD grid becomes a gradient on the spline nodes."""
+
+    @staticmethod
+    def forward(ctx, m, context, zs, xs):
+        g = context.grid
+        v = torch.empty((g.nz, g.nx), dtype=torch.float32, device=m.device)
+        context.spline(zs, xs, m.detach().contiguous(), v)
+        ctx.context, ctx.zs, ctx.xs, ctx.shape = context, zs, xs, m.shape
+        return v
+
+    @staticmethod
+    def backward(ctx, gv):
+        gm = torch.empty(ctx.shape, dtype=torch.float32, device=gv.device)
+        ctx.context.spline(ctx.zs, ctx.xs, gv.contiguous().to(torch.float32), gm, adjoint=True)
+        return gm, None, None, None
+
+
+def spline_param(context, zs, xs, m):
+    """S m as a differentiable map from the spline nodes zs x xs (metres) to the context's grid."""
+    return SplineParam.apply(m, context, zs, xs)

@@ -56,7 +56,18 @@ struct fwime_ctx {
     size_t max_ws = 0;
     int device = 0;
     // options
-    int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0;
+    int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0, opt_reuse_bg = 0;
+    // background-wavefield checkpoints of every shot, [nseg][2][nshot][P], written by B and B~ and
+    // read by B* and B~* on the same v, w (FWIME_OPT_REUSE_BACKGROUND)
+    struct BgCache {
+        float *buf = nullptr;
+        size_t bytes = 0;
+        bool valid = false;
+        const float *v = nullptr, *w = nullptr;
+        int K = 0;
+    } bg;
+    bool bg_written = false;        // set by the last enqueued B / B~ that filled the cache
+    bool bg_used = false;           // the last call started from the cache
     long long launches = 0;
     // persistent device memory
     int *d_src_off = nullptr, *d_rec_off = nullptr, *d_status = nullptr;
@@ -191,7 +202,7 @@ struct Sizes {
 static size_t al(size_t n) { return (n + 63) & ~(size_t)63; }   // 256-byte granules
 
 static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int NZ, int NXP, int op, int K,
-                      bool host_io)
+                      bool host_io, bool no_ckpt = false)
 {
     Sizes s;
     const size_t nh = g.nh, nseg = (size_t)((g.nt - 1 + K - 1) / K), R = K + 2;
@@ -201,8 +212,8 @@ static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int
     case FWIME_OP_FORWARD: f = 2; break;
     case FWIME_OP_BORN: s.model += al(P); f = 5; break;
     case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 4 + 2 * K; break;
-    case FWIME_OP_BORN_ADJ: s.model += al(P); f = 2 + K + R + 2 * nseg; break;
-    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + 2 * nseg; break;
+    case FWIME_OP_BORN_ADJ: s.model += al(P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
+    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
     case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
     case FWIME_OP_TOMO_ADJ:
     case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + 4 * nseg; break;
@@ -251,14 +262,14 @@ struct WS {
     float *sv, *sw, *sd1, *sd2, *sm1, *sdv, *smo;
 };
 
-static int plan(fwime_ctx *x, int op, WS &w)
+static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
 {
     w.K = x->opt_K > 0 ? x->opt_K : auto_K(x->g.nt);
     w.K = std::min(w.K, x->g.nt - 1);
     w.K = std::max(w.K, 1);
     w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;
     w.R = w.K + 2;
-    Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0);
+    Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0, no_ckpt);
     size_t budget = x->max_ws;
     if (budget == 0 && x->capturing) budget = x->ws_bytes;   // the workspace was planned before capture
     if (budget == 0) {
@@ -303,6 +314,14 @@ static int plan(fwime_ctx *x, int op, WS &w)
     auto take = [&](size_t n) { float *r = p; p += al(n); return r; };
     const long long P = x->P;
     const size_t nh = x->g.nh;
+    // host-I/O staging first: the same addresses for every operator (a staged v or w keeps its address
+    // from one call to the next as long as the arena is not reallocated)
+    w.sv = w.sw = w.sd1 = w.sd2 = w.sm1 = w.sdv = w.smo = nullptr;
+    if (x->opt_host_io) {
+        const size_t nd = (size_t)x->nshot * x->g.nt * x->nrec, nm = (size_t)x->g.nz * x->g.nx;
+        w.sv = take(nm); w.sw = take((size_t)x->nshot * x->g.nt); w.sd1 = take(nd); w.sd2 = take(nd);
+        w.sm1 = take(nh * nm); w.sdv = take(nm); w.smo = take(nh * nm);
+    }
     w.c = take(P); w.bpad = take(P); w.gz = take(x->NZ); w.gx = take(x->NXP);
     w.coef = w.W = w.W2 = w.ptp = w.acc1 = w.acc2 = nullptr;
     switch (op) {
@@ -326,7 +345,7 @@ static int plan(fwime_ctx *x, int op, WS &w)
     case FWIME_OP_BORN: nf = 5; break;
     case FWIME_OP_BORN_EXT: nf = 4; nk = 2; break;
     case FWIME_OP_BORN_ADJ:
-    case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = 2; break;
+    case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = no_ckpt ? 0 : 2; break;
     case FWIME_OP_TOMO: nf = 8; nk = 4; break;
     case FWIME_OP_OBJECTIVE: nf = 4; nk = 2; break;
     default: nf = 4; nk = 3; nr = 3; nck = 4; break;
@@ -336,12 +355,6 @@ static int plan(fwime_ctx *x, int op, WS &w)
     for (int i = 0; i < nr; ++i) w.ring[nk + i] = take((size_t)w.R * SP);
     if (nck) w.ckpt = take((size_t)w.nseg * nck * SP);
     if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
-    w.sv = w.sw = w.sd1 = w.sd2 = w.sm1 = w.sdv = w.smo = nullptr;
-    if (x->opt_host_io) {
-        const size_t nd = (size_t)x->nshot * x->g.nt * x->nrec, nm = (size_t)x->g.nz * x->g.nx;
-        w.sv = take(nm); w.sw = take((size_t)x->nshot * x->g.nt); w.sd1 = take(nd); w.sd2 = take(nd);
-        w.sm1 = take(nh * nm); w.sdv = take(nm); w.smo = take(nh * nm);
-    }
     if ((char *)p > x->ws + x->ws_bytes) return fail(x, FWIME_ENOMEM, "workspace layout overflow");
     return FWIME_OK;
 }
@@ -498,6 +511,55 @@ static int prep_model(fwime_ctx *x, Run &r, const float *v)
 
 // ------------------------------------------------------------- schedules
 
+// ---------------------------------------------------------------- background checkpoint cache
+// B and B~ propagate the background wavefield forward anyway; with FWIME_OPT_REUSE_BACKGROUND they also
+// copy its state (q^n0, q^n0-1) at every segment start n0 = j K, for every shot, into a context-owned
+// array [nseg][2][nshot][P].  B* and B~* on the same v and w then start their backward sweeps from these
+// states instead of running their own checkpointing sweep (one propagation fewer per call; the states are
+// those the sweep would compute).
+
+static int seg_K(const fwime_ctx *x)
+{
+    int K = x->opt_K > 0 ? x->opt_K : auto_K(x->g.nt);
+    return std::max(std::min(K, x->g.nt - 1), 1);
+}
+
+static size_t bg_bytes(const fwime_ctx *x, int K)
+{
+    const size_t nseg = (size_t)((x->g.nt - 1 + K - 1) / K);
+    return nseg * 2 * (size_t)x->nshot * (size_t)x->P * sizeof(float);
+}
+
+// Makes room for the cache; false when it does not fit (the call then runs without it).
+static bool bg_reserve(fwime_ctx *x, int K)
+{
+    const size_t need = bg_bytes(x, K);
+    if (x->bg.buf && x->bg.bytes >= need) return true;
+    if (x->capturing) return false;
+    if (x->max_ws && x->ws_bytes + need > x->max_ws) return false;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (need + ((size_t)4 << 30) > fr + x->bg.bytes) return false;   // leave room for the operator's workspace
+    if (x->bg.buf) cudaFreeAsync(x->bg.buf, x->st);
+    x->bg = fwime_ctx::BgCache{};
+    if (cudaMallocAsync(reinterpret_cast<void **>(&x->bg.buf), need, x->st) != cudaSuccess) {
+        cudaGetLastError();
+        x->bg.buf = nullptr;
+        return false;
+    }
+    x->bg.bytes = need;
+    return true;
+}
+
+// cache slot of state t (0: q^n0, 1: q^n0-1) of segment j for the batch starting at shot s0
+static float *bg_slot(fwime_ctx *x, int j, int t, int s0)
+{
+    return x->bg.buf + ((2LL * j + t) * x->nshot + s0) * x->P;
+}
+
 static int run_forward(fwime_ctx *x, Run &r, const float *v, const float *w, float *d)
 {
     const int nt = x->g.nt, S = r.w.S;
@@ -532,6 +594,10 @@ static int run_born(fwime_ctx *x, Run &r, const float *v, const float *w, const 
         float *db = d + s0 * nd;
         TRY(zero(x, db, sizeof(float) * Sb * nd));
         for (int n = 0; n + 1 < nt; ++n) {
+            if (x->bg_written && n % r.w.K == 0) {
+                TRY(copyf(x, bg_slot(x, n / r.w.K, 0, s0), c0, (size_t)Sb * x->P));
+                TRY(copyf(x, bg_slot(x, n / r.w.K, 1, s0), p0, (size_t)Sb * x->P));
+            }
             TRY(prop(r, Sb, c0, p0, p0, D, w + (size_t)s0 * nt + n, s0));
             TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, r.w.coef, D));
             TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
@@ -561,6 +627,10 @@ static int run_born_ext(fwime_ctx *x, Run &r, const float *v, const float *w, co
         TRY(zero(x, db, sizeof(float) * Sb * nd));
         for (int n0 = 0; n0 < nt - 1; n0 += K) {
             const int n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            if (x->bg_written) {
+                TRY(copyf(x, bg_slot(x, n0 / K, 0, s0), c0, (size_t)Sb * x->P));
+                TRY(copyf(x, bg_slot(x, n0 / K, 1, s0), p0, (size_t)Sb * x->P));
+            }
             for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, c0, p0, p0, Dr + (n - n0) * SP, w + (size_t)s0 * nt + n, s0));
                 std::swap(c0, p0);
@@ -578,7 +648,7 @@ static int run_born_ext(fwime_ctx *x, Run &r, const float *v, const float *w, co
 
 // B* (ext = false) and B~* (ext = true)
 static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const float *w, const float *d, float *out,
-                        int accumulate)
+                        int accumulate, bool use_bg)
 {
     const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
     const size_t nd = (size_t)nt * x->nrec;
@@ -594,8 +664,9 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
         TRY(zero(x, prv, fb));
         TRY(zero(x, Mu, sizeof(float) * R * SP));
         const float *ws = w + (size_t)s0 * nt;
-        // forward sweep: checkpoint (q^{n0}, q^{n0-1}) at every segment start
-        for (int j = 0; j < nseg; ++j) {
+        // checkpoint (q^{n0}, q^{n0-1}) at every segment start: from the background cache, or a forward sweep
+        auto ckp = [&](int j, int t) -> float * { return use_bg ? bg_slot(x, j, t, s0) : ck + (2LL * j + t) * SP; };
+        for (int j = 0; j < nseg && !use_bg; ++j) {
             TRY(copyf(x, ck + (2LL * j) * SP, cur, (size_t)Sb * x->P));
             TRY(copyf(x, ck + (2LL * j + 1) * SP, prv, (size_t)Sb * x->P));
             if (j == nseg - 1) break;
@@ -607,8 +678,8 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
         // backward sweep
         for (int j = nseg - 1; j >= 0; --j) {
             const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
-            TRY(copyf(x, cur, ck + (2LL * j) * SP, (size_t)Sb * x->P));
-            TRY(copyf(x, prv, ck + (2LL * j + 1) * SP, (size_t)Sb * x->P));
+            TRY(copyf(x, cur, ckp(j, 0), (size_t)Sb * x->P));
+            TRY(copyf(x, prv, ckp(j, 1), (size_t)Sb * x->P));
             for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, cur, prv, prv, Dr + (n - n0) * SP, ws + n, s0));
                 std::swap(cur, prv);
@@ -819,18 +890,43 @@ struct Call {
     float eps;
 };
 
+static bool is_bg_writer(int op) { return op == FWIME_OP_BORN || op == FWIME_OP_BORN_EXT; }
+static bool is_bg_reader(int op) { return op == FWIME_OP_BORN_ADJ || op == FWIME_OP_BORN_EXT_ADJ; }
+
+// does this call start from the cached background checkpoints?
+static bool bg_usable(const fwime_ctx *x, const Call &c)
+{
+    return is_bg_reader(c.op) && x->opt_reuse_bg && x->bg.valid && x->bg.v == c.v && x->bg.w == c.w &&
+           x->bg.K == seg_K(x) && x->bg.buf;
+}
+
+// host-side bookkeeping once a call has been enqueued (directly or as a graph replay)
+static void bg_after(fwime_ctx *x, const Call &c, bool wrote)
+{
+    if (is_bg_writer(c.op)) {
+        x->bg.valid = wrote;
+        x->bg.v = c.v; x->bg.w = c.w; x->bg.K = seg_K(x);
+    } else if (!is_bg_reader(c.op)) {
+        x->bg.valid = false;
+    }
+}
+
 static int enqueue(fwime_ctx *x, const Call &c)
 {
     Run r;
-    TRY(plan(x, c.op, r.w));
+    const bool use_bg = bg_usable(x, c);
+    x->bg_used = use_bg;
+    x->bg_written = is_bg_writer(c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
+    if (x->bg_written) x->bg.valid = false;   // being overwritten
+    TRY(plan(x, c.op, r.w, use_bg));
     init_run(x, r, r.w.S);
     TRY(prep_model(x, r, c.v));
     switch (c.op) {
     case FWIME_OP_FORWARD: return run_forward(x, r, c.v, c.w, c.out);
     case FWIME_OP_BORN: return run_born(x, r, c.v, c.w, c.in1, c.out);
-    case FWIME_OP_BORN_ADJ: return run_born_adj(x, r, false, c.v, c.w, c.in1, c.out, c.accumulate);
+    case FWIME_OP_BORN_ADJ: return run_born_adj(x, r, false, c.v, c.w, c.in1, c.out, c.accumulate, use_bg);
     case FWIME_OP_BORN_EXT: return run_born_ext(x, r, c.v, c.w, c.in1, c.out);
-    case FWIME_OP_BORN_EXT_ADJ: return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate);
+    case FWIME_OP_BORN_EXT_ADJ: return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate, use_bg);
     case FWIME_OP_TOMO: return run_tomo(x, r, c.v, c.w, c.in1, c.in2, c.out);
     case FWIME_OP_TOMO_ADJ: return run_tomo_adj(x, r, 0, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, 0.f);
     case FWIME_OP_GRADIENT: return run_tomo_adj(x, r, 1, c.v, c.w, c.in1, c.in2, c.out, 0, c.eps);
@@ -839,22 +935,31 @@ static int enqueue(fwime_ctx *x, const Call &c)
     return fail(x, FWIME_EINVAL, "unknown operator %d", c.op);
 }
 
+static int enqueue_noted(fwime_ctx *x, const Call &c)
+{
+    const int rc = enqueue(x, c);
+    if (rc == FWIME_OK) bg_after(x, c, x->bg_written);
+    return rc;
+}
+
 static int run_call(fwime_ctx *x, const Call &c)
 {
     if (!x->opt_graph || x->opt_plain || x->opt_profile) {
         x->launches = 0;
-        return enqueue(x, c);
+        return enqueue_noted(x, c);
     }
     if (x->st == nullptr) return fail(x, FWIME_EINVAL, "graph mode needs a non-default stream");
-    // plan first so the workspace never grows inside a capture
+    // plan (and reserve the background cache) first so that no allocation happens inside a capture
+    const bool use_bg = bg_usable(x, c);
+    const bool write_bg = is_bg_writer(c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
     {
         WS w;
-        TRY(plan(x, c.op, w));
+        TRY(plan(x, c.op, w, use_bg));
     }
-    char key[256];
-    snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d", c.op, (const void *)c.v, (const void *)c.w,
+    char key[320];
+    snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d|%d%d|%p", c.op, (const void *)c.v, (const void *)c.w,
              (const void *)c.in1, (const void *)c.in2, (void *)c.out, c.accumulate, (double)c.eps, x->opt_S, x->opt_K,
-             x->opt_zchunk);
+             x->opt_zchunk, use_bg ? 1 : 0, write_bg ? 1 : 0, (const void *)(use_bg || write_bg ? x->bg.buf : nullptr));
     auto it = x->graphs.find(key);
     if (it == x->graphs.end()) {
         CK(cudaStreamBeginCapture(x->st, cudaStreamCaptureModeThreadLocal));
@@ -878,6 +983,8 @@ static int run_call(fwime_ctx *x, const Call &c)
     }
     x->launches = it->second.launches;
     CK(cudaGraphLaunch(it->second.exec, x->st));
+    x->bg_used = use_bg;
+    bg_after(x, c, write_bg);
     return FWIME_OK;
 }
 
@@ -889,8 +996,17 @@ static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
     if (!x) return FWIME_EINVAL;
     if (!c.v || !c.w || (!c.out && c.op != FWIME_OP_OBJECTIVE)) return fail(x, FWIME_EINVAL, "null pointer argument");
     if (!x->opt_host_io) return run_call(x, c);
+    // the staged v and w sit at the start of the arena: a B~* can reuse the background of the B~ before it
+    // (FWIME_OPT_REUSE_BACKGROUND) when the arena has not moved in between
+    auto staged = [&](Call s) {
+        s.v = reinterpret_cast<const float *>(x->ws);
+        s.w = reinterpret_cast<const float *>(x->ws) + al((size_t)x->g.nz * x->g.nx);
+        return s;
+    };
+    bool use_bg = x->ws && bg_usable(x, staged(c));
     WS w;
-    TRY(plan(x, c.op, w));
+    TRY(plan(x, c.op, w, use_bg));
+    if (use_bg && !bg_usable(x, staged(c))) TRY(plan(x, c.op, w, false));   // the arena moved
     const size_t nm = (size_t)x->g.nz * x->g.nx, nd = (size_t)x->nshot * x->g.nt * x->nrec;
     auto count = [&](int k) -> size_t {
         return k == K_DATA ? nd : (k == K_MODEL ? nm : (k == K_EXT ? (size_t)x->g.nh * nm : 0));
@@ -908,7 +1024,7 @@ static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
     float *user_out = c.out;
     c.v = w.sv; c.w = w.sw; c.in1 = in1; c.in2 = in2; c.out = out;
     x->launches = 0;
-    TRY(enqueue(x, c));
+    TRY(enqueue_noted(x, c));
     if (kout != K_NONE) CK(cudaMemcpyAsync(user_out, out, count(kout) * sizeof(float), cudaMemcpyDeviceToHost, x->st));
     return fwime_sync(x);
 }
@@ -1008,6 +1124,7 @@ void fwime_destroy(fwime_ctx *x)
     if (x->ws) cudaFreeAsync(x->ws, x->st);
     if (x->small) cudaFreeAsync(x->small, x->st);
     if (x->vp_hist_dev) cudaFreeAsync(x->vp_hist_dev, x->st);
+    if (x->bg.buf) cudaFreeAsync(x->bg.buf, x->st);
     cudaGetLastError();
     delete x;
 }
@@ -1024,6 +1141,14 @@ int fwime_set_option(fwime_ctx *x, int option, long long value)
     case FWIME_OPT_HOST_IO: x->opt_host_io = value != 0; return FWIME_OK;
     case FWIME_OPT_ZCHUNK: if (value < 0 || value > 4096) break; x->opt_zchunk = (int)value; return FWIME_OK;
     case FWIME_OPT_PROFILE: x->opt_profile = value != 0; return FWIME_OK;
+    case FWIME_OPT_REUSE_BACKGROUND:
+        x->opt_reuse_bg = value != 0;
+        x->bg.valid = false;
+        if (!x->opt_reuse_bg && x->bg.buf) {   // give the memory back
+            cudaFreeAsync(x->bg.buf, x->st);
+            x->bg = fwime_ctx::BgCache{};
+        }
+        return FWIME_OK;
     default: break;
     }
     return fail(x, FWIME_EINVAL, "bad option %d = %lld", option, value);
@@ -1042,6 +1167,8 @@ int fwime_get_option(fwime_ctx *x, int option, long long *value)
     case FWIME_OPT_LAUNCHES: *value = x->launches; return FWIME_OK;
     case FWIME_OPT_WORKSPACE: *value = (long long)x->ws_bytes; return FWIME_OK;
     case FWIME_OPT_PROFILE: *value = x->opt_profile; return FWIME_OK;
+    case FWIME_OPT_REUSE_BACKGROUND: *value = x->opt_reuse_bg; return FWIME_OK;
+    case FWIME_OPT_BACKGROUND_REUSED: *value = x->bg_used; return FWIME_OK;
     }
     return fail(x, FWIME_EINVAL, "bad option %d", option);
 }
@@ -1132,8 +1259,8 @@ int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dr
     };
     // H q = B~* B~ q + eps^2 D^2 q  (Eq. 3)
     auto apply_H = [&](const float *q, float *out) -> int {
-        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT, v, w, q, nullptr, dtmp, 0, 0.f}));
-        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, out, 0, 0.f}));
+        TRY(enqueue_noted(x, Call{FWIME_OP_BORN_EXT, v, w, q, nullptr, dtmp, 0, 0.f}));
+        TRY(enqueue_noted(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, out, 0, 0.f}));
         LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_dso_add(q, out, x->g.nh, PP, eps2, x->st));
         return FWIME_OK;
     };
@@ -1147,12 +1274,12 @@ int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dr
         const double consts[8] = {0, 0, 0, 0, 0, 0, 1.0, -1.0};   // sc[6] = 1, sc[7] = -1
         CK(cudaMemcpyAsync(sc, consts, sizeof(consts), cudaMemcpyHostToDevice, x->st));
         // r0 = B~* (dres - B~ p0) - eps^2 D^2 p0,  Phi(p0) = 1/2 ||B~ p0 - dres||^2 + eps^2/2 ||D p0||^2
-        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT, v, w, pt, nullptr, dtmp, 0, 0.f}));
+        TRY(enqueue_noted(x, Call{FWIME_OP_BORN_EXT, v, w, pt, nullptr, dtmp, 0, 0.f}));
         LAUNCH(FWIME_K_OTHER, 12.0 * nd, launch_axpby_dev(dtmp, dres, (long long)nd, sc, 6, 1.f, 7, x->st));   // dres - B~ p0
         TRY(dot(dtmp, dtmp, nd, sc + 5, 0.5, 0));
         LAUNCH(FWIME_K_OTHER, 4.0 * nm, launch_dso(pt, x->g.nh, PP, x->d_part, nred, x->st));
         LAUNCH(FWIME_K_OTHER, 8.0, launch_sum_partials(x->d_part, nred, sc + 5, 1, 0.5 * (double)eps2, x->st));
-        TRY(enqueue(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, r, 0, 0.f}));
+        TRY(enqueue_noted(x, Call{FWIME_OP_BORN_EXT_ADJ, v, w, dtmp, nullptr, r, 0, 0.f}));
         LAUNCH(FWIME_K_OTHER, 12.0 * nm, launch_dso_add(pt, r, x->g.nh, PP, -eps2, x->st));
         CK(cudaMemcpyAsync(pdir, r, nm * sizeof(float), cudaMemcpyDeviceToDevice, x->st));
         TRY(dot(r, r, nm, sc + 0, 1.0, 0));
@@ -1169,7 +1296,16 @@ int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dr
         }
         return FWIME_OK;
     };
+    // v and w cannot change during the solve: every B~* starts from the checkpoints of the B~ before it
+    const int saved_reuse = x->opt_reuse_bg;
+    x->opt_reuse_bg = 1;
     const int rc = solve();
+    x->opt_reuse_bg = saved_reuse;
+    x->bg.valid = false;
+    if (!saved_reuse && x->bg.buf) {
+        cudaFreeAsync(x->bg.buf, x->st);
+        x->bg = fwime_ctx::BgCache{};
+    }
     for (void *q : {(void *)r, (void *)pdir, (void *)hp, (void *)dtmp, (void *)sc})
         if (q) cudaFreeAsync(q, x->st);
     if (rc != FWIME_OK) {
@@ -1181,6 +1317,37 @@ int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dr
     x->vp_hist_user = history;
     x->vp_hist_n = niter + 1;
     return FWIME_OK;
+}
+
+int fwime_spline(fwime_ctx *x, int nzs, const float *zs, int nxs, const float *xs, const float *in, float *out,
+                 int adjoint, int accumulate)
+{
+    if (!x) return FWIME_EINVAL;
+    if (nzs < 1 || nxs < 1 || !zs || !xs || !in || !out) return fail(x, FWIME_EINVAL, "spline arguments");
+    if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "spline takes device pointers, no capture");
+    for (int i = 0; i < nzs; ++i)
+        if (!std::isfinite(zs[i]) || (i && !(zs[i] > zs[i - 1]))) return fail(x, FWIME_EINVAL, "zs must increase");
+    for (int i = 0; i < nxs; ++i)
+        if (!std::isfinite(xs[i]) || (i && !(xs[i] > xs[i - 1]))) return fail(x, FWIME_EINVAL, "xs must increase");
+    x->launches = 0;
+    float *dn = nullptr;
+    const size_t nn = (size_t)nzs + nxs, nt = adjoint ? (size_t)x->g.nz * nxs : 0;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&dn), (nn + nt) * sizeof(float), x->st));
+    int rc = FWIME_OK;
+    cudaError_t e = cudaMemcpyAsync(dn, zs, nzs * sizeof(float), cudaMemcpyHostToDevice, x->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dn + nzs, xs, nxs * sizeof(float), cudaMemcpyHostToDevice, x->st);
+    if (e != cudaSuccess) rc = fail(x, FWIME_ECUDA, "spline nodes: %s", cudaGetErrorString(e));
+    if (rc == FWIME_OK) {
+        auto go = [&]() -> int {
+            LAUNCH(FWIME_K_OTHER, 4.0 * ((double)x->g.nz * x->g.nx + (double)nzs * nxs) * (adjoint ? 2 : 1),
+                   launch_spline(dn, nzs, dn + nzs, nxs, x->g.nz, x->g.nx, x->g.dz, x->g.dx, in, out,
+                                 dn + nn, adjoint, accumulate, x->st));
+            return FWIME_OK;
+        };
+        rc = go();
+    }
+    cudaFreeAsync(dn, x->st);
+    return rc;
 }
 
 int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, const float *const *w, float *const *d)

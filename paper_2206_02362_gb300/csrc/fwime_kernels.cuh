@@ -148,6 +148,9 @@ cudaError_t launch_sum_partials(const double *partials, int n, double *out, int 
                                 cudaStream_t st);
 cudaError_t launch_dso(const float *pt, int nh, long long PP, double *partials, int nblocks, cudaStream_t st);
 cudaError_t launch_copy_fields(float *dst, const float *src, long long n, cudaStream_t st);
+// linear spline re-parametrisation: out = S in (adjoint = 0) or S* in (tmp: nz * nxs floats)
+cudaError_t launch_spline(const float *zs, int nzs, const float *xs, int nxs, int nz, int nx, float dz, float dx,
+                          const float *in, float *out, float *tmp, int adjoint, int accumulate, cudaStream_t st);
 // VP conjugate gradients (device scalars)
 cudaError_t launch_dot(const float *x, const float *y, long long n, double *partials, int nblocks, double *out,
                        int accumulate, double scale, cudaStream_t st);
