@@ -7,7 +7,8 @@ CUDA path in ``paper_2206_02362_gb300``.
 
 Operators (Barnier et al., Theory section): ``forward`` = f(m) (Eq. 1),
 ``born``/``born_adj`` = B, B* (Eq. 8), ``born_ext``/``born_ext_adj`` = B~, B~*
-(Eqs. 1-2, subsurface-offset extension), ``tomo``/``tomo_adj`` = T, T* (Eq. 9),
+(Eqs. 1-2; subsurface-offset extension, or the time-lag extension when
+``Grid.lag`` > 0), ``tomo``/``tomo_adj`` = T, T* (Eq. 9),
 ``gradient`` = (Phi at fixed p~, B* r + T* r) (Eqs. 1, 7-9), ``vp_solve`` =
 linear conjugate gradients for the variable projection step (Eqs. 2-5),
 ``spline``/``spline_adj`` = the linear spline re-parametrisation S, S* (Eq. 1),
@@ -50,7 +51,7 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("W", ctypes.c_int),
                 ("nt", ctypes.c_int), ("nh", ctypes.c_int),
-                ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("lag", ctypes.c_int)]
 
 
 class _Shot(ctypes.Structure):
@@ -81,7 +82,8 @@ def _L():
 
 @dataclass(frozen=True)
 class Grid:
-    """Physical grid nz x nx at spacing dz, dx; sponge W points; nt samples at dt; nh offsets."""
+    """Physical grid nz x nx at spacing dz, dx; sponge W points; nt samples at dt; nh extension points:
+    subsurface offsets (lag = 0) or time lags spaced lag * dt (lag > 0; B~ and B~* only)."""
     nz: int
     nx: int
     W: int
@@ -90,6 +92,7 @@ class Grid:
     dx: float
     dz: float | None = None
     nh: int = 1
+    lag: int = 0
 
     @property
     def NZ(self) -> int:
@@ -105,7 +108,7 @@ class Grid:
 
     def c(self) -> _Grid:
         dz = self.dx if self.dz is None else self.dz
-        return _Grid(self.nz, self.nx, self.W, self.nt, self.nh, float(dz), float(self.dx), float(self.dt))
+        return _Grid(self.nz, self.nx, self.W, self.nt, self.nh, float(dz), float(self.dx), float(self.dt), self.lag)
 
 
 def _d(a):

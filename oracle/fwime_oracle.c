@@ -31,6 +31,9 @@
  *   Born   secondary source b dv D2t q0, b = 2/v^3 (d c / d v = c b v).
  *   ext.   e^n(y) = sum_h W(y-h,h) D^n(y-2h), W = b p~, h along x, nh odd,
  *          terms whose points leave the active region dropped.
+ *   lags   (lag > 0) e^n(x) = sum_i W(x,i) D^{n-2 s_i}(x), s_i = (i-hm) lag, D^m = 0
+ *          outside 0 <= m <= nt-2: lag tau couples the source side at t - tau
+ *          with the receiver side at t + tau.
  *   adj.   the literal transpose of each primitive, composed in reverse.
  * Everything is double precision, sequential loops, no reordering of sums
  * beyond the loop order written here (compile with -ffp-contract=off).
@@ -43,8 +46,9 @@ typedef struct {
     int nz, nx;       /* physical grid */
     int W;            /* sponge width in points */
     int nt;           /* number of time samples */
-    int nh;           /* number of subsurface offsets (odd) */
+    int nh;           /* number of extension points (odd): subsurface offsets, or time lags */
     double dz, dx, dt;
+    int lag;          /* 0: subsurface-offset extension; > 0: time-lag extension, lags spaced lag*dt */
 } og_grid;
 
 /* ------------------------------------------------------------------ grid */
@@ -494,6 +498,72 @@ void og_born_ext_adj(const og_grid *g, const double *v, const og_shot *sh, const
 }
 
 /*
+ * Time-lag extension (Theory section: B~ is Born modelling extended with time
+ * lags or with horizontal subsurface offsets, Eq. 1).  Symmetric convention:
+ * lag tau_i = s_i dt, s_i = (i - hm) lag, couples the source wavefield at
+ * t - tau with the receiver side at t + tau, so the secondary source of step n
+ * reads the background's D2t 2 s_i steps earlier:
+ *   e^n(x) = sum_i W(x, i) D^{n - 2 s_i}(x),   W = b p~,   D^m = 0 unless 0 <= m <= nt-2.
+ * Overwrites e (physical points only carry weights).
+ */
+void og_scatter_tlag(const og_grid *g, const double *Wt, const double *D_seq, int n, double *e)
+{
+    int NX = og_NX(g), o = og_pad(g), hm = (g->nh - 1) / 2;
+    size_t P = (size_t)og_NZ(g) * NX, PP = (size_t)g->nz * g->nx;
+    memset(e, 0, P * sizeof(double));
+    for (int i = 0; i < g->nh; i++) {
+        int m = n - 2 * (i - hm) * g->lag;
+        if (m < 0 || m > g->nt - 2) continue;
+        const double *D = D_seq + (size_t)m * P;
+        for (int iz = 0; iz < g->nz; iz++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                size_t at = (size_t)(iz + o) * NX + ix + o;
+                e[at] += Wt[i * PP + (size_t)iz * g->nx + ix] * D[at];
+            }
+    }
+}
+
+/* B~(m) p~ with the time-lag extension: scatter every step, propagate, record */
+void og_born_tlag(const og_grid *g, const double *v, const og_shot *sh, const double *pt, double *d)
+{
+    model_t m; model_init(g, v, &m);
+    size_t P = m.P;
+    double *q0, *D0; background(g, &m, sh, &q0, &D0);
+    double *Wt = ext_weights(g, &m, pt);
+    double *s = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
+    for (int n = 0; n + 1 < g->nt; n++) og_scatter_tlag(g, Wt, D0, n, s + (size_t)n * P);
+    double *dq = (double *)malloc((size_t)g->nt * P * sizeof(double));
+    og_prop(g, m.c, m.gam, s, dq);
+    record_seq(g, sh, dq, d);
+    free(q0); free(D0); free(Wt); free(s); free(dq); model_free(&m);
+}
+
+/* B~*(m) d with the time-lag extension: pt[i][x] = b(x) sum_n D0^{n - 2 s_i}(x) s*^n(x) */
+void og_born_tlag_adj(const og_grid *g, const double *v, const og_shot *sh, const double *d, double *pt)
+{
+    model_t m; model_init(g, v, &m);
+    size_t P = m.P, PP = m.PP;
+    int NX = og_NX(g), o = og_pad(g), hm = (g->nh - 1) / 2;
+    double *q0, *D0; background(g, &m, sh, &q0, &D0);
+    double *a = inject_seq(g, sh, d);
+    double *ss = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
+    og_prop_T(g, m.c, m.gam, a, ss);
+    for (int i = 0; i < g->nh; i++)
+        for (int iz = 0; iz < g->nz; iz++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                size_t at = (size_t)(iz + o) * NX + ix + o;
+                double acc = 0.0;
+                for (int n = 0; n + 1 < g->nt; n++) {
+                    int mm = n - 2 * (i - hm) * g->lag;
+                    if (mm < 0 || mm > g->nt - 2) continue;
+                    acc += D0[(size_t)mm * P + at] * ss[(size_t)n * P + at];
+                }
+                pt[i * PP + (size_t)iz * g->nx + ix] = m.b[(size_t)iz * g->nx + ix] * acc;
+            }
+    free(q0); free(D0); free(a); free(ss); model_free(&m);
+}
+
+/*
  * T(m, p~) dv: derivative of m -> B~(m) p~ along dv (Eq. 9 operator).  Three
  * secondary sources drive one more propagation:
  *   (i)   b dv D2t dqs           dqs = extended Born wavefield of p~
@@ -701,8 +771,11 @@ double og_shots(const og_grid *g, int op, const double *v, int nshot, const int 
         case OP_FWD: og_forward(g, v, &sh, o); break;
         case OP_BORN: og_born(g, v, &sh, in1, o); break;
         case OP_BORN_ADJ: og_born_adj(g, v, &sh, ds, o); break;
-        case OP_EXT: og_born_ext(g, v, &sh, in1, o); break;
-        case OP_EXT_ADJ: og_born_ext_adj(g, v, &sh, ds, o); break;
+        case OP_EXT: if (g->lag > 0) og_born_tlag(g, v, &sh, in1, o); else og_born_ext(g, v, &sh, in1, o); break;
+        case OP_EXT_ADJ:
+            if (g->lag > 0) og_born_tlag_adj(g, v, &sh, ds, o);
+            else og_born_ext_adj(g, v, &sh, ds, o);
+            break;
         case OP_TOMO: og_tomo(g, v, &sh, in1, in2 ? in2 : NULL, o); break;
         case OP_TOMO_ADJ: og_tomo_adj(g, v, &sh, in1, ds, o); break;
         case OP_GRAD: Js[s] = og_gradient(g, v, &sh, in1, ds, o, NULL); break;
