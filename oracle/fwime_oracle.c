@@ -467,6 +467,73 @@ void og_born_adj(const og_grid *g, const double *v, const og_shot *sh, const dou
 }
 
 /* B~(m) p~: extended Born (subsurface offsets) */
+/* Transpose of og_scatter_tlag w.r.t. D: z^m(x) = sum_i W(x, i) es^{m + 2 s_i}(x).  Overwrites z. */
+void og_scatter_tlag_TD(const og_grid *g, const double *Wt, const double *es_seq, int m, double *z)
+{
+    int NX = og_NX(g), o = og_pad(g), hm = (g->nh - 1) / 2;
+    size_t P = (size_t)og_NZ(g) * NX, PP = (size_t)g->nz * g->nx;
+    memset(z, 0, P * sizeof(double));
+    for (int i = 0; i < g->nh; i++) {
+        int n = m + 2 * (i - hm) * g->lag;
+        if (n < 0 || n > g->nt - 2) continue;
+        const double *es = es_seq + (size_t)n * P;
+        for (int iz = 0; iz < g->nz; iz++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                size_t at = (size_t)(iz + o) * NX + ix + o;
+                z[at] += Wt[i * PP + (size_t)iz * g->nx + ix] * es[at];
+            }
+    }
+}
+
+/* Transpose of og_scatter_tlag w.r.t. W, accumulated: Ws(x, i) += sum_n D^{n - 2 s_i}(x) es^n(x) */
+void og_scatter_tlag_TW_acc(const og_grid *g, const double *D_seq, const double *es_seq, double *Ws)
+{
+    int NX = og_NX(g), o = og_pad(g), hm = (g->nh - 1) / 2;
+    size_t P = (size_t)og_NZ(g) * NX, PP = (size_t)g->nz * g->nx;
+    for (int i = 0; i < g->nh; i++)
+        for (int iz = 0; iz < g->nz; iz++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                size_t at = (size_t)(iz + o) * NX + ix + o;
+                double acc = 0.0;
+                for (int n = 0; n + 1 < g->nt; n++) {
+                    int mm = n - 2 * (i - hm) * g->lag;
+                    if (mm < 0 || mm > g->nt - 2) continue;
+                    acc += D_seq[(size_t)mm * P + at] * es_seq[(size_t)n * P + at];
+                }
+                Ws[i * PP + (size_t)iz * g->nx + ix] += acc;
+            }
+}
+
+void og_scatter_tlag(const og_grid *g, const double *Wt, const double *D_seq, int n, double *e);
+
+/* The extension over whole sequences (steps 0..nt-2): subsurface offsets (lag = 0) or time lags */
+static void ext_scatter_seq(const og_grid *g, const double *Wt, const double *D_seq, double *e_seq)
+{
+    size_t P = (size_t)og_NZ(g) * og_NX(g);
+    for (int n = 0; n + 1 < g->nt; n++) {
+        if (g->lag > 0) og_scatter_tlag(g, Wt, D_seq, n, e_seq + (size_t)n * P);
+        else og_scatter(g, Wt, D_seq + (size_t)n * P, e_seq + (size_t)n * P);
+    }
+}
+static void ext_scatter_TD_seq(const og_grid *g, const double *Wt, const double *es_seq, double *z_seq)
+{
+    size_t P = (size_t)og_NZ(g) * og_NX(g);
+    for (int n = 0; n + 1 < g->nt; n++) {
+        if (g->lag > 0) og_scatter_tlag_TD(g, Wt, es_seq, n, z_seq + (size_t)n * P);
+        else og_scatter_TD(g, Wt, es_seq + (size_t)n * P, z_seq + (size_t)n * P);
+    }
+}
+static void ext_scatter_TW_seq(const og_grid *g, const double *D_seq, const double *es_seq, double *Ws)
+{
+    size_t P = (size_t)og_NZ(g) * og_NX(g);
+    if (g->lag > 0) {
+        og_scatter_tlag_TW_acc(g, D_seq, es_seq, Ws);
+        return;
+    }
+    for (int n = 0; n + 1 < g->nt; n++) og_scatter_TW_acc(g, D_seq + (size_t)n * P, es_seq + (size_t)n * P, Ws);
+}
+
+/* B~(m) p~ (either extension): scatter every step, propagate, record */
 void og_born_ext(const og_grid *g, const double *v, const og_shot *sh, const double *pt, double *d)
 {
     model_t m; model_init(g, v, &m);
@@ -474,14 +541,15 @@ void og_born_ext(const og_grid *g, const double *v, const og_shot *sh, const dou
     double *q0, *D0; background(g, &m, sh, &q0, &D0);
     double *Wt = ext_weights(g, &m, pt);
     double *s = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
-    for (int n = 0; n + 1 < g->nt; n++) og_scatter(g, Wt, D0 + (size_t)n * P, s + (size_t)n * P);
+    ext_scatter_seq(g, Wt, D0, s);
     double *dq = (double *)malloc((size_t)g->nt * P * sizeof(double));
     og_prop(g, m.c, m.gam, s, dq);
     record_seq(g, sh, dq, d);
     free(q0); free(D0); free(Wt); free(s); free(dq); model_free(&m);
 }
 
-/* B~*(m) d: extended imaging condition, pt[nh][nz][nx] = b(x) sum_n D0^n(x-h) s*^n(x+h) */
+/* B~*(m) d: extended imaging condition, pt[nh][nz][nx] = b(x) sum_n D0^n(x-h) s*^n(x+h) (offsets) or
+ * b(x) sum_n D0^{n - 2 s_i}(x) s*^n(x) (time lags) */
 void og_born_ext_adj(const og_grid *g, const double *v, const og_shot *sh, const double *d, double *pt)
 {
     model_t m; model_init(g, v, &m);
@@ -491,7 +559,7 @@ void og_born_ext_adj(const og_grid *g, const double *v, const og_shot *sh, const
     double *ss = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
     og_prop_T(g, m.c, m.gam, a, ss);
     double *Ws = (double *)calloc((size_t)g->nh * PP, sizeof(double));
-    for (int n = 0; n + 1 < g->nt; n++) og_scatter_TW_acc(g, D0 + (size_t)n * P, ss + (size_t)n * P, Ws);
+    ext_scatter_TW_seq(g, D0, ss, Ws);
     for (int ih = 0; ih < g->nh; ih++)
         for (size_t i = 0; i < PP; i++) pt[ih * PP + i] = m.b[i] * Ws[ih * PP + i];
     free(q0); free(D0); free(a); free(ss); free(Ws); model_free(&m);
@@ -523,46 +591,6 @@ void og_scatter_tlag(const og_grid *g, const double *Wt, const double *D_seq, in
     }
 }
 
-/* B~(m) p~ with the time-lag extension: scatter every step, propagate, record */
-void og_born_tlag(const og_grid *g, const double *v, const og_shot *sh, const double *pt, double *d)
-{
-    model_t m; model_init(g, v, &m);
-    size_t P = m.P;
-    double *q0, *D0; background(g, &m, sh, &q0, &D0);
-    double *Wt = ext_weights(g, &m, pt);
-    double *s = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
-    for (int n = 0; n + 1 < g->nt; n++) og_scatter_tlag(g, Wt, D0, n, s + (size_t)n * P);
-    double *dq = (double *)malloc((size_t)g->nt * P * sizeof(double));
-    og_prop(g, m.c, m.gam, s, dq);
-    record_seq(g, sh, dq, d);
-    free(q0); free(D0); free(Wt); free(s); free(dq); model_free(&m);
-}
-
-/* B~*(m) d with the time-lag extension: pt[i][x] = b(x) sum_n D0^{n - 2 s_i}(x) s*^n(x) */
-void og_born_tlag_adj(const og_grid *g, const double *v, const og_shot *sh, const double *d, double *pt)
-{
-    model_t m; model_init(g, v, &m);
-    size_t P = m.P, PP = m.PP;
-    int NX = og_NX(g), o = og_pad(g), hm = (g->nh - 1) / 2;
-    double *q0, *D0; background(g, &m, sh, &q0, &D0);
-    double *a = inject_seq(g, sh, d);
-    double *ss = (double *)malloc((size_t)(g->nt - 1) * P * sizeof(double));
-    og_prop_T(g, m.c, m.gam, a, ss);
-    for (int i = 0; i < g->nh; i++)
-        for (int iz = 0; iz < g->nz; iz++)
-            for (int ix = 0; ix < g->nx; ix++) {
-                size_t at = (size_t)(iz + o) * NX + ix + o;
-                double acc = 0.0;
-                for (int n = 0; n + 1 < g->nt; n++) {
-                    int mm = n - 2 * (i - hm) * g->lag;
-                    if (mm < 0 || mm > g->nt - 2) continue;
-                    acc += D0[(size_t)mm * P + at] * ss[(size_t)n * P + at];
-                }
-                pt[i * PP + (size_t)iz * g->nx + ix] = m.b[(size_t)iz * g->nx + ix] * acc;
-            }
-    free(q0); free(D0); free(a); free(ss); model_free(&m);
-}
-
 /*
  * T(m, p~) dv: derivative of m -> B~(m) p~ along dv (Eq. 9 operator).  Three
  * secondary sources drive one more propagation:
@@ -591,18 +619,20 @@ void og_tomo(const og_grid *g, const double *v, const og_shot *sh, const double 
     og_prop(g, m.c, m.gam, s, dq0);
     og_d2t(g, dq0, Dq0);
     /* dqs: extended Born wavefield of p~ */
-    for (int n = 0; n + 1 < g->nt; n++) og_scatter(g, Wt, D0 + (size_t)n * P, s + (size_t)n * P);
+    ext_scatter_seq(g, Wt, D0, s);
     og_prop(g, m.c, m.gam, s, dqs);
     og_d2t(g, dqs, Dqs);
     /* the three secondary sources of T dv */
+    double *e2 = (double *)malloc(SP * sizeof(double)), *e3 = (double *)malloc(SP * sizeof(double));
+    ext_scatter_seq(g, W2, D0, e2);
+    ext_scatter_seq(g, Wt, Dq0, e3);
     for (int n = 0; n + 1 < g->nt; n++) {
         double *sn = s + (size_t)n * P;
         for (size_t p = 0; p < P; p++) sn[p] = m.bpad[p] * dvp[p] * Dqs[(size_t)n * P + p];
-        og_scatter(g, W2, D0 + (size_t)n * P, tmp);
-        for (size_t p = 0; p < P; p++) sn[p] += tmp[p];
-        og_scatter(g, Wt, Dq0 + (size_t)n * P, tmp);
-        for (size_t p = 0; p < P; p++) sn[p] += tmp[p];
+        for (size_t p = 0; p < P; p++) sn[p] += e2[(size_t)n * P + p];
+        for (size_t p = 0; p < P; p++) sn[p] += e3[(size_t)n * P + p];
     }
+    free(e2); free(e3);
     double *dqt = (double *)malloc(QP * sizeof(double));
     og_prop(g, m.c, m.gam, s, dqt);
     record_seq(g, sh, dqt, d);
@@ -627,7 +657,7 @@ static void tomo_adj_core(const og_grid *g, const double *v, const model_t *m, c
     double *Wt = ext_weights(g, m, pt);
     double *s = (double *)malloc(SP * sizeof(double));
     double *dqs = (double *)malloc(QP * sizeof(double)), *Dqs = (double *)malloc(SP * sizeof(double));
-    for (int n = 0; n + 1 < nt; n++) og_scatter(g, Wt, D0 + (size_t)n * P, s + (size_t)n * P);
+    ext_scatter_seq(g, Wt, D0, s);
     og_prop(g, m->c, m->gam, s, dqs);
     og_d2t(g, dqs, Dqs);
     /* adjoint wavefield of the residual */
@@ -636,10 +666,10 @@ static void tomo_adj_core(const og_grid *g, const double *v, const model_t *m, c
     og_prop_T(g, m->c, m->gam, a, ss);
     /* term (ii): extended image of r, contracted with p~ */
     double *Ws = (double *)calloc((size_t)g->nh * PP, sizeof(double));
-    for (int n = 0; n + 1 < nt; n++) og_scatter_TW_acc(g, D0 + (size_t)n * P, ss + (size_t)n * P, Ws);
+    ext_scatter_TW_seq(g, D0, ss, Ws);
     /* term (iii): z^n = E_D^T(W, s*^n), then d2t^T, then prop^T */
     double *z = (double *)malloc(SP * sizeof(double));
-    for (int n = 0; n + 1 < nt; n++) og_scatter_TD(g, Wt, ss + (size_t)n * P, z + (size_t)n * P);
+    ext_scatter_TD_seq(g, Wt, ss, z);
     double *a2 = (double *)malloc(QP * sizeof(double));
     og_d2t_T(g, z, a2);
     double *ss2 = (double *)malloc(SP * sizeof(double));
@@ -771,11 +801,8 @@ double og_shots(const og_grid *g, int op, const double *v, int nshot, const int 
         case OP_FWD: og_forward(g, v, &sh, o); break;
         case OP_BORN: og_born(g, v, &sh, in1, o); break;
         case OP_BORN_ADJ: og_born_adj(g, v, &sh, ds, o); break;
-        case OP_EXT: if (g->lag > 0) og_born_tlag(g, v, &sh, in1, o); else og_born_ext(g, v, &sh, in1, o); break;
-        case OP_EXT_ADJ:
-            if (g->lag > 0) og_born_tlag_adj(g, v, &sh, ds, o);
-            else og_born_ext_adj(g, v, &sh, ds, o);
-            break;
+        case OP_EXT: og_born_ext(g, v, &sh, in1, o); break;
+        case OP_EXT_ADJ: og_born_ext_adj(g, v, &sh, ds, o); break;
         case OP_TOMO: og_tomo(g, v, &sh, in1, in2 ? in2 : NULL, o); break;
         case OP_TOMO_ADJ: og_tomo_adj(g, v, &sh, in1, ds, o); break;
         case OP_GRAD: Js[s] = og_gradient(g, v, &sh, in1, ds, o, NULL); break;
