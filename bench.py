@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--grad-shots", type=int, default=120)
+    ap.add_argument("--no-tlag", action="store_true", help="skip the time-lag extension section")
     ap.add_argument("--no-reuse", action="store_true",
                     help="B~* runs its own checkpointing sweep instead of starting from the background states "
                          "kept by the B~ of the same step")
@@ -221,6 +222,40 @@ def serving_section(nreq: int, rate: float):
     out["plain_sample"] = f"first {len(sub)} requests served alone, one shot per launch"
     out["served_vs_plain"] = out["shots_per_s"] / out["plain_shots_per_s"]
     return out
+
+
+def time_lag_section(fw, torch, dev, wl, nh=21, lag=2):
+    """B~ then B~* with the time-lag extension (nh lags spaced lag * dt) on the bench workload, all
+    shots batched, one step: useful Gupd/s (4 propagations per step) and the extension kernels'
+    share and GB/s."""
+    grid = fw.Grid(nz=wl.nz, nx=wl.nx, sponge=wl.W, nt=wl.nt, dt=wl.dt, dx=wl.dx, nh=nh)
+    geom = fw.Geometry(wl.src_iz, wl.src_ix, wl.rec_iz, wl.rec_ix)
+    rng = np.random.default_rng(synth.SEED0 + 31)
+    v = torch.from_numpy(wl.v).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(wl.w.astype(np.float32), (wl.nshot, wl.nt)))).to(dev)
+    pt = torch.from_numpy(rng.standard_normal((nh, wl.nz, wl.nx)).astype(np.float32)).to(dev)
+    d = torch.zeros((wl.nshot, wl.nt, wl.nrec), device=dev)
+    img = torch.zeros((nh, wl.nz, wl.nx), device=dev)
+    with fw.Context(grid, geom, profile=1, time_lag=lag) as c:
+        c.autotune(fw.OP_BORN_EXT_ADJ)
+        c.born_ext(v, w, pt, d)
+        c.born_ext_adj(v, w, d, img)
+        c.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        c.born_ext(v, w, pt, d, sync=False)
+        c.born_ext_adj(v, w, d, img, sync=False)
+        e1.record()
+        c.sync()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = c.profile_read(reset=True)
+    kern = sum(p["ms"] for p in prof.values())
+    return {"workload": f"{wl.name} with {nh} time lags every {lag} dt (+-{(nh - 1) // 2 * lag * wl.dt * 1e3:.1f} ms)",
+            "ms_per_step": ms, "value": updates_per_step(wl) / (ms * 1e-3) / 1e9, "unit": "Gupd/s",
+            "time_share": {k: round(p["ms"] / kern, 4) for k, p in prof.items()} if kern else None,
+            "family_gbs": {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items() if p["ms"] > 0}}
 
 
 def gradient_section(fw, torch, dev, nshot):
@@ -477,6 +512,8 @@ def main():
     # FWIME gradient (Eqs. 7-9) on the North-Sea-shaped workload: batched vs plain shots/s
     if not args.no_grad and rank == 0:
         line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots)
+    if not args.no_tlag and rank == 0 and world == 1:
+        line["time_lag"] = time_lag_section(fw, torch, dev, wl)
     # serving mix: continuous batching with memory admission, p50/p99 (Poisson arrivals)
     if not args.no_serve and rank == 0:
         line["serving"] = serving_section(args.serve_requests, args.serve_rate)

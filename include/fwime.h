@@ -97,7 +97,13 @@ enum {
                                        checkpointing sweep (one propagation fewer).  The caller guarantees
                                        that v and w are not modified in between; any other operator call
                                        drops the states.  0 (default) frees them. */
-    FWIME_OPT_BACKGROUND_REUSED = 11 /* read-only: 1 if the last call started from those states */
+    FWIME_OPT_BACKGROUND_REUSED = 11, /* read-only: 1 if the last call started from those states */
+    FWIME_OPT_TIME_LAG = 12         /* 0 (default): B~ / B~* extend with nh horizontal subsurface offsets;
+                                       L > 0: with nh time lags tau_i = (i - (nh-1)/2) L dt, the symmetric
+                                       convention (source side at t - tau, receiver side at t + tau):
+                                       e^n(x) = sum_i b p~(x,i) D2t q0^{n - 2 (i-(nh-1)/2) L}(x).  Every
+                                       operator (B~, B~*, T, T*, gradient, objective, VP solve) then uses
+                                       the lag form. */
 };
 
 /* Kernel families, for fwime_profile_read. */

@@ -29,6 +29,7 @@ OPT_SHOTS_PER_BATCH, OPT_SEGMENT, OPT_PLAIN, OPT_GRAPH, OPT_HOST_IO, OPT_ZCHUNK,
 OPT_PROFILE = 9
 OPT_REUSE_BACKGROUND = 10
 OPT_BACKGROUND_REUSED = 11
+OPT_TIME_LAG = 12
 K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
 KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 (OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
@@ -225,7 +226,7 @@ class Context:
 
     _OPTS = {"shots_per_batch": OPT_SHOTS_PER_BATCH, "segment": OPT_SEGMENT, "plain": OPT_PLAIN,
              "graph": OPT_GRAPH, "host_io": OPT_HOST_IO, "zchunk": OPT_ZCHUNK, "profile": OPT_PROFILE,
-             "reuse_background": OPT_REUSE_BACKGROUND}
+             "reuse_background": OPT_REUSE_BACKGROUND, "time_lag": OPT_TIME_LAG}
 
     def set_option(self, name, value):
         opt = self._OPTS[name] if isinstance(name, str) else int(name)

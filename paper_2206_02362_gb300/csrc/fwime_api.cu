@@ -57,6 +57,7 @@ struct fwime_ctx {
     int device = 0;
     // options
     int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0, opt_reuse_bg = 0;
+    int opt_tlag = 0;               // > 0: B~ / B~* extend with time lags spaced opt_tlag steps
     // background-wavefield checkpoints of every shot, [nseg][2][nshot][P], written by B and B~ and
     // read by B* and B~* on the same v, w (FWIME_OPT_REUSE_BACKGROUND)
     struct BgCache {
@@ -201,11 +202,36 @@ struct Sizes {
 
 static size_t al(size_t n) { return (n + 63) & ~(size_t)63; }   // 256-byte granules
 
+// time-lag extension: shifts reach Hs = 2 hm lag steps either way; the background D2t ring holds K + 2 Hs
+// steps; the adjoint recomputes the background in blocks [j K - Hs, (j+1) K - Hs), j = 0 .. tlag_blocks - 1
+static int tlag_Hs(const fwime_grid &g, int lag) { return (g.nh - 1) * lag; }
+static int tlag_blocks(const fwime_grid &g, int K, int lag) { return (g.nt - 2 + tlag_Hs(g, lag)) / K + 1; }
+
 static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int NZ, int NXP, int op, int K,
-                      bool host_io, bool no_ckpt = false)
+                      bool host_io, bool no_ckpt = false, int tlag = 0)
 {
     Sizes s;
     const size_t nh = g.nh, nseg = (size_t)((g.nt - 1 + K - 1) / K), R = K + 2;
+    if (tlag > 0 && op != FWIME_OP_FORWARD && op != FWIME_OP_BORN && op != FWIME_OP_BORN_ADJ) {
+        const size_t Hs = tlag_Hs(g, tlag), RD = (size_t)K + 2 * Hs, NB = tlag_blocks(g, K, tlag);
+        s.model = al(P) * 2 + al(NZ) + al(NXP);
+        size_t f = 0;
+        switch (op) {
+        case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 4 + RD + K; break;
+        case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + RD + R + 2 * NB; break;
+        case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 2 * RD + 2 * K; break;
+        default:   // T*, gradient, objective
+            s.model += 2 * al(nh * P) + al(P);
+            f = 4 + RD + 2 * (size_t)K + (RD + 2) + 2 * R + 2 * NB + 2 * nseg;
+        }
+        s.per_shot = f * (size_t)P;
+        if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) s.per_shot += (size_t)g.nt * nrec;
+        if (host_io) {
+            const size_t nd = (size_t)nshot * g.nt * nrec, nm = (size_t)g.nz * g.nx;
+            s.staging = al(nm) + al((size_t)nshot * g.nt) + 2 * al(nd) + al(nh * nm) + al(nm) + al(nh * nm);
+        }
+        return s;
+    }
     s.model = al(P) * 2 + al(NZ) + al(NXP);   // c, bpad, gz, gx
     size_t f = 0;
     switch (op) {
@@ -269,7 +295,8 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
     w.K = std::max(w.K, 1);
     w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;
     w.R = w.K + 2;
-    Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0, no_ckpt);
+    Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0, no_ckpt,
+                        x->opt_tlag);
     size_t budget = x->max_ws;
     if (budget == 0 && x->capturing) budget = x->ws_bytes;   // the workspace was planned before capture
     if (budget == 0) {
@@ -340,6 +367,33 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
     for (auto &q : w.ring) q = nullptr;
     w.ckpt = w.pred = nullptr;
     int nf = 0, nk = 0, nr = 0, nck = 0;
+    if (x->opt_tlag > 0 && op != FWIME_OP_FORWARD && op != FWIME_OP_BORN && op != FWIME_OP_BORN_ADJ) {
+        const size_t RD = (size_t)w.K + 2 * tlag_Hs(x->g, x->opt_tlag), NB = tlag_blocks(x->g, w.K, x->opt_tlag);
+        const size_t K = w.K, R = w.R;
+        switch (op) {
+        case FWIME_OP_BORN_EXT:   // fields q0, dq; ring[0] D2t q0 (K + 2 Hs), ring[1] scatter output (K)
+            for (int i = 0; i < 4; ++i) w.f[i] = take(SP);
+            w.ring[0] = take(RD * SP); w.ring[1] = take(K * SP);
+            break;
+        case FWIME_OP_BORN_EXT_ADJ:   // ring[0] D2t q0, ring[1] adjoint field (K + 2); block checkpoints
+            for (int i = 0; i < 2; ++i) w.f[i] = take(SP);
+            w.ring[0] = take(RD * SP); w.ring[1] = take(R * SP);
+            w.ckpt = take(NB * 2 * SP);
+            break;
+        case FWIME_OP_TOMO:   // rings: D2t q0, D2t dq0 (K + 2 Hs), scatter output, D2t dqs (K)
+            for (int i = 0; i < 8; ++i) w.f[i] = take(SP);
+            w.ring[0] = take(RD * SP); w.ring[1] = take(RD * SP); w.ring[2] = take(K * SP); w.ring[3] = take(K * SP);
+            break;
+        default:   // T*, gradient, objective: D2t q0, scatter output, D2t dqs, mu (K + 2 Hs + 2), z, mu2
+            for (int i = 0; i < 4; ++i) w.f[i] = take(SP);
+            w.ring[0] = take(RD * SP); w.ring[1] = take(K * SP); w.ring[2] = take(K * SP);
+            w.ring[3] = take((RD + 2) * SP); w.ring[4] = take(R * SP); w.ring[5] = take(R * SP);
+            w.ckpt = take((NB + (size_t)w.nseg) * 2 * SP);
+            if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
+        }
+        if ((char *)p > x->ws + x->ws_bytes) return fail(x, FWIME_ENOMEM, "workspace layout overflow");
+        return FWIME_OK;
+    }
     switch (op) {
     case FWIME_OP_FORWARD: nf = 2; break;
     case FWIME_OP_BORN: nf = 5; break;
@@ -703,6 +757,323 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
     return FWIME_OK;
 }
 
+// ---------------------------------------------------------------- time-lag extension
+
+static int tlag_launch(Run &r, int Sb, int n0, int n1, bool image, RingRef D, RingRef E, RingRef L, float *img,
+                       const float *W = nullptr, int sigma = 1, int accumulate = 0)
+{
+    fwime_ctx *x = r.x;
+    TlagArgs a{};
+    a.NXP = x->NXP; a.nh = x->g.nh; a.S = Sb; a.lag = x->opt_tlag; a.nt = x->g.nt; a.n0 = n0; a.n1 = n1;
+    a.nchunk = tlag_chunks(r.w.K, x->opt_tlag); a.P = x->P; a.sigma = sigma;
+    a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;
+    a.W = W ? W : r.w.W; a.D = D; a.E = E; a.L = L; a.img = img; a.accumulate = accumulate;
+    const double pts = (double)Sb * x->g.nz * x->g.nx * (n1 - n0);
+    if (image) LAUNCH(FWIME_K_IMAGE, pts * 8.0 + 8.0 * x->g.nh * x->g.nz * x->g.nx, launch_tlag_image(a, x->st));
+    else LAUNCH(FWIME_K_SCATTER, pts * 8.0 + 4.0 * x->g.nh * x->g.nz * x->g.nx, launch_tlag_scatter(a, x->st));
+    return FWIME_OK;
+}
+
+// B~ with time lags: the background runs Hs = 2 hm lag steps ahead of the scattered field so that every
+// segment's secondary sources find D2t q0 at n - 2 s_i for all lags in the ring
+static int run_born_tlag(fwime_ctx *x, Run &r, const float *w, const float *pt, float *d)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, Hs = tlag_Hs(x->g, x->opt_tlag), RD = K + 2 * Hs;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * x->g.nh * x->P));
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * x->g.nz * x->g.nx,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    float *Dr = r.w.ring[0], *Er = r.w.ring[1];
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *c0 = r.w.f[0], *p0 = r.w.f[1], *c1 = r.w.f[2], *p1 = r.w.f[3];
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        int bg = 0;   // next background step (produces D2t of that step)
+        for (int n0 = 0; n0 < nt - 1; n0 += K) {
+            const int n1 = std::min(n0 + K, nt - 1);
+            for (const int top = std::min(n1 - 1 + Hs, nt - 2); bg <= top; ++bg) {
+                TRY(prop(r, Sb, c0, p0, p0, Dr + (long long)(bg % RD) * SP, w + (size_t)s0 * nt + bg, s0));
+                std::swap(c0, p0);
+            }
+            TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Dr, SP, RD, 0), ringref(Er, SP, 0, 0),
+                            ringref(nullptr, 0, 0, 0), nullptr));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                std::swap(c1, p1);
+            }
+        }
+    }
+    return FWIME_OK;
+}
+
+// B~* with time lags.  Output segments j = nseg-1 .. 0 need the background's D2t on [jK - Hs, (j+1)K - 1 + Hs];
+// walking backwards, segment j adds the block [jK - Hs, (j+1)K - Hs), recomputed from the state stored at its
+// start by a forward checkpointing sweep, so every D2t step is recomputed once.
+static int run_born_tlag_adj(fwime_ctx *x, Run &r, const float *v, const float *w, const float *d, float *out,
+                             int accumulate)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
+    const int Hs = tlag_Hs(x->g, x->opt_tlag), RD = K + 2 * Hs, NB = tlag_blocks(x->g, K, x->opt_tlag);
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    TRY(zero(x, r.w.acc1, sizeof(float) * x->g.nh * x->P));
+    float *Dr = r.w.ring[0], *Mu = r.w.ring[1], *ck = r.w.ckpt;
+    auto bstart = [&](int j) { return std::max(j * K - Hs, 0); };
+    auto bend = [&](int j) { return std::min((j + 1) * K - Hs, nt - 1); };   // exclusive; D2t steps end at nt-2
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        const size_t fb = sizeof(float) * (size_t)Sb * x->P;
+        float *cur = r.w.f[0], *prv = r.w.f[1];
+        TRY(zero(x, cur, fb));
+        TRY(zero(x, prv, fb));
+        TRY(zero(x, Mu, sizeof(float) * R * SP));
+        const float *ws = w + (size_t)s0 * nt;
+        // checkpointing sweep: the state at the start of every block
+        int n = 0;
+        for (int j = 0; j < NB; ++j) {
+            const int b0 = bstart(j);
+            if (b0 >= bend(j)) continue;   // empty block (all before step 0)
+            for (; n < b0; ++n) {
+                TRY(prop(r, Sb, cur, prv, prv, nullptr, ws + n, s0));
+                std::swap(cur, prv);
+            }
+            TRY(copyf(x, ck + (2LL * j) * SP, cur, (size_t)Sb * x->P));
+            TRY(copyf(x, ck + (2LL * j + 1) * SP, prv, (size_t)Sb * x->P));
+        }
+        auto block = [&](int j) -> int {   // recompute block j's D2t into the ring
+            const int b0 = bstart(j), b1 = bend(j);
+            if (b0 >= b1) return FWIME_OK;
+            TRY(copyf(x, cur, ck + (2LL * j) * SP, (size_t)Sb * x->P));
+            TRY(copyf(x, prv, ck + (2LL * j + 1) * SP, (size_t)Sb * x->P));
+            for (int m = b0; m < b1; ++m) {
+                TRY(prop(r, Sb, cur, prv, prv, Dr + (long long)(m % RD) * SP, ws + m, s0));
+                std::swap(cur, prv);
+            }
+            return FWIME_OK;
+        };
+        int next_block = NB - 1;   // blocks > next_block are in the ring
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1);
+            for (; next_block >= j; --next_block) TRY(block(next_block));
+            for (int m = n1; m >= n0 + 1; --m) {
+                float *mo = Mu + (m % R) * SP;
+                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
+                TRY(inject(r, Sb, mo, d + s0 * nd + (size_t)m * x->nrec));
+            }
+            TRY(tlag_launch(r, Sb, n0, n1, true, ringref(Dr, SP, RD, 0), ringref(nullptr, 0, 0, 0),
+                            ringref(Mu, SP, R, 1), r.w.acc1));
+        }
+    }
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * x->g.nz * x->g.nx,
+           launch_finalize(r.w.acc1, nullptr, r.w.bpad, v, out, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                           accumulate, x->st));
+    return FWIME_OK;
+}
+
+// T with time lags: the background q0 and the Born wavefield dq0 of dv run Hs steps ahead (their D2t in rings
+// of K + 2 Hs steps), the extended Born wavefield dqs and the tomographic wavefield follow segment by segment
+static int run_tomo_tlag(fwime_ctx *x, Run &r, const float *v, const float *w, const float *pt, const float *dv,
+                         float *d)
+{
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, Hs = tlag_Hs(x->g, x->opt_tlag), RD = K + 2 * Hs;
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    const size_t nhP = (size_t)x->g.nh * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * nhP));
+    TRY(zero(x, r.w.W2, sizeof(float) * nhP));
+    TRY(zero(x, r.w.coef, sizeof(float) * x->P));
+    const double nm = (double)x->g.nz * x->g.nx;
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    LAUNCH(FWIME_K_OTHER, 20.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, dv, v, r.w.W2, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1, x->st));
+    LAUNCH(FWIME_K_OTHER, 12.0 * nm,
+           launch_embed_scale(dv, r.w.bpad, r.w.coef, x->g.nz, x->g.nx, x->o, x->NXP, 1.f, x->st));
+    float *D0r = r.w.ring[0], *Dq0r = r.w.ring[1], *Er = r.w.ring[2], *Dsr = r.w.ring[3];
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    const RingRef none = ringref(nullptr, 0, 0, 0), er = ringref(Er, SP, 0, 0);
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        float *f[8];
+        for (int i = 0; i < 8; ++i) {
+            f[i] = r.w.f[i];
+            TRY(zero(x, f[i], sizeof(float) * Sb * x->P));
+        }
+        float *db = d + s0 * nd;
+        TRY(zero(x, db, sizeof(float) * Sb * nd));
+        const float *ws = w + (size_t)s0 * nt;
+        int bg = 0;
+        for (int n0 = 0; n0 < nt - 1; n0 += K) {
+            const int n1 = std::min(n0 + K, nt - 1);
+            for (const int top = std::min(n1 - 1 + Hs, nt - 2); bg <= top; ++bg) {
+                float *D0 = D0r + (long long)(bg % RD) * SP;
+                TRY(prop(r, Sb, f[0], f[1], f[1], D0, ws + bg, s0));                       // background q0
+                std::swap(f[0], f[1]);
+                TRY(prop(r, Sb, f[2], f[3], f[3], Dq0r + (long long)(bg % RD) * SP, nullptr, 0, nullptr, 0, nullptr, 0,
+                         nullptr, 0, r.w.coef, D0));                                            // Born wavefield of dv
+                std::swap(f[2], f[3]);
+            }
+            TRY(tlag_launch(r, Sb, n0, n1, false, ringref(D0r, SP, RD, 0), er, none, nullptr));
+            for (int n = n0; n < n1; ++n) {   // extended Born wavefield of p~
+                TRY(prop(r, Sb, f[4], f[5], f[5], Dsr + (n - n0) * SP, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                std::swap(f[4], f[5]);
+            }
+            TRY(tlag_launch(r, Sb, n0, n1, false, ringref(D0r, SP, RD, 0), er, none, nullptr, r.w.W2, 1, 0));
+            TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Dq0r, SP, RD, 0), er, none, nullptr, r.w.W, 1, 1));
+            for (int n = n0; n < n1; ++n) {   // tomographic wavefield
+                TRY(prop(r, Sb, f[6], f[7], f[7], nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0, nullptr, 0,
+                         r.w.coef, Dsr + (n - n0) * SP));
+                TRY(record(r, Sb, f[7], nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                std::swap(f[6], f[7]);
+            }
+        }
+    }
+    return FWIME_OK;
+}
+
+// T*, the FWIME gradient and the objective with time lags (modes as run_tomo_adj).  Forward sweep: q0 runs Hs
+// steps ahead (its state stored at every block start), dqs follows segment by segment (its state stored at
+// every segment start), both recorded for the residual.  Backward sweep: per segment, add the block of q0's
+// D2t, recompute dqs, run the residual's adjoint field Hs steps ahead (the transposed lag scatter reads it
+// up to Hs steps either way), then the second adjoint field and the images.
+static int run_tomo_adj_tlag(fwime_ctx *x, Run &r, int mode, const float *v, const float *w, const float *pt,
+                             const float *d, float *out, int accumulate, float eps)
+{
+    const bool grad = mode >= 1, objective_only = mode == 2;
+    const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
+    const int Hs = tlag_Hs(x->g, x->opt_tlag), RD = K + 2 * Hs, RM = RD + 2, NB = tlag_blocks(x->g, K, x->opt_tlag);
+    const size_t nd = (size_t)nt * x->nrec;
+    const long long SP = (long long)S * x->P;
+    const size_t nhP = (size_t)x->g.nh * x->P;
+    TRY(zero(x, r.w.W, sizeof(float) * nhP));
+    TRY(zero(x, r.w.acc1, sizeof(float) * x->P));
+    TRY(zero(x, r.w.acc2, sizeof(float) * nhP));
+    const double nm = (double)x->g.nz * x->g.nx;
+    LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
+           launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
+                              x->st));
+    float *D0r = r.w.ring[0], *Er = r.w.ring[1], *Dsr = r.w.ring[2];
+    float *Mu = r.w.ring[3], *Zr = r.w.ring[4], *Mu2 = r.w.ring[5];
+    float *ckq = r.w.ckpt, *cks = r.w.ckpt + 2LL * NB * SP;
+    TRY(zero(x, Er, sizeof(float) * K * SP));
+    if (grad) TRY(zero(x, x->d_J, sizeof(double)));
+    const int nred = 1024;
+    const float idt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
+    const RingRef none = ringref(nullptr, 0, 0, 0), er = ringref(Er, SP, 0, 0), dring = ringref(D0r, SP, RD, 0);
+    auto bstart = [&](int j) { return std::max(j * K - Hs, 0); };
+    auto bend = [&](int j) { return std::min((j + 1) * K - Hs, nt - 1); };
+    for (int s0 = 0; s0 < x->nshot; s0 += S) {
+        const int Sb = std::min(S, x->nshot - s0);
+        const size_t fb = sizeof(float) * (size_t)Sb * x->P;
+        const size_t fn = (size_t)Sb * x->P;
+        float *q0c = r.w.f[0], *q0p = r.w.f[1], *qsc = r.w.f[2], *qsp = r.w.f[3];
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], fb));
+        if (!objective_only) {
+            TRY(zero(x, Mu, sizeof(float) * RM * SP));
+            TRY(zero(x, Zr, sizeof(float) * R * SP));
+            TRY(zero(x, Mu2, sizeof(float) * R * SP));
+        }
+        const float *ws = w + (size_t)s0 * nt;
+        float *pred = r.w.pred;
+        if (grad) TRY(zero(x, pred, sizeof(float) * Sb * nd));
+        // forward sweep
+        int bg = 0, nblk = 0;
+        for (int j = 0; j < nseg; ++j) {
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1);
+            if (!objective_only) {
+                TRY(copyf(x, cks + (2LL * j) * SP, qsc, fn));
+                TRY(copyf(x, cks + (2LL * j + 1) * SP, qsp, fn));
+            }
+            for (const int top = std::min(n1 - 1 + Hs, nt - 2); bg <= top; ++bg) {
+                for (; !objective_only && nblk < NB && bstart(nblk) <= bg; ++nblk) {
+                    if (bstart(nblk) < bend(nblk) && bstart(nblk) == bg) {
+                        TRY(copyf(x, ckq + (2LL * nblk) * SP, q0c, fn));
+                        TRY(copyf(x, ckq + (2LL * nblk + 1) * SP, q0p, fn));
+                    }
+                }
+                TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (long long)(bg % RD) * SP, ws + bg, s0));
+                if (grad) TRY(record(r, Sb, q0p, nullptr, pred + (size_t)(bg + 1) * x->nrec, 0));
+                std::swap(q0c, q0p);
+            }
+            TRY(tlag_launch(r, Sb, n0, n1, false, dring, er, none, nullptr));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                if (grad) TRY(record(r, Sb, qsp, nullptr, pred + (size_t)(n + 1) * x->nrec, 1));
+                std::swap(qsc, qsp);
+            }
+        }
+        const float *rr = d + s0 * nd;
+        if (grad) {
+            LAUNCH(FWIME_K_OTHER, 12.0 * Sb * nd,
+                   launch_residual(pred, d + s0 * nd, pred, (long long)Sb * nd, x->d_part, nred, x->st));
+            LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
+            rr = pred;
+        }
+        if (objective_only) continue;
+        // backward sweep
+        int next_block = NB - 1, mu_lo = nt;   // mu^k computed for k >= mu_lo (mu^nt = mu^nt+1 = 0)
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+            for (; next_block >= j; --next_block) {   // q0's D2t block [b0, b1) from its checkpoint
+                const int b0 = bstart(next_block), b1 = bend(next_block);
+                if (b0 >= b1) continue;
+                TRY(copyf(x, q0c, ckq + (2LL * next_block) * SP, fn));
+                TRY(copyf(x, q0p, ckq + (2LL * next_block + 1) * SP, fn));
+                for (int m = b0; m < b1; ++m) {
+                    TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (long long)(m % RD) * SP, ws + m, s0));
+                    std::swap(q0c, q0p);
+                }
+            }
+            TRY(copyf(x, qsc, cks + (2LL * j) * SP, fn));
+            TRY(copyf(x, qsp, cks + (2LL * j + 1) * SP, fn));
+            TRY(tlag_launch(r, Sb, n0, n1, false, dring, er, none, nullptr));
+            for (int n = n0; n < n1; ++n) {
+                TRY(prop(r, Sb, qsc, qsp, qsp, Dsr + (n - n0) * SP, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                std::swap(qsc, qsp);
+            }
+            // the residual's adjoint field, Hs steps ahead: mu^k down to k = n0 - Hs + 1
+            for (const int lo = std::max(n0 - Hs + 1, 1); mu_lo - 1 >= lo; --mu_lo) {
+                const int k = mu_lo - 1;
+                float *mo = Mu + (long long)(k % RM) * SP;
+                TRY(prop(r, Sb, Mu + (long long)((k + 1) % RM) * SP, Mu + (long long)((k + 2) % RM) * SP, mo, nullptr,
+                         nullptr, 0));
+                TRY(inject(r, Sb, mo, rr + (size_t)k * x->nrec));
+            }
+            // z^m = sum_i W_i lambda^(m + 2 s_i) for m in [n0, n1) (lambda^n = mu^(n+1))
+            TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Mu, SP, RM, 1), ringref(Zr, SP, R, n0), none, nullptr, r.w.W,
+                            -1, 0));
+            // second adjoint field driven by d2t^T z
+            for (int m = n1; m >= n0 + 1; --m) {
+                TRY(prop(r, Sb, Mu2 + ((m + 1) % R) * SP, Mu2 + ((m + 2) % R) * SP, Mu2 + (m % R) * SP, nullptr,
+                         nullptr, 0, Zr + ((m - 1) % R) * SP, idt2, Zr + (m % R) * SP, -2.f * idt2,
+                         Zr + ((m + 1) % R) * SP, idt2));
+            }
+            TRY(image(r, Sb, n0, kk, IMG_LOCAL, dring, ringref(Mu, SP, RM, 1), ringref(Mu2, SP, R, 1),
+                      ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc1));
+            TRY(tlag_launch(r, Sb, n0, n1, true, dring, none, ringref(Mu, SP, RM, 1), r.w.acc2));
+        }
+    }
+    if (!objective_only)
+        LAUNCH(FWIME_K_OTHER, 20.0 * nm,
+               launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
+                               accumulate, x->st, pt, x->g.nh));
+    if (grad) {
+        LAUNCH(FWIME_K_OTHER, 4.0 * x->g.nh * nm,
+               launch_dso(pt, x->g.nh, (long long)x->g.nz * x->g.nx, x->d_part, nred, x->st));
+        LAUNCH(FWIME_K_OTHER, 8.0 * nred,
+               launch_sum_partials(x->d_part, nred, x->d_J, 1, 0.5 * (double)eps * (double)eps, x->st));
+        CK(cudaMemcpyAsync(x->h_J, x->d_J, sizeof(double), cudaMemcpyDeviceToHost, x->st));
+    }
+    return FWIME_OK;
+}
+
 static int run_tomo(fwime_ctx *x, Run &r, const float *v, const float *w, const float *pt, const float *dv, float *d)
 {
     const int nt = x->g.nt, S = r.w.S, K = r.w.K;
@@ -892,19 +1263,21 @@ struct Call {
 
 static bool is_bg_writer(int op) { return op == FWIME_OP_BORN || op == FWIME_OP_BORN_EXT; }
 static bool is_bg_reader(int op) { return op == FWIME_OP_BORN_ADJ || op == FWIME_OP_BORN_EXT_ADJ; }
+// the time-lag schedules place their checkpoints differently: no background cache for them
+static bool bg_applies(const fwime_ctx *x, int op) { return !(x->opt_tlag > 0 && (op == FWIME_OP_BORN_EXT || op == FWIME_OP_BORN_EXT_ADJ)); }
 
 // does this call start from the cached background checkpoints?
 static bool bg_usable(const fwime_ctx *x, const Call &c)
 {
-    return is_bg_reader(c.op) && x->opt_reuse_bg && x->bg.valid && x->bg.v == c.v && x->bg.w == c.w &&
-           x->bg.K == seg_K(x) && x->bg.buf;
+    return is_bg_reader(c.op) && bg_applies(x, c.op) && x->opt_reuse_bg && x->bg.valid && x->bg.v == c.v &&
+           x->bg.w == c.w && x->bg.K == seg_K(x) && x->bg.buf;
 }
 
 // host-side bookkeeping once a call has been enqueued (directly or as a graph replay)
 static void bg_after(fwime_ctx *x, const Call &c, bool wrote)
 {
     if (is_bg_writer(c.op)) {
-        x->bg.valid = wrote;
+        x->bg.valid = wrote && bg_applies(x, c.op);
         x->bg.v = c.v; x->bg.w = c.w; x->bg.K = seg_K(x);
     } else if (!is_bg_reader(c.op)) {
         x->bg.valid = false;
@@ -916,7 +1289,7 @@ static int enqueue(fwime_ctx *x, const Call &c)
     Run r;
     const bool use_bg = bg_usable(x, c);
     x->bg_used = use_bg;
-    x->bg_written = is_bg_writer(c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
+    x->bg_written = is_bg_writer(c.op) && bg_applies(x, c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
     if (x->bg_written) x->bg.valid = false;   // being overwritten
     TRY(plan(x, c.op, r.w, use_bg));
     init_run(x, r, r.w.S);
@@ -925,12 +1298,25 @@ static int enqueue(fwime_ctx *x, const Call &c)
     case FWIME_OP_FORWARD: return run_forward(x, r, c.v, c.w, c.out);
     case FWIME_OP_BORN: return run_born(x, r, c.v, c.w, c.in1, c.out);
     case FWIME_OP_BORN_ADJ: return run_born_adj(x, r, false, c.v, c.w, c.in1, c.out, c.accumulate, use_bg);
-    case FWIME_OP_BORN_EXT: return run_born_ext(x, r, c.v, c.w, c.in1, c.out);
-    case FWIME_OP_BORN_EXT_ADJ: return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate, use_bg);
-    case FWIME_OP_TOMO: return run_tomo(x, r, c.v, c.w, c.in1, c.in2, c.out);
-    case FWIME_OP_TOMO_ADJ: return run_tomo_adj(x, r, 0, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, 0.f);
-    case FWIME_OP_GRADIENT: return run_tomo_adj(x, r, 1, c.v, c.w, c.in1, c.in2, c.out, 0, c.eps);
-    case FWIME_OP_OBJECTIVE: return run_tomo_adj(x, r, 2, c.v, c.w, c.in1, c.in2, nullptr, 0, c.eps);
+    case FWIME_OP_BORN_EXT:
+        if (x->opt_tlag > 0) return run_born_tlag(x, r, c.w, c.in1, c.out);
+        return run_born_ext(x, r, c.v, c.w, c.in1, c.out);
+    case FWIME_OP_BORN_EXT_ADJ:
+        if (x->opt_tlag > 0) return run_born_tlag_adj(x, r, c.v, c.w, c.in1, c.out, c.accumulate);
+        return run_born_adj(x, r, true, c.v, c.w, c.in1, c.out, c.accumulate, use_bg);
+    case FWIME_OP_TOMO:
+        if (x->opt_tlag > 0) return run_tomo_tlag(x, r, c.v, c.w, c.in1, c.in2, c.out);
+        return run_tomo(x, r, c.v, c.w, c.in1, c.in2, c.out);
+    case FWIME_OP_TOMO_ADJ:
+    case FWIME_OP_GRADIENT:
+    case FWIME_OP_OBJECTIVE: {
+        const int mode = c.op == FWIME_OP_TOMO_ADJ ? 0 : (c.op == FWIME_OP_GRADIENT ? 1 : 2);
+        float *o = c.op == FWIME_OP_OBJECTIVE ? nullptr : c.out;
+        const int acc = c.op == FWIME_OP_TOMO_ADJ ? c.accumulate : 0;
+        const float e = c.op == FWIME_OP_TOMO_ADJ ? 0.f : c.eps;
+        if (x->opt_tlag > 0) return run_tomo_adj_tlag(x, r, mode, c.v, c.w, c.in1, c.in2, o, acc, e);
+        return run_tomo_adj(x, r, mode, c.v, c.w, c.in1, c.in2, o, acc, e);
+    }
     }
     return fail(x, FWIME_EINVAL, "unknown operator %d", c.op);
 }
@@ -951,15 +1337,16 @@ static int run_call(fwime_ctx *x, const Call &c)
     if (x->st == nullptr) return fail(x, FWIME_EINVAL, "graph mode needs a non-default stream");
     // plan (and reserve the background cache) first so that no allocation happens inside a capture
     const bool use_bg = bg_usable(x, c);
-    const bool write_bg = is_bg_writer(c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
+    const bool write_bg = is_bg_writer(c.op) && bg_applies(x, c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
     {
         WS w;
         TRY(plan(x, c.op, w, use_bg));
     }
     char key[320];
-    snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d|%d%d|%p", c.op, (const void *)c.v, (const void *)c.w,
+    snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d|%d%d|%p|%d", c.op, (const void *)c.v, (const void *)c.w,
              (const void *)c.in1, (const void *)c.in2, (void *)c.out, c.accumulate, (double)c.eps, x->opt_S, x->opt_K,
-             x->opt_zchunk, use_bg ? 1 : 0, write_bg ? 1 : 0, (const void *)(use_bg || write_bg ? x->bg.buf : nullptr));
+             x->opt_zchunk, use_bg ? 1 : 0, write_bg ? 1 : 0, (const void *)(use_bg || write_bg ? x->bg.buf : nullptr),
+             x->opt_tlag);
     auto it = x->graphs.find(key);
     if (it == x->graphs.end()) {
         CK(cudaStreamBeginCapture(x->st, cudaStreamCaptureModeThreadLocal));
@@ -1141,6 +1528,11 @@ int fwime_set_option(fwime_ctx *x, int option, long long value)
     case FWIME_OPT_HOST_IO: x->opt_host_io = value != 0; return FWIME_OK;
     case FWIME_OPT_ZCHUNK: if (value < 0 || value > 4096) break; x->opt_zchunk = (int)value; return FWIME_OK;
     case FWIME_OPT_PROFILE: x->opt_profile = value != 0; return FWIME_OK;
+    case FWIME_OPT_TIME_LAG:
+        if (value < 0 || value > 100000) break;
+        x->opt_tlag = (int)value;
+        x->bg.valid = false;
+        return FWIME_OK;
     case FWIME_OPT_REUSE_BACKGROUND:
         x->opt_reuse_bg = value != 0;
         x->bg.valid = false;
@@ -1169,6 +1561,7 @@ int fwime_get_option(fwime_ctx *x, int option, long long *value)
     case FWIME_OPT_PROFILE: *value = x->opt_profile; return FWIME_OK;
     case FWIME_OPT_REUSE_BACKGROUND: *value = x->opt_reuse_bg; return FWIME_OK;
     case FWIME_OPT_BACKGROUND_REUSED: *value = x->bg_used; return FWIME_OK;
+    case FWIME_OPT_TIME_LAG: *value = x->opt_tlag; return FWIME_OK;
     }
     return fail(x, FWIME_EINVAL, "bad option %d", option);
 }

@@ -115,6 +115,20 @@ struct ImgArgs {
     float *img;                    // IMG_EXT: [nh][P]; others: [P]
 };
 
+// time-lag extension: one segment [n0, n1) of output steps, S shots
+struct TlagArgs {
+    int NXP, nh, S, lag, nt, n0, n1, nchunk;
+    int sigma;                     // scatter: +1 reads D at n - 2 s_i, -1 (transpose) at n + 2 s_i
+    long long P;
+    int z_lo, z_hi, x_lo, x_hi;    // physical rows / columns
+    const float *W;                // [nh][P] weights b p~ (scatter)
+    RingRef D;                     // scatter input (background D2t; adjoint field for sigma = -1), slot of step m
+    RingRef E;                     // scatter output, slot of n - n0 (with shift n0 and mod: a ring indexed by n)
+    RingRef L;                     // image: receiver side, slot of step n
+    float *img;                    // image [nh][P]
+    int accumulate;
+};
+
 // launchers (return cudaGetLastError())
 cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
 cudaError_t prop_occupancy(int *blocks_per_sm);
@@ -123,6 +137,9 @@ cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const
 cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st);
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st);
+cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st);
+int tlag_chunks(int K, int lag);   // output chunks per residue class for a segment of K steps
 
 // model preparation
 struct PrepArgs {

@@ -1,0 +1,183 @@
+// Time-lag extension kernels (Barnier et al., Theory section: Born modelling extended with time lags,
+// Eq. 1, and its adjoint, the extended imaging condition, Eqs. 2-5).  Symmetric lags
+// tau_i = s_i dt, s_i = (i - hm) L, couple the source side at t - tau with the receiver side at t + tau:
+//
+//   scatter  e^n(x)    = sum_i W(x, i) D^{n - 2 s_i}(x)           (W = b p~, D^m = 0 outside 0..nt-2)
+//   transpose z^m(x)   = sum_i W(x, i) L^{m + 2 s_i}(x)           (sigma = -1: the lag index reversed)
+//   image    I(x, i)  += sum_{shots} sum_n D^{n - 2 s_i}(x) L^n(x)
+//
+// Output step n = base + 2 L j only reads D at steps of the same residue modulo 2L,
+// m = base + 2 L (j - i + hm), so a thread that owns one point and JC consecutive outputs of one residue
+// class needs the JC + 2 hm samples m_k = base + 2 L (k - hm) of that class: every sample it loads
+// serves up to JC (scatter) or nh (image) multiply-adds, with the nh weights or accumulators in
+// registers.  Planes of the rings are [S][P]; consecutive threads take consecutive columns of one row
+// (coalesced), the time samples of a point are strided by the ring's slot stride.
+#include "fwime_kernels.cuh"
+
+namespace fwk {
+
+constexpr int TL_TX = 128;      // threads per CTA (consecutive columns)
+constexpr int TL_JC = 16;       // outputs of one residue class per thread
+
+// element offset of time step m in ring r (m >= 0)
+__device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
+{
+    return (long long)((r.mod > 0 ? (m + r.shift) % r.mod : m + r.shift)) * r.slot_stride;
+}
+
+// blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue, chunk)
+template <int NH, int SIGMA>
+__global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
+{
+    constexpr int HM = (NH - 1) / 2, NW = TL_JC + 2 * HM;
+    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    if (X >= a.x_hi) return;
+    const int Z = a.z_lo + blockIdx.y;
+    int q = blockIdx.z;
+    const int chunk = q % a.nchunk; q /= a.nchunk;
+    const int r = q % (2 * a.lag); const int s = q / (2 * a.lag);
+    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;   // output j of this thread: base + 2 L j
+    if (base >= a.n1) return;
+    float Wr[NH];   // sigma = -1 reads lag i at m + 2 s_i = m - 2 s_(nh-1-i): the weights reversed
+#pragma unroll
+    for (int i = 0; i < NH; ++i) Wr[i] = __ldg(a.W + (SIGMA > 0 ? i : NH - 1 - i) * a.P + pp);
+    float win[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const int m = base + 2 * a.lag * (k - HM);
+        win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + tl_slot(a.D, m) + off) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < TL_JC; ++j) {
+        const int n = base + 2 * a.lag * j;
+        if (n >= a.n1) break;
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < NH; ++i) acc = fmaf(Wr[i], win[j - i + 2 * HM], acc);
+        float *o = const_cast<float *>(a.E.base) + tl_slot(a.E, n - a.n0) + off;
+        *o = a.accumulate ? *o + acc : acc;
+    }
+}
+
+// generic nh: weights and samples re-read per output (any odd nh)
+__global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
+{
+    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    if (X >= a.x_hi) return;
+    const int Z = a.z_lo + blockIdx.y;
+    int q = blockIdx.z;
+    const int chunk = q % a.nchunk; q /= a.nchunk;
+    const int r = q % (2 * a.lag); const int s = q / (2 * a.lag);
+    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;
+    const int hm = (a.nh - 1) / 2;
+    for (int j = 0; j < TL_JC; ++j) {
+        const int n = base + 2 * a.lag * j;
+        if (n >= a.n1) break;
+        float acc = 0.f;
+        for (int i = 0; i < a.nh; ++i) {
+            const int m = n - a.sigma * 2 * a.lag * (i - hm);
+            if (m >= 0 && m <= a.nt - 2) acc = fmaf(__ldg(a.W + i * a.P + pp), __ldg(a.D.base + tl_slot(a.D, m) + off), acc);
+        }
+        float *o = const_cast<float *>(a.E.base) + tl_slot(a.E, n - a.n0) + off;
+        *o = a.accumulate ? *o + acc : acc;
+    }
+}
+
+// blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks
+template <int NH>
+__global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
+{
+    constexpr int HM = (NH - 1) / 2, NW = TL_JC + 2 * HM;
+    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    if (X >= a.x_hi) return;
+    const int Z = a.z_lo + blockIdx.y;
+    const long long pp = (long long)Z * a.NXP + X;
+    float acc[NH];
+#pragma unroll
+    for (int i = 0; i < NH; ++i) acc[i] = 0.f;
+    for (int s = 0; s < a.S; ++s) {
+        const long long off = (long long)s * a.P + pp;
+        for (int r = 0; r < 2 * a.lag; ++r) {
+            for (int base = a.n0 + r; base < a.n1; base += 2 * a.lag * TL_JC) {
+                float win[NW], lv[TL_JC];
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    const int m = base + 2 * a.lag * (k - HM);
+                    win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + tl_slot(a.D, m) + off) : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < TL_JC; ++j) {
+                    const int n = base + 2 * a.lag * j;
+                    lv[j] = n < a.n1 ? __ldg(a.L.base + tl_slot(a.L, n) + off) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < NH; ++i)
+#pragma unroll
+                    for (int j = 0; j < TL_JC; ++j) acc[i] = fmaf(win[j - i + 2 * HM], lv[j], acc[i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NH; ++i) a.img[i * a.P + pp] += acc[i];
+}
+
+__global__ void __launch_bounds__(TL_TX) k_tlag_image_gen(const TlagArgs a)
+{
+    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    if (X >= a.x_hi) return;
+    const int Z = a.z_lo + blockIdx.y;
+    const long long pp = (long long)Z * a.NXP + X;
+    const int hm = (a.nh - 1) / 2;
+    for (int i = 0; i < a.nh; ++i) {
+        float acc = 0.f;
+        for (int s = 0; s < a.S; ++s) {
+            const long long off = (long long)s * a.P + pp;
+            for (int n = a.n0; n < a.n1; ++n) {
+                const int m = n - 2 * a.lag * (i - hm);
+                if (m >= 0 && m <= a.nt - 2)
+                    acc = fmaf(__ldg(a.D.base + tl_slot(a.D, m) + off), __ldg(a.L.base + tl_slot(a.L, n) + off), acc);
+            }
+        }
+        a.img[i * a.P + pp] += acc;
+    }
+}
+
+cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
+{
+    if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
+    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag * a.nchunk);
+#define FWIME_TL_SC(NH)                                                                    \
+    case NH:                                                                               \
+        if (a.sigma > 0) k_tlag_scatter<NH, 1><<<grid, TL_TX, 0, st>>>(a);                 \
+        else k_tlag_scatter<NH, -1><<<grid, TL_TX, 0, st>>>(a);                            \
+        break;
+    switch (a.nh) {
+        FWIME_TL_SC(1) FWIME_TL_SC(3) FWIME_TL_SC(5) FWIME_TL_SC(11) FWIME_TL_SC(21) FWIME_TL_SC(31) FWIME_TL_SC(41)
+    default: k_tlag_scatter_gen<<<grid, TL_TX, 0, st>>>(a);
+    }
+#undef FWIME_TL_SC
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
+{
+    if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
+    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo);
+    switch (a.nh) {
+    case 1: k_tlag_image<1><<<grid, TL_TX, 0, st>>>(a); break;
+    case 3: k_tlag_image<3><<<grid, TL_TX, 0, st>>>(a); break;
+    case 5: k_tlag_image<5><<<grid, TL_TX, 0, st>>>(a); break;
+    case 11: k_tlag_image<11><<<grid, TL_TX, 0, st>>>(a); break;
+    case 21: k_tlag_image<21><<<grid, TL_TX, 0, st>>>(a); break;
+    case 31: k_tlag_image<31><<<grid, TL_TX, 0, st>>>(a); break;
+    case 41: k_tlag_image<41><<<grid, TL_TX, 0, st>>>(a); break;
+    default: k_tlag_image_gen<<<grid, TL_TX, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int tlag_chunks(int K, int lag) { return (K + 2 * lag * TL_JC - 1) / (2 * lag * TL_JC); }
+
+}  // namespace fwk
