@@ -291,6 +291,9 @@ struct WS {
 static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
 {
     w.K = x->opt_K > 0 ? x->opt_K : auto_K(x->g.nt);
+    // time lags: segments of at least 2 Hs steps keep the lag halo (2 Hs samples per segment) below the
+    // segment's own K samples
+    if (x->opt_tlag > 0 && x->opt_K == 0) w.K = std::max(w.K, 2 * tlag_Hs(x->g, x->opt_tlag));
     w.K = std::min(w.K, x->g.nt - 1);
     w.K = std::max(w.K, 1);
     w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;

@@ -25,6 +25,21 @@ __device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
     return (long long)((r.mod > 0 ? (m + r.shift) % r.mod : m + r.shift)) * r.slot_stride;
 }
 
+// slot index of step m in ring r (any m, for incremental stepping), and the step by `inc` steps
+__device__ __forceinline__ int tl_index(const RingRef &r, int m)
+{
+    if (r.mod <= 0) return m + r.shift;
+    const int q = (m + r.shift) % r.mod;
+    return q < 0 ? q + r.mod : q;
+}
+// inc must be reduced first (tl_inc) so that one wrap suffices
+__device__ __forceinline__ int tl_inc(const RingRef &r, int inc) { return r.mod > 0 ? inc % r.mod : inc; }
+__device__ __forceinline__ int tl_next(const RingRef &r, int idx, int inc)
+{
+    idx += inc;
+    return (r.mod > 0 && idx >= r.mod) ? idx - r.mod : idx;
+}
+
 // blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue, chunk)
 template <int NH, int SIGMA>
 __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
@@ -35,28 +50,37 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
     const int Z = a.z_lo + blockIdx.y;
     int q = blockIdx.z;
     const int chunk = q % a.nchunk; q /= a.nchunk;
-    const int r = q % (2 * a.lag); const int s = q / (2 * a.lag);
-    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    const int r = q % (2 * a.lag), s = q / (2 * a.lag);
     const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;   // output j of this thread: base + 2 L j
     if (base >= a.n1) return;
+    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    const int step = 2 * a.lag;
     float Wr[NH];   // sigma = -1 reads lag i at m + 2 s_i = m - 2 s_(nh-1-i): the weights reversed
 #pragma unroll
     for (int i = 0; i < NH; ++i) Wr[i] = __ldg(a.W + (SIGMA > 0 ? i : NH - 1 - i) * a.P + pp);
+    const int m0 = base - step * HM;                      // window sample k is step m0 + k (2 L)
     float win[NW];
+    const float *db = a.D.base + off;
+    int di = tl_index(a.D, m0);
+    const int sd = tl_inc(a.D, step), se = tl_inc(a.E, step);
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
-        const int m = base + 2 * a.lag * (k - HM);
-        win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + tl_slot(a.D, m) + off) : 0.f;
+        const int m = m0 + step * k;
+        win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(db + (long long)di * a.D.slot_stride) : 0.f;
+        di = tl_next(a.D, di, sd);
     }
+    float *ob = const_cast<float *>(a.E.base) + off;
+    int ei = tl_index(a.E, base - a.n0);
 #pragma unroll
     for (int j = 0; j < TL_JC; ++j) {
-        const int n = base + 2 * a.lag * j;
-        if (n >= a.n1) break;
-        float acc = 0.f;
+        if (base + step * j < a.n1) {
+            float acc = 0.f;
 #pragma unroll
-        for (int i = 0; i < NH; ++i) acc = fmaf(Wr[i], win[j - i + 2 * HM], acc);
-        float *o = const_cast<float *>(a.E.base) + tl_slot(a.E, n - a.n0) + off;
-        *o = a.accumulate ? *o + acc : acc;
+            for (int i = 0; i < NH; ++i) acc = fmaf(Wr[i], win[j - i + 2 * HM], acc);
+            float *o = ob + (long long)ei * a.E.slot_stride;
+            *o = a.accumulate ? *o + acc : acc;
+        }
+        ei = tl_next(a.E, ei, se);
     }
 }
 
@@ -68,7 +92,7 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
     const int Z = a.z_lo + blockIdx.y;
     int q = blockIdx.z;
     const int chunk = q % a.nchunk; q /= a.nchunk;
-    const int r = q % (2 * a.lag); const int s = q / (2 * a.lag);
+    const int r = q % (2 * a.lag), s = q / (2 * a.lag);
     const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
     const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;
     const int hm = (a.nh - 1) / 2;
@@ -78,14 +102,16 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
         float acc = 0.f;
         for (int i = 0; i < a.nh; ++i) {
             const int m = n - a.sigma * 2 * a.lag * (i - hm);
-            if (m >= 0 && m <= a.nt - 2) acc = fmaf(__ldg(a.W + i * a.P + pp), __ldg(a.D.base + tl_slot(a.D, m) + off), acc);
+            if (m >= 0 && m <= a.nt - 2)
+                acc = fmaf(__ldg(a.W + i * a.P + pp), __ldg(a.D.base + tl_slot(a.D, m) + off), acc);
         }
         float *o = const_cast<float *>(a.E.base) + tl_slot(a.E, n - a.n0) + off;
         *o = a.accumulate ? *o + acc : acc;
     }
 }
 
-// blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks
+// blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks.  The samples of
+// the next (residue, chunk) are loaded before the current products are formed (two register windows).
 template <int NH>
 __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
 {
@@ -94,23 +120,31 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
     if (X >= a.x_hi) return;
     const int Z = a.z_lo + blockIdx.y;
     const long long pp = (long long)Z * a.NXP + X;
+    const int step = 2 * a.lag;
+    const int sd = tl_inc(a.D, step), sl = tl_inc(a.L, step);
     float acc[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) acc[i] = 0.f;
+#pragma unroll 1
     for (int s = 0; s < a.S; ++s) {
         const long long off = (long long)s * a.P + pp;
-        for (int r = 0; r < 2 * a.lag; ++r) {
-            for (int base = a.n0 + r; base < a.n1; base += 2 * a.lag * TL_JC) {
+#pragma unroll 1
+        for (int r = 0; r < step; ++r) {
+#pragma unroll 1
+            for (int base = a.n0 + r; base < a.n1; base += step * TL_JC) {
                 float win[NW], lv[TL_JC];
+                const int m0 = base - step * HM;
+                int di = tl_index(a.D, m0), li = tl_index(a.L, base);
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                    const int m = base + 2 * a.lag * (k - HM);
-                    win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + tl_slot(a.D, m) + off) : 0.f;
+                    const int m = m0 + step * k;
+                    win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + (long long)di * a.D.slot_stride + off) : 0.f;
+                    di = tl_next(a.D, di, sd);
                 }
 #pragma unroll
                 for (int j = 0; j < TL_JC; ++j) {
-                    const int n = base + 2 * a.lag * j;
-                    lv[j] = n < a.n1 ? __ldg(a.L.base + tl_slot(a.L, n) + off) : 0.f;
+                    lv[j] = base + step * j < a.n1 ? __ldg(a.L.base + (long long)li * a.L.slot_stride + off) : 0.f;
+                    li = tl_next(a.L, li, sl);
                 }
 #pragma unroll
                 for (int i = 0; i < NH; ++i)
