@@ -51,7 +51,8 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("W", ctypes.c_int),
                 ("nt", ctypes.c_int), ("nh", ctypes.c_int),
-                ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("lag", ctypes.c_int)]
+                ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("lag", ctypes.c_int),
+                ("fs", ctypes.c_int)]
 
 
 class _Shot(ctypes.Structure):
@@ -83,7 +84,8 @@ def _L():
 @dataclass(frozen=True)
 class Grid:
     """Physical grid nz x nx at spacing dz, dx; sponge W points; nt samples at dt; nh extension points:
-    subsurface offsets (lag = 0) or time lags spaced lag * dt (lag > 0; B~ and B~* only)."""
+    subsurface offsets (lag = 0) or time lags spaced lag * dt (lag > 0); fs = 1: free surface (pressure
+    release) at the top physical row instead of a sponge."""
     nz: int
     nx: int
     W: int
@@ -93,6 +95,7 @@ class Grid:
     dz: float | None = None
     nh: int = 1
     lag: int = 0
+    fs: int = 0
 
     @property
     def NZ(self) -> int:
@@ -108,7 +111,7 @@ class Grid:
 
     def c(self) -> _Grid:
         dz = self.dx if self.dz is None else self.dz
-        return _Grid(self.nz, self.nx, self.W, self.nt, self.nh, float(dz), float(self.dx), float(self.dt), self.lag)
+        return _Grid(self.nz, self.nx, self.W, self.nt, self.nh, float(dz), float(self.dx), float(self.dt), self.lag, self.fs)
 
 
 def _d(a):

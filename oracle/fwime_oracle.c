@@ -31,6 +31,9 @@
  *   Born   secondary source b dv D2t q0, b = 2/v^3 (d c / d v = c b v).
  *   ext.   e^n(y) = sum_h W(y-h,h) D^n(y-2h), W = b p~, h along x, nh odd,
  *          terms whose points leave the active region dropped.
+ *   fs     (fs = 1) the top physical row is a pressure-release surface: after every
+ *          step q = 0 there and the 4 rows above hold the odd mirror -q of the 4
+ *          rows below (the projection M); rows further up are inactive.
  *   lags   (lag > 0) e^n(x) = sum_i W(x,i) D^{n-2 s_i}(x), s_i = (i-hm) lag, D^m = 0
  *          outside 0 <= m <= nt-2: lag tau couples the source side at t - tau
  *          with the receiver side at t + tau.
@@ -49,6 +52,7 @@ typedef struct {
     int nh;           /* number of extension points (odd): subsurface offsets, or time lags */
     double dz, dx, dt;
     int lag;          /* 0: subsurface-offset extension; > 0: time-lag extension, lags spaced lag*dt */
+    int fs;           /* 1: free surface (pressure release) at the top physical row instead of a sponge */
 } og_grid;
 
 /* ------------------------------------------------------------------ grid */
@@ -91,11 +95,13 @@ void og_prep(const og_grid *g, const double *v, double *c, double *gam, double *
     for (int IZ = 0; IZ < NZ; IZ++)
         for (int IX = 0; IX < NX; IX++) {
             size_t p = (size_t)IZ * NX + IX;
-            if (!is_active(g, IZ, IX)) { c[p] = 0.0; gam[p] = 0.0; continue; }
+            if (!is_active(g, IZ, IX) || (g->fs && IZ < o - 4)) { c[p] = 0.0; gam[p] = 0.0; continue; }
             int iz = clampi(IZ - o, 0, g->nz - 1), ix = clampi(IX - o, 0, g->nx - 1);
             double vv = v[(size_t)iz * g->nx + ix];
             c[p] = vv * vv * g->dt * g->dt;
-            gam[p] = taper1(outside(IZ, o, g->nz), g->W) * taper1(outside(IX, o, g->nx), g->W);
+            /* with a free surface there is no sponge on top (the mirror rows are overwritten by M) */
+            double gz = (g->fs && IZ < o) ? 1.0 : taper1(outside(IZ, o, g->nz), g->W);
+            gam[p] = gz * taper1(outside(IX, o, g->nx), g->W);
         }
     if (b)
         for (size_t i = 0; i < (size_t)g->nz * g->nx; i++) b[i] = 2.0 / (v[i] * v[i] * v[i]);
@@ -126,6 +132,29 @@ void og_lap(const og_grid *g, const double *q, double *out)
 /* --------------------------------------------------------------- one step */
 
 /* qn = gam (2 qc - gam qp + c (L qc + s)) at active points, 0 elsewhere; s may be NULL */
+/* free-surface projection M: q = 0 on the surface row, odd mirror on the 4 rows above */
+static void fs_project(const og_grid *g, double *q)
+{
+    int NX = og_NX(g), o = og_pad(g);
+    for (int IX = 0; IX < NX; IX++) {
+        q[(size_t)o * NX + IX] = 0.0;
+        for (int k = 1; k <= 4; k++) q[(size_t)(o - k) * NX + IX] = -q[(size_t)(o + k) * NX + IX];
+    }
+}
+
+/* its transpose M^T, in place on an adjoint field */
+static void fs_project_T(const og_grid *g, double *a)
+{
+    int NX = og_NX(g), o = og_pad(g);
+    for (int IX = 0; IX < NX; IX++) {
+        for (int k = 1; k <= 4; k++) {
+            a[(size_t)(o + k) * NX + IX] -= a[(size_t)(o - k) * NX + IX];
+            a[(size_t)(o - k) * NX + IX] = 0.0;
+        }
+        a[(size_t)o * NX + IX] = 0.0;
+    }
+}
+
 void og_step(const og_grid *g, const double *c, const double *gam, const double *qc,
              const double *qp, const double *s, double *qn)
 {
@@ -136,6 +165,7 @@ void og_step(const og_grid *g, const double *c, const double *gam, const double 
         double src = s ? s[p] : 0.0;
         qn[p] = gam[p] * (2.0 * qc[p] - gam[p] * qp[p] + c[p] * (lq[p] + src));
     }
+    if (g->fs) fs_project(g, qn);
     free(lq);
 }
 
@@ -144,12 +174,20 @@ void og_step(const og_grid *g, const double *c, const double *gam, const double 
  *   qc* = 2 gam qn* + L (c gam qn*),  qp* = -gam^2 qn*,  s* = c gam qn*
  * Any output pointer may be NULL.
  */
-void og_step_T(const og_grid *g, const double *c, const double *gam, const double *qn_s,
+void og_step_T(const og_grid *g, const double *c, const double *gam, const double *qn_s_in,
                double *qc_s, double *qp_s, double *s_s)
 {
     size_t P = (size_t)og_NZ(g) * og_NX(g);
     double *t = (double *)malloc(P * sizeof(double));
     double *lt = (double *)malloc(P * sizeof(double));
+    double *pr = NULL;
+    const double *qn_s = qn_s_in;
+    if (g->fs) {   /* the step's output passes through M: its adjoint through M^T first */
+        pr = (double *)malloc(P * sizeof(double));
+        memcpy(pr, qn_s_in, P * sizeof(double));
+        fs_project_T(g, pr);
+        qn_s = pr;
+    }
     for (size_t p = 0; p < P; p++) t[p] = c[p] * gam[p] * qn_s[p];
     og_lap(g, t, lt);
     for (size_t p = 0; p < P; p++) {
@@ -159,6 +197,7 @@ void og_step_T(const og_grid *g, const double *c, const double *gam, const doubl
     }
     free(t);
     free(lt);
+    free(pr);
 }
 
 /* ------------------------------------------------- dense time propagation */
