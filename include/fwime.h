@@ -98,12 +98,17 @@ enum {
                                        that v and w are not modified in between; any other operator call
                                        drops the states.  0 (default) frees them. */
     FWIME_OPT_BACKGROUND_REUSED = 11, /* read-only: 1 if the last call started from those states */
-    FWIME_OPT_TIME_LAG = 12         /* 0 (default): B~ / B~* extend with nh horizontal subsurface offsets;
+    FWIME_OPT_TIME_LAG = 12,        /* 0 (default): B~ / B~* extend with nh horizontal subsurface offsets;
                                        L > 0: with nh time lags tau_i = (i - (nh-1)/2) L dt, the symmetric
                                        convention (source side at t - tau, receiver side at t + tau):
                                        e^n(x) = sum_i b p~(x,i) D2t q0^{n - 2 (i-(nh-1)/2) L}(x).  Every
                                        operator (B~, B~*, T, T*, gradient, objective, VP solve) then uses
                                        the lag form. */
+    FWIME_OPT_FREE_SURFACE = 13     /* 1: pressure-release free surface at the top physical row (iz = 0)
+                                       instead of the top sponge: q = 0 there and the 4 rows above hold
+                                       the odd mirror of the 4 rows below after every step (forward and
+                                       adjoint); receivers on the surface row record 0.  Not available in
+                                       fwime_forward_group. */
 };
 
 /* Kernel families, for fwime_profile_read. */
@@ -167,7 +172,7 @@ int fwime_tomo_adj(fwime_ctx *ctx, const float *v, const float *w, const float *
  *   grad[nz][nx] = B* r + T* r (overwritten), *objective = Phi (host double,
  *   written when the call's work has completed, i.e. after fwime_sync).
  * D = diag(|ih - (nh-1)/2| + 1) is this library's reading of the paper's
- * "invertible modified DSO" operator; it does not enter the gradient. */
+ * invertible, modified DSO operator; it does not enter the gradient. */
 int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                    const float *dobs, float eps, float *grad, double *objective);
 

@@ -17,7 +17,7 @@ linear conjugate gradients for the variable projection step (Eqs. 2-5),
 for dot-product pins.
 
 Parity unpinned: the DSO weights of ``dso_penalty`` (a reading of the
-"invertible modified DSO" operator; only its arithmetic is pinned).
+invertible, modified DSO operator of the Theory section; only its arithmetic is pinned).
 """
 from __future__ import annotations
 

@@ -774,7 +774,7 @@ double og_gradient(const og_grid *g, const double *v, const og_shot *sh, const d
 
 /*
  * eps^2/2 ||D p~||^2 with D = diag(|ih - hm| + 1): one reading of the
- * "invertible modified DSO" operator named in the Theory section.
+ * invertible, modified DSO operator named in the Theory section.
  */
 double og_dso_penalty(const og_grid *g, const double *pt, double eps)
 {

@@ -58,6 +58,7 @@ struct fwime_ctx {
     // options
     int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0, opt_reuse_bg = 0;
     int opt_tlag = 0;               // > 0: B~ / B~* extend with time lags spaced opt_tlag steps
+    int opt_fs = 0;                 // 1: free surface at the top physical row
     // background-wavefield checkpoints of every shot, [nseg][2][nshot][P], written by B and B~ and
     // read by B* and B~* on the same v, w (FWIME_OPT_REUSE_BACKGROUND)
     struct BgCache {
@@ -472,6 +473,9 @@ static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out,
     const double per = 12.0 + (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) +
                        (fc ? 4 : 0);
     LAUNCH(FWIME_K_PROP, pts * (Sb * per + 4.0 + (coef ? 4.0 : 0.0)), launch_prop(a, Sb, x->st));
+    if (x->opt_fs)
+        LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * (d2 ? 44.0 : 40.0),
+               launch_free_surface(out, d2, Sb, x->P, x->NXP, x->o, x->st));
     return FWIME_OK;
 }
 
@@ -493,6 +497,9 @@ static int inject(Run &r, int Sb, float *fld, const float *val)
     a.nrec = x->nrec; a.P = x->P; a.rec_off = x->d_rec_off;
     a.fld = fld; a.val = val; a.vstride = (long long)x->g.nt * x->nrec; a.c = r.w.c;
     LAUNCH(FWIME_K_POINTS, (double)Sb * x->nrec * 12.0, launch_points(a, Sb, x->st));
+    // free surface: receivers within 4 rows of the surface change rows whose mirror the next step reads
+    if (x->opt_fs)
+        LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * 40.0, launch_free_surface(fld, nullptr, Sb, x->P, x->NXP, x->o, x->st));
     return FWIME_OK;
 }
 
@@ -562,6 +569,7 @@ static int prep_model(fwime_ctx *x, Run &r, const float *v)
                               std::sqrt(LAMBDA_MAX * (1.0 / ((double)x->g.dx * x->g.dx) + 1.0 / ((double)x->g.dz * x->g.dz))));
     a.cfl_limit2 = (float)(lim * lim);
     a.v = v; a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx; a.bpad = r.w.bpad; a.status = x->d_status;
+    a.fs = x->opt_fs;
     LAUNCH(FWIME_K_OTHER, 12.0 * x->NZ * x->NXP, launch_prep(a, x->st));
     return FWIME_OK;
 }
@@ -1349,7 +1357,7 @@ static int run_call(fwime_ctx *x, const Call &c)
     snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d|%d%d|%p|%d", c.op, (const void *)c.v, (const void *)c.w,
              (const void *)c.in1, (const void *)c.in2, (void *)c.out, c.accumulate, (double)c.eps, x->opt_S, x->opt_K,
              x->opt_zchunk, use_bg ? 1 : 0, write_bg ? 1 : 0, (const void *)(use_bg || write_bg ? x->bg.buf : nullptr),
-             x->opt_tlag);
+             x->opt_tlag * 2 + x->opt_fs);
     auto it = x->graphs.find(key);
     if (it == x->graphs.end()) {
         CK(cudaStreamBeginCapture(x->st, cudaStreamCaptureModeThreadLocal));
@@ -1531,6 +1539,10 @@ int fwime_set_option(fwime_ctx *x, int option, long long value)
     case FWIME_OPT_HOST_IO: x->opt_host_io = value != 0; return FWIME_OK;
     case FWIME_OPT_ZCHUNK: if (value < 0 || value > 4096) break; x->opt_zchunk = (int)value; return FWIME_OK;
     case FWIME_OPT_PROFILE: x->opt_profile = value != 0; return FWIME_OK;
+    case FWIME_OPT_FREE_SURFACE:
+        x->opt_fs = value != 0;
+        x->bg.valid = false;
+        return FWIME_OK;
     case FWIME_OPT_TIME_LAG:
         if (value < 0 || value > 100000) break;
         x->opt_tlag = (int)value;
@@ -1565,6 +1577,7 @@ int fwime_get_option(fwime_ctx *x, int option, long long *value)
     case FWIME_OPT_REUSE_BACKGROUND: *value = x->opt_reuse_bg; return FWIME_OK;
     case FWIME_OPT_BACKGROUND_REUSED: *value = x->bg_used; return FWIME_OK;
     case FWIME_OPT_TIME_LAG: *value = x->opt_tlag; return FWIME_OK;
+    case FWIME_OPT_FREE_SURFACE: *value = x->opt_fs; return FWIME_OK;
     }
     return fail(x, FWIME_EINVAL, "bad option %d", option);
 }
@@ -1755,6 +1768,7 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
         if (!ctxs[i] || !v[i] || !w[i] || !d[i]) return fail(x, FWIME_EINVAL, "null member %d", i);
         if (ctxs[i]->st != x->st) return fail(x, FWIME_EINVAL, "group members must share one stream");
         if (ctxs[i]->capturing || ctxs[i]->opt_host_io) return fail(x, FWIME_EINVAL, "member %d: capture/host I/O", i);
+        if (ctxs[i]->opt_fs) return fail(x, FWIME_EINVAL, "member %d: the grouped forward has no free surface", i);
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return fail(x, FWIME_EINVAL, "member %d repeats member %d", i, j);
     }

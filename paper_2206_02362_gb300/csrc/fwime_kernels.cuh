@@ -148,8 +148,10 @@ struct PrepArgs {
     const float *v;                // [nz][nx]
     float *c, *gz, *gx, *bpad;     // padded outputs
     int *status;
+    int fs;                        // 1: free surface at the top physical row
 };
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st);
+cudaError_t launch_free_surface(float *q, float *d2, int nshot, long long P, int NXP, int o, cudaStream_t st);
 
 // elementwise helpers on padded / physical grids
 cudaError_t launch_embed_scale(const float *phys, const float *scale_pad, float *out_pad, int nz, int nx,

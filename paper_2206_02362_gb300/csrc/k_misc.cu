@@ -29,12 +29,37 @@ __global__ void k_prep(const PrepArgs a)
     const int iz = min(max(IZ - a.o, 0), a.nz - 1), ix = min(max(IX - a.o, 0), a.nx - 1);
     const float vv = a.v[(long long)iz * a.nx + ix];
     const long long p = (long long)IZ * a.NXP + IX;
-    a.c[p] = act ? vv * vv * a.dt * a.dt : 0.f;
+    // free surface: no sponge on top, the 4 mirror rows above the surface row are rewritten after every
+    // step, rows further up are inactive; c = 0 on the surface row (nothing is injected there)
+    const bool dead = a.fs && (IZ < a.o - 4 || IZ == a.o);
+    a.c[p] = act && !dead ? vv * vv * a.dt * a.dt : 0.f;
     const bool phys = IZ >= a.o && IZ < a.o + a.nz && IX >= a.o && IX < a.o + a.nx;
     a.bpad[p] = phys ? 2.f / (vv * vv * vv) : 0.f;
     if (phys && !(vv > 0.f && vv * vv < a.cfl_limit2)) atomicOr(a.status, ST_CFL);
     if (IZ == 0) a.gx[IX] = (IX >= 4 && IX < a.NX - 4) ? taper1(outside(IX, a.o, a.nx), a.W) : 0.f;
-    if (IX == 0) a.gz[IZ] = (IZ >= 4 && IZ < a.NZ - 4) ? taper1(outside(IZ, a.o, a.nz), a.W) : 0.f;
+    if (IX == 0)
+        a.gz[IZ] = (IZ >= 4 && IZ < a.NZ - 4 && !(a.fs && IZ < a.o - 4))
+                       ? ((a.fs && IZ < a.o) ? 1.f : taper1(outside(IZ, a.o, a.nz), a.W))
+                       : 0.f;
+}
+
+// free surface (pressure release at the top physical row IZ = o): after a step, q = 0 on the surface row
+// and the 4 rows above hold the odd mirror -q of the 4 rows below; D2t is 0 on the surface row
+__global__ void k_free_surface(float *q, float *d2, long long P, int NXP, int o)
+{
+    const int IX = blockIdx.x * blockDim.x + threadIdx.x;
+    if (IX >= NXP) return;
+    const long long f = (long long)blockIdx.y * P + IX;
+    q[f + (long long)o * NXP] = 0.f;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) q[f + (long long)(o - k) * NXP] = -q[f + (long long)(o + k) * NXP];
+    if (d2) d2[f + (long long)o * NXP] = 0.f;
+}
+
+cudaError_t launch_free_surface(float *q, float *d2, int nshot, long long P, int NXP, int o, cudaStream_t st)
+{
+    k_free_surface<<<dim3((NXP + 127) / 128, nshot), 128, 0, st>>>(q, d2, P, NXP, o);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st)
