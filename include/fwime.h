@@ -104,11 +104,18 @@ enum {
                                        e^n(x) = sum_i b p~(x,i) D2t q0^{n - 2 (i-(nh-1)/2) L}(x).  Every
                                        operator (B~, B~*, T, T*, gradient, objective, VP solve) then uses
                                        the lag form. */
-    FWIME_OPT_FREE_SURFACE = 13     /* 1: pressure-release free surface at the top physical row (iz = 0)
+    FWIME_OPT_FREE_SURFACE = 13,    /* 1: pressure-release free surface at the top physical row (iz = 0)
                                        instead of the top sponge: q = 0 there and the 4 rows above hold
                                        the odd mirror of the 4 rows below after every step (forward and
                                        adjoint); receivers on the surface row record 0.  Not available in
                                        fwime_forward_group. */
+    FWIME_OPT_TWO_STEP = 14        /* 1: the forward, background and scattered propagations of f, B~ and
+                                       the adjoints' recomputations advance two time steps per stencil
+                                       launch (temporal blocking: 16 instead of 24 bytes per two updates;
+                                       identical arithmetic); 0 (default): one step per launch, which
+                                       measures faster on GB300 (the one-step stencil is issue-bound, not
+                                       byte-bound).  Not used with the free surface, the plain path or
+                                       time lags. */
 };
 
 /* Kernel families, for fwime_profile_read. */

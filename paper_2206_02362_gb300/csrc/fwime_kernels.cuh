@@ -50,6 +50,24 @@ struct PropArgs {
     int naux_max;                  // rows per aux stage (set by launch_prop)
 };
 
+// two time steps per launch (k_prop2): q^{n+1} -> out1, q^{n+2} -> out2 (both distinct from cur, prev)
+struct Prop2Args {
+    int NZ, NXP, zchunk, nstrip, nchunk;
+    long long P;
+    float ax[5], az[5];
+    float inv_dt2;
+    const float *c, *gz, *gx;
+    const float *cur, *prev;       // q^n, q^{n-1}
+    float *out1, *out2;            // q^{n+1}, q^{n+2}
+    float *d2a, *d2b;              // optional D2t of steps n and n+1
+    const int *src_off;            // optional point source; amplitudes of steps n, n+1 at src_amp[s*stride + 0, 1]
+    const float *src_amp;
+    long long src_stride;
+    float src_scale;
+    const float *f0, *f1;          // optional dense local source of steps n and n+1 (weight a0)
+    float a0;
+};
+
 // grouped forward: one member = one shot batch on its own grid
 struct GroupMember {
     PropArgs a[2];                 // even / odd steps (cur and prev swap); src_amp = wavelet base
@@ -131,6 +149,8 @@ struct TlagArgs {
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
+cudaError_t launch_prop2(const Prop2Args &a, int nshot, cudaStream_t st);
+int prop2_strips(int NXP);         // warps per row of a two-step launch (120 owned columns each)
 cudaError_t prop_occupancy(int *blocks_per_sm);
 cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const GroupRec *g, int nrec_threads,
                               int step, cudaStream_t st, bool record);
