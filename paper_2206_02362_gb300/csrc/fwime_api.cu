@@ -1883,6 +1883,7 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
         a.src_off = m->d_src_off; a.src_amp = w[i]; a.src_stride = m->g.nt;
         a.f0 = a.f1 = a.f2 = a.coef = a.fc = nullptr;
         a.naux_max = 2;
+        prop_pairs(a);
         gm[k].a[0] = a; gm[k].a[0].cur = r.w.f[0]; gm[k].a[0].prev = r.w.f[1]; gm[k].a[0].out = r.w.f[1];
         gm[k].a[1] = a; gm[k].a[1].cur = r.w.f[1]; gm[k].a[1].prev = r.w.f[0]; gm[k].a[1].out = r.w.f[0];
         gm[k].ctas_per_shot = (r.nstrip * r.nchunk + PROP_WARPS - 1) / PROP_WARPS;

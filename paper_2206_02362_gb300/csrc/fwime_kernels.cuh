@@ -48,7 +48,24 @@ struct PropArgs {
     float a0, a1, a2;
     const float *coef, *fc;
     int naux_max;                  // rows per aux stage (set by launch_prop)
+    // each scalar twice, the operands of the packed two-lane (f32x2) arithmetic (set by prop_pairs)
+    float2 kx2[5], kz2[5], axc2, inv2, a02, a12, a22;
 };
+
+// Fills the packed-operand copies of a's coefficients (host side, after they are final).
+inline void prop_pairs(PropArgs &a)
+{
+    for (int k = 0; k < 5; ++k) {
+        a.kx2[k] = make_float2(a.ax[k], a.ax[k]);
+        a.kz2[k] = make_float2(a.az[k], a.az[k]);
+    }
+    const float axc = a.ax[0] + a.az[0];
+    a.axc2 = make_float2(axc, axc);
+    a.inv2 = make_float2(a.inv_dt2, a.inv_dt2);
+    a.a02 = make_float2(a.a0, a.a0);
+    a.a12 = make_float2(a.a1, a.a1);
+    a.a22 = make_float2(a.a2, a.a2);
+}
 
 // two time steps per launch (k_prop2): q^{n+1} -> out1, q^{n+2} -> out2 (both distinct from cur, prev)
 struct Prop2Args {
@@ -197,5 +214,45 @@ cudaError_t launch_dso_add(const float *p, float *hp, int nh, long long PP, floa
 cudaError_t launch_axpby_dev(float *y, const float *x, long long n, const double *sc, int ia, float sa, int ib,
                              cudaStream_t st);
 cudaError_t launch_cg_scalars(double *sc, int mode, double *history, int k, cudaStream_t st);
+
+// ---- packed two-lane FP32 arithmetic (add/sub/mul/fma.rn.f32x2, sm_100 and later): one instruction
+// performs the operation on two independent FP32 values held in a 64-bit register pair, each with
+// the rounding of the scalar instruction, so it halves the floating-point issue slots.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 bits(const float2 &v) { return *reinterpret_cast<const f32x2 *>(&v); }
 
 }  // namespace fwk

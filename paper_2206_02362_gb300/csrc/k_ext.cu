@@ -167,6 +167,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_SC_A21
 #define FWIME_SC_A21 4
 #endif
+#ifndef FWIME_SC_F32X2
+#define FWIME_SC_F32X2 0
+#endif
 constexpr int SC_WARPS = FWIME_SC_WARPS;     // warps per CTA (independent pipelines)
 constexpr int SC_STAGES = FWIME_SC_STAGES;   // cp.async ring depth per warp
 
@@ -215,6 +218,30 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
             Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
         }
     }
+    // packed two-lane arithmetic where the weights leave room for their pairs (no spills)
+    constexpr bool PACK = FWIME_SC_F32X2 && NH * A <= 96;
+    // Packed form: output j reads dv[j + o] at offset ih, o = HM - SIGMA (ih - HM), and o has the
+    // parity of ih.  For even o the pairs of outputs (0, 1) and (2, 3) read the aligned register
+    // pairs (dv[o], dv[o + 1]), (dv[o + 2], dv[o + 3]); for odd o the pair (1, 2) reads the aligned
+    // (dv[o + 1], dv[o + 2]) and outputs 0 and 3 stay scalar.  Each output sums its even-o and
+    // odd-o products separately (two chains, as in the scalar form).
+    constexpr int NE = PACK ? (NH + 1) / 2 : 1, NO = PACK && NH / 2 > 0 ? NH / 2 : 1;   // even / odd o (o = ih mod 2)
+    f32x2 WE[NE][A / 2], WO[NO];
+    float WO0[NO], WO3[NO];
+#pragma unroll
+    for (int ih = 0; ih < (PACK ? NH : 0); ++ih) {
+        if (ih % 2 == 0) {
+#pragma unroll
+            for (int q = 0; q < A / 2; ++q) WE[ih / 2][q] = pk(Wr[2 * q][ih], Wr[2 * q + 1][ih]);
+        } else if (A == 4) {
+            WO[ih / 2] = pk(Wr[1][ih], Wr[A - 2][ih]);
+            WO0[ih / 2] = Wr[0][ih];
+            WO3[ih / 2] = Wr[A - 1][ih];
+        } else {
+            WO0[ih / 2] = Wr[0][ih];
+            WO3[ih / 2] = Wr[A - 1][ih];
+        }
+    }
     // the lane copies window samples n = lane + 32 c (column wal + n) into its parity's array
     const unsigned sm0 =
         static_cast<unsigned>(__cvta_generic_to_shared(wsm)) + 4u * ((lane & 1) * Sh::OFF + (lane >> 1));
@@ -255,21 +282,49 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
         float dv[Sh::NWV];                         // dv[k] = D(yf - 2 HM + 2k)
         lds_vec<Sh::VW>(dv, lsm + st_c);
         st_c = st_c + Sh::STG == NS * Sh::STG ? 0 : st_c + Sh::STG;
-        // two partial sums per output (even / odd offsets): 2 A independent chains.  Offsets are
-        // visited in the order of their samples, so the first products wait only for the first load.
-        float acc[2][A];
-#pragma unroll
-        for (int j = 0; j < A; ++j) acc[0][j] = acc[1][j] = 0.f;
-#pragma unroll
-        for (int m = 0; m < NH; ++m) {
-            const int ih = SIGMA > 0 ? NH - 1 - m : m;
-#pragma unroll
-            for (int j = 0; j < A; ++j)            // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
-                acc[m & 1][j] = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], acc[m & 1][j]);
-        }
         float e[A];
+        if constexpr (PACK) {
+            f32x2 ae[A / 2], ao = pk(0.f, 0.f);
+            float ao0 = 0.f, ao3 = 0.f;
 #pragma unroll
-        for (int j = 0; j < A; ++j) e[j] = acc[0][j] + acc[1][j];
+            for (int q = 0; q < A / 2; ++q) ae[q] = pk(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < NH; ++m) {             // offsets in the order of their samples
+                const int ih = SIGMA > 0 ? NH - 1 - m : m;
+                const int o = HM - SIGMA * (ih - HM);
+                if (ih % 2 == 0) {
+#pragma unroll
+                    for (int q = 0; q < A / 2; ++q) ae[q] = fma2(WE[ih / 2][q], pk(dv[o + 2 * q], dv[o + 2 * q + 1]), ae[q]);
+                } else {
+                    if (A == 4) ao = fma2(WO[ih / 2], pk(dv[o + 1], dv[o + 2]), ao);
+                    ao0 = fmaf(WO0[ih / 2], dv[o], ao0);
+                    ao3 = fmaf(WO3[ih / 2], dv[o + A - 1], ao3);
+                }
+            }
+            float el[A], ol[A];
+#pragma unroll
+            for (int q = 0; q < A / 2; ++q) upk(ae[q], el[2 * q], el[2 * q + 1]);
+            ol[0] = ao0;
+            ol[A - 1] = ao3;
+            if (A == 4) upk(ao, ol[1], ol[A - 2]);
+#pragma unroll
+            for (int j = 0; j < A; ++j) e[j] = el[j] + ol[j];
+        } else {
+            // two partial sums per output (even / odd offsets): 2 A independent chains.  Offsets are
+            // visited in the order of their samples, so the first products wait only for the first load.
+            float acc[2][A];
+#pragma unroll
+            for (int j = 0; j < A; ++j) acc[0][j] = acc[1][j] = 0.f;
+#pragma unroll
+            for (int m = 0; m < NH; ++m) {
+                const int ih = SIGMA > 0 ? NH - 1 - m : m;
+#pragma unroll
+                for (int j = 0; j < A; ++j)            // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
+                    acc[m & 1][j] = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], acc[m & 1][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < A; ++j) e[j] = acc[0][j] + acc[1][j];
+        }
         float v[A];
         if constexpr (A == 4) {
             const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[0] : e[2], 16);

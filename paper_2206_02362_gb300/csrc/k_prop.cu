@@ -76,6 +76,116 @@ constexpr int AUX_SLOTS = FWIME_PROP_AUX_SLOTS;   // pipeline depth of the q^{n-
 constexpr int CUR_ROW = STRIP + 8;
 static_assert(CUR_SLOTS >= AUX_SLOTS + 4, "the q^n ring must hold rows z .. z+4+depth");
 
+// The arithmetic of one output row of a lane (four consecutive columns): the Laplacian from the
+// x-neighbours (L | Q4 | Rr, 12 consecutive samples) and the nine queue rows Q0..Q8 (the output row
+// is Q4), then the sponge-damped update and optionally D2t.  In the scalar form every product and
+// sum is the same as
+//   lap = (ax0 + az0) q + sum_k ax_k (q[x-k] + q[x+k]) + sum_k az_k (q[z-k] + q[z+k])   (k = 1..4)
+//   out = g (2 q - g p + c (lap + s)),   d2 = (out - 2 q + p) / dt^2.
+#ifndef FWIME_PROP_F32X2
+#define FWIME_PROP_F32X2 1
+#endif
+#if FWIME_PROP_F32X2
+// Packed two-lane FP32 (f32x2, see fwime_kernels.cuh) on columns (j, j + 1): half the floating-point
+// issue slots of the scalar form, with its rounding.
+// columns (2 h, 2 h + 1) of a float4
+__device__ __forceinline__ f32x2 half2(const float4 &v, int h) { return h == 0 ? pk(v.x, v.y) : pk(v.z, v.w); }
+
+template <bool LOCAL, bool D2, bool SRC>
+__device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
+                                         const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
+                                         const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
+                                         const float4 &pv, const float4 &cv, const float4 &lf0, const float4 &lf1,
+                                         const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
+                                         const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
+{
+    const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};
+    const f32x2 GZ = pk(gzz, gzz), NGZ = pk(-gzz, -gzz);
+    float ov[4], dv[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = 2 * h;
+        const f32x2 C0 = half2(Q4, h);
+        f32x2 lap = mul2(bits(a.axc2), C0);
+        lap = fma2(bits(a.kx2[1]), add2(pk(rr[j + 3], rr[j + 4]), pk(rr[j + 5], rr[j + 6])), lap);
+        lap = fma2(bits(a.kx2[2]), add2(pk(rr[j + 2], rr[j + 3]), pk(rr[j + 6], rr[j + 7])), lap);
+        lap = fma2(bits(a.kx2[3]), add2(pk(rr[j + 1], rr[j + 2]), pk(rr[j + 7], rr[j + 8])), lap);
+        lap = fma2(bits(a.kx2[4]), add2(pk(rr[j + 0], rr[j + 1]), pk(rr[j + 8], rr[j + 9])), lap);
+        lap = fma2(bits(a.kz2[1]), add2(half2(Q3, h), half2(Q5, h)), lap);
+        lap = fma2(bits(a.kz2[2]), add2(half2(Q2, h), half2(Q6, h)), lap);
+        lap = fma2(bits(a.kz2[3]), add2(half2(Q1, h), half2(Q7, h)), lap);
+        lap = fma2(bits(a.kz2[4]), add2(half2(Q0, h), half2(Q8, h)), lap);
+        if (LOCAL || SRC) {
+            f32x2 sv = pk(0.f, 0.f);
+            if (LOCAL) {
+                sv = fma2(bits(a.a02), half2(lf0, h), sv);
+                sv = fma2(bits(a.a12), half2(lf1, h), sv);
+                sv = fma2(bits(a.a22), half2(lf2, h), sv);
+                sv = fma2(half2(lcf, h), half2(lfc, h), sv);
+            }
+            if (SRC) sv = add2(sv, pk(sj == j ? amp : 0.f, sj == j + 1 ? amp : 0.f));
+            lap = add2(lap, sv);
+        }
+        const f32x2 GX = half2(gxv, h);
+        const f32x2 G = mul2(GZ, GX), NG = mul2(NGZ, GX);
+        const f32x2 P = half2(pv, h);
+        const f32x2 TC = add2(C0, C0);
+        const f32x2 O = mul2(G, fma2(half2(cv, h), lap, fma2(NG, P, TC)));
+        upk(O, ov[j], ov[j + 1]);
+        if (D2) {
+            const f32x2 D = mul2(add2(sub2(O, TC), P), bits(a.inv2));
+            upk(D, dv[j], dv[j + 1]);
+        }
+    }
+    o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    if (D2) d2 = make_float4(dv[0], dv[1], dv[2], dv[3]);
+}
+#else
+template <bool LOCAL, bool D2, bool SRC>
+__device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
+                                         const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
+                                         const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
+                                         const float4 &pv, const float4 &cv, const float4 &lf0, const float4 &lf1,
+                                         const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
+                                         const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
+{
+    const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};
+    const float axc = a.ax[0] + a.az[0];
+    float ov[4], dv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float c0v = rr[j + 4];
+        float lap = axc * c0v;
+        lap = fmaf(a.ax[1], rr[j + 3] + rr[j + 5], lap);
+        lap = fmaf(a.ax[2], rr[j + 2] + rr[j + 6], lap);
+        lap = fmaf(a.ax[3], rr[j + 1] + rr[j + 7], lap);
+        lap = fmaf(a.ax[4], rr[j + 0] + rr[j + 8], lap);
+        lap = fmaf(a.az[1], cmp(Q3, j) + cmp(Q5, j), lap);
+        lap = fmaf(a.az[2], cmp(Q2, j) + cmp(Q6, j), lap);
+        lap = fmaf(a.az[3], cmp(Q1, j) + cmp(Q7, j), lap);
+        lap = fmaf(a.az[4], cmp(Q0, j) + cmp(Q8, j), lap);
+        if (LOCAL || SRC) {
+            float sv = 0.f;
+            if (LOCAL) {
+                sv = fmaf(a.a0, cmp(lf0, j), sv);
+                sv = fmaf(a.a1, cmp(lf1, j), sv);
+                sv = fmaf(a.a2, cmp(lf2, j), sv);
+                sv = fmaf(cmp(lcf, j), cmp(lfc, j), sv);
+            }
+            if (SRC) sv += sj == j ? amp : 0.f;
+            lap += sv;
+        }
+        const float g = gzz * cmp(gxv, j);
+        const float pj = cmp(pv, j);
+        const float tc = c0v + c0v;
+        ov[j] = g * fmaf(cmp(cv, j), lap, fmaf(-g, pj, tc));
+        dv[j] = (ov[j] - tc + pj) * a.inv_dt2;
+    }
+    o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    if (D2) d2 = make_float4(dv[0], dv[1], dv[2], dv[3]);
+}
+#endif
+
 // The time step of one warp's work item (strip, chunk) of shot `shot`; wsm is the warp's shared
 // memory (CUR_SLOTS x CUR_ROW + AUX_SLOTS x naux_max x STRIP floats).
 template <bool LOCAL, bool D2, bool SRC>
@@ -150,7 +260,6 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         soff = a.src_off[shot];
         amp = a.src_amp[(long long)shot * a.src_stride] * a.src_scale;
     }
-    const float axc = a.ax[0] + a.az[0];
 
     // One output row zz; the queue's logical row k (zz-4+k) lives in q[(k + R) % 9], so nine
     // consecutive rows rotate the queue through the registers without moving any of them.
@@ -173,40 +282,20 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
             if (a.f2) lf2 = lds4(arow + i_f2 * STRIP);                                                       \
             if (a.fc) { lcf = lds4(arow + i_cf * STRIP); lfc = lds4(arow + (i_cf + 1) * STRIP); }            \
         }                                                                                                    \
-        const float4 Q0 = q[(0 + (R)) % 9], Q1 = q[(1 + (R)) % 9], Q2 = q[(2 + (R)) % 9],                    \
-                     Q3 = q[(3 + (R)) % 9], Q4 = q[(4 + (R)) % 9], Q5 = q[(5 + (R)) % 9],                    \
-                     Q6 = q[(6 + (R)) % 9], Q7 = q[(7 + (R)) % 9], Q8 = q[(8 + (R)) % 9];                    \
-        const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};           \
         const long long idx = (long long)zz * NXP + x;                                                       \
         const float gzz = __ldg(a.gz + zz);                                                                  \
-        float o[4], d2[4];                                                                                   \
-        _Pragma("unroll") for (int j = 0; j < 4; ++j) {                                                      \
-            const float c0v = rr[j + 4];                                                                     \
-            float lap = axc * c0v;                                                                           \
-            lap = fmaf(a.ax[1], rr[j + 3] + rr[j + 5], lap);                                                 \
-            lap = fmaf(a.ax[2], rr[j + 2] + rr[j + 6], lap);                                                 \
-            lap = fmaf(a.ax[3], rr[j + 1] + rr[j + 7], lap);                                                 \
-            lap = fmaf(a.ax[4], rr[j + 0] + rr[j + 8], lap);                                                 \
-            lap = fmaf(a.az[1], cmp(Q3, j) + cmp(Q5, j), lap);                                               \
-            lap = fmaf(a.az[2], cmp(Q2, j) + cmp(Q6, j), lap);                                               \
-            lap = fmaf(a.az[3], cmp(Q1, j) + cmp(Q7, j), lap);                                               \
-            lap = fmaf(a.az[4], cmp(Q0, j) + cmp(Q8, j), lap);                                               \
-            float sv = 0.f;                                                                                  \
-            if (LOCAL) {                                                                                     \
-                sv = fmaf(a.a0, cmp(lf0, j), sv);                                                            \
-                sv = fmaf(a.a1, cmp(lf1, j), sv);                                                            \
-                sv = fmaf(a.a2, cmp(lf2, j), sv);                                                            \
-                sv = fmaf(cmp(lcf, j), cmp(lfc, j), sv);                                                     \
-            }                                                                                                \
-            if (SRC) sv += (soff == idx + j) ? amp : 0.f;                                                    \
-            const float g = gzz * cmp(gxv, j);                                                               \
-            const float pj = cmp(pv, j);                                                                     \
-            o[j] = g * (2.f * c0v - g * pj + cmp(cv, j) * (lap + sv));                                       \
-            d2[j] = (o[j] - 2.f * c0v + pj) * a.inv_dt2;                                                     \
+        int sj = -1; /* the point source's column within this lane's four, if it is in them */              \
+        if (SRC) {                                                                                           \
+            const long long sd = soff - idx;                                                                 \
+            sj = (sd >= 0 && sd < 4) ? (int)sd : -1;                                                         \
         }                                                                                                    \
+        float4 o, d2;                                                                                        \
+        row_math<LOCAL, D2, SRC>(a, L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
+                                 q[(4 + (R)) % 9], q[(5 + (R)) % 9], q[(6 + (R)) % 9], q[(7 + (R)) % 9],      \
+                                 q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
         if (xin) {                                                                                           \
-            st4(out + idx, make_float4(o[0], o[1], o[2], o[3]));                                             \
-            if (D2) st4(a.d2 + so + idx, make_float4(d2[0], d2[1], d2[2], d2[3]));                           \
+            st4(out + idx, o);                                                                               \
+            if (D2) st4(a.d2 + so + idx, d2);                                                                \
         }                                                                                                    \
         __syncwarp(); /* every lane is done with this row's slots before they are refilled */              \
         issue_cur(zz + 4 + AUX_SLOTS);                                                                       \
@@ -319,6 +408,7 @@ cudaError_t prop_occupancy(int *blocks_per_sm)
 cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
 {
     PropArgs a = a0;
+    prop_pairs(a);
     const int nwarps = a.nstrip * a.nchunk;
     dim3 grid((nwarps + PROP_WARPS - 1) / PROP_WARPS, nshot);
     dim3 block(PROP_WARPS * 32);
