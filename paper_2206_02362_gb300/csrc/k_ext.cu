@@ -167,8 +167,14 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_SC_A21
 #define FWIME_SC_A21 4
 #endif
+// packed two-lane FP32 (f32x2) forms of the multiply-adds, per kernel where they measured faster
+// (B~ + B~* on the Marmousi2-shaped grid: scatter -1 % at nh 21; imaging -5.5 % at nh 21, +2.7 %
+// at nh 31, so the imaging kernel packs only up to nh 21)
 #ifndef FWIME_SC_F32X2
-#define FWIME_SC_F32X2 0
+#define FWIME_SC_F32X2 1
+#endif
+#ifndef FWIME_IMG_F32X2
+#define FWIME_IMG_F32X2 1
 #endif
 constexpr int SC_WARPS = FWIME_SC_WARPS;     // warps per CTA (independent pipelines)
 constexpr int SC_STAGES = FWIME_SC_STAGES;   // cp.async ring depth per warp
@@ -663,13 +669,22 @@ struct ImgTaskBody {
     static constexpr ImgTask T = img_task(NH, K);
     static constexpr int HM = (NH - 1) / 2;
     static constexpr int W1 = 4 * T.nl1, W2 = T.nl2 > 0 ? 4 * T.nl2 : 1;
+    // packed two-lane form: the products of one D sample with the L pair (2 q, 2 q + 1) of a window
+    // accumulate in one register pair when both lie in the band; the band's edge entries whose
+    // partner lies outside stay scalar
+    static constexpr bool PACK = FWIME_IMG_F32X2 && NH <= 21;   // measured slower at nh 31
+    static constexpr int P1 = PACK ? W1 / 2 : 1, P2 = PACK && W2 >= 2 ? W2 / 2 : 1;
     float acc1[8][W1], acc2[8][W2];
+    f32x2 pac1[8][P1], pac2[8][P2];
 
     __device__ __forceinline__ static constexpr bool in1(int i, int j) { return (T.lo1 + j - i) <= HM && (T.lo1 + j - i) >= -HM; }
     __device__ __forceinline__ static constexpr bool in2(int i, int j)
     {
         return T.nl2 > 0 && (T.lo2 + j - i) <= HM && (T.lo2 + j - i) >= -HM;
     }
+    // entry (i, j) accumulates in the pair (i, j / 2)
+    __device__ __forceinline__ static constexpr bool pk1(int i, int j) { return PACK && in1(i, j & ~1) && in1(i, j | 1); }
+    __device__ __forceinline__ static constexpr bool pk2(int i, int j) { return PACK && in2(i, j & ~1) && in2(i, j | 1); }
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
@@ -678,6 +693,10 @@ struct ImgTaskBody {
             for (int j = 0; j < W1; ++j) acc1[i][j] = 0.f;
 #pragma unroll
             for (int j = 0; j < W2; ++j) acc2[i][j] = 0.f;
+#pragma unroll
+            for (int q = 0; q < P1; ++q) pac1[i][q] = pk(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < P2; ++q) pac2[i][q] = pk(0.f, 0.f);
         }
     }
     // loads the lane's L window [8 b + LOW, 8 b + LOW + 4 NL) of wt: chunks c0 + q of the L region
@@ -706,19 +725,51 @@ struct ImgTaskBody {
         float l1[W1];
         load_window<T.lo1, T.nl1>(l1, sl, b, Sh::HCL);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+            const f32x2 dd = pk(dv[i], dv[i]);
 #pragma unroll
-            for (int j = 0; j < W1; ++j)
-                if (in1(i, j)) acc1[i][j] = fmaf(dv[i], l1[j], acc1[i][j]);
+            for (int j = 0; j < W1; ++j) {
+                if (pk1(i, j)) {
+                    if (!(j & 1)) pac1[i][j / 2] = fma2(dd, pk(l1[j], l1[j + 1]), pac1[i][j / 2]);
+                } else if (in1(i, j)) {
+                    acc1[i][j] = fmaf(dv[i], l1[j], acc1[i][j]);
+                }
+            }
+        }
         if constexpr (T.nl2 > 0) {
             float l2[W2];
             load_window<T.lo2, (T.nl2 > 0 ? T.nl2 : 1)>(l2, sl, b, Sh::HCL);
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const f32x2 dd = pk(dv[i], dv[i]);
 #pragma unroll
-                for (int j = 0; j < W2; ++j)
-                    if (in2(i, j)) acc2[i][j] = fmaf(dv[i], l2[j], acc2[i][j]);
+                for (int j = 0; j < W2; ++j) {
+                    if (pk2(i, j)) {
+                        if (!(j & 1)) pac2[i][j / 2] = fma2(dd, pk(l2[j], l2[j + 1]), pac2[i][j / 2]);
+                    } else if (in2(i, j)) {
+                        acc2[i][j] = fmaf(dv[i], l2[j], acc2[i][j]);
+                    }
+                }
+            }
         }
+    }
+    __device__ __forceinline__ float val1(int i, int j) const
+    {
+        if (pk1(i, j)) {
+            float lo, hi;
+            upk(pac1[i][(j / 2) % P1], lo, hi);
+            return (j & 1) ? hi : lo;
+        }
+        return acc1[i][j];
+    }
+    __device__ __forceinline__ float val2(int i, int j) const
+    {
+        if (pk2(i, j)) {
+            float lo, hi;
+            upk(pac2[i][(j / 2) % P2], lo, hi);
+            return (j & 1) ? hi : lo;
+        }
+        return acc2[i][j];
     }
     // adds the accumulators into img at x = x1 + i + o, h = o - i (o = lo + j), x1 = the lane's
     // first u + its first ut offset; only physical columns [x_lo, x_hi)
@@ -730,14 +781,14 @@ struct ImgTaskBody {
             for (int j = 0; j < W1; ++j) {
                 if (in1(i, j)) {
                     const int x = x1 + i + T.lo1 + j;
-                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo1 + j - i + HM) * a.P + rowoff + x] += acc1[i][j];
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo1 + j - i + HM) * a.P + rowoff + x] += val1(i, j);
                 }
             }
 #pragma unroll
             for (int j = 0; j < W2; ++j) {
                 if (in2(i, j)) {
                     const int x = x1 + i + T.lo2 + j;
-                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo2 + j - i + HM) * a.P + rowoff + x] += acc2[i][j];
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo2 + j - i + HM) * a.P + rowoff + x] += val2(i, j);
                 }
             }
         }

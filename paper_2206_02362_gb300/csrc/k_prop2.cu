@@ -3,8 +3,8 @@
 //   q^{n+1} = g (2 q^n     - g q^{n-1} + c (L q^n     + s^n))
 //   q^{n+2} = g (2 q^{n+1} - g q^n     + c (L q^{n+1} + s^{n+1}))
 //
-// with the same arithmetic, point by point and in the same order, as two launches of k_prop, so the
-// results are identical.  Each launch reads q^n and q^{n-1} and writes q^{n+1} and q^{n+2}: 16 bytes
+// with the same arithmetic, point by point and in the same order, as two launches of k_prop (whose
+// packed two-lane form rounds every operation as this scalar form does), so the results are identical.  Each launch reads q^n and q^{n-1} and writes q^{n+1} and q^{n+2}: 16 bytes
 // per two updates of a shot-point instead of 24 (plus one D2t field per step and one local-source field
 // per step when the variant has them).
 //
@@ -166,13 +166,17 @@ __device__ __forceinline__ void prop2_body(const Prop2Args &a, const int wid, co
                 const float c0v = rr[j + 4];                                                                 \
                 float lap;                                                                                   \
                 FWIME_P2_LAP(rr, Q0, Q1, Q2, Q3, Q5, Q6, Q7, Q8, j, lap)                                     \
-                float sv = 0.f;                                                                              \
-                if (LOCAL) sv = fmaf(a.a0, c4(f1v, j), sv);                                                  \
-                if (SRC) sv += (xin && soff == i1 + j) ? amp0 : 0.f;                                         \
+                if (LOCAL || SRC) {                                                                           \
+                    float sv = 0.f;                                                                          \
+                    if (LOCAL) sv = fmaf(a.a0, c4(f1v, j), sv);                                              \
+                    if (SRC) sv += (xin && soff == i1 + j) ? amp0 : 0.f;                                     \
+                    lap += sv;                                                                               \
+                }                                                                                            \
                 const float g = gz1 * c4(gxv, j);                                                            \
                 const float pj = c4(pv, j);                                                                  \
-                n1[j] = g * (2.f * c0v - g * pj + c4(cv1, j) * (lap + sv));                                  \
-                d1[j] = (n1[j] - 2.f * c0v + pj) * a.inv_dt2;                                                \
+                const float tc = c0v + c0v;                                                                  \
+                n1[j] = g * fmaf(c4(cv1, j), lap, fmaf(-g, pj, tc));                                         \
+                d1[j] = (n1[j] - tc + pj) * a.inv_dt2;                                                       \
             }                                                                                                \
         }                                                                                                    \
         p[(8 + (R)) % 9] = make_float4(n1[0], n1[1], n1[2], n1[3]);                                          \
@@ -195,13 +199,17 @@ __device__ __forceinline__ void prop2_body(const Prop2Args &a, const int wid, co
                 const float c0v = rr[j + 4];                                                                 \
                 float lap;                                                                                   \
                 FWIME_P2_LAP(rr, P0, P1, P2, P3, P5, P6, P7, P8, j, lap)                                     \
-                float sv = 0.f;                                                                              \
-                if (LOCAL) sv = fmaf(a.a0, c4(f2v, j), sv);                                                  \
-                if (SRC) sv += (xin && soff == i2 + j) ? amp1 : 0.f;                                         \
-                const float g = gz2 * c4(gxv, j);                                                            \
-                const float pj = c4(Q0, j);                                                                  \
-                n2[j] = g * (2.f * c0v - g * pj + c4(cv2, j) * (lap + sv));                                  \
-                d2v[j] = (n2[j] - 2.f * c0v + pj) * a.inv_dt2;                                               \
+                if (LOCAL || SRC) {                                                                                  \
+                    float sv = 0.f;                                                                                  \
+                    if (LOCAL) sv = fmaf(a.a0, c4(f2v, j), sv);                                                      \
+                    if (SRC) sv += (xin && soff == i2 + j) ? amp1 : 0.f;                                             \
+                    lap += sv;                                                                                       \
+                }                                                                                                    \
+                const float g = gz2 * c4(gxv, j);                                                                    \
+                const float pj = c4(Q0, j);                                                                          \
+                const float tc = c0v + c0v;                                                                          \
+                n2[j] = g * fmaf(c4(cv2, j), lap, fmaf(-g, pj, tc));                                                 \
+                d2v[j] = (n2[j] - tc + pj) * a.inv_dt2;                                                              \
             }                                                                                                \
             if (own) {                                                                                       \
                 s4(a.out2 + so + i2, make_float4(n2[0], n2[1], n2[2], n2[3]));                               \
