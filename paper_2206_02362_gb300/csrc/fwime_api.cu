@@ -853,7 +853,8 @@ static int tlag_launch(Run &r, int Sb, int n0, int n1, bool image, RingRef D, Ri
     fwime_ctx *x = r.x;
     TlagArgs a{};
     a.NXP = x->NXP; a.nh = x->g.nh; a.S = Sb; a.lag = x->opt_tlag; a.nt = x->g.nt; a.n0 = n0; a.n1 = n1;
-    a.nchunk = tlag_chunks(r.w.K, x->opt_tlag); a.P = x->P; a.sigma = sigma;
+    a.jc = tlag_jc(r.w.K, x->opt_tlag, x->g.nh); a.nchunk = tlag_chunks(r.w.K, x->opt_tlag, a.jc);
+    a.P = x->P; a.sigma = sigma;
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;
     a.W = W ? W : r.w.W; a.D = D; a.E = E; a.L = L; a.img = img; a.accumulate = accumulate;
     const double pts = (double)Sb * x->g.nz * x->g.nx * (n1 - n0);

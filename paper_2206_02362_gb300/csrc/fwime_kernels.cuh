@@ -153,6 +153,7 @@ struct ImgArgs {
 // time-lag extension: one segment [n0, n1) of output steps, S shots
 struct TlagArgs {
     int NXP, nh, S, lag, nt, n0, n1, nchunk;
+    int jc;                        // outputs of one residue class per thread and chunk (16, 24, 32: tlag_jc)
     int sigma;                     // scatter: +1 reads D at n - 2 s_i, -1 (transpose) at n + 2 s_i
     long long P;
     int z_lo, z_hi, x_lo, x_hi;    // physical rows / columns
@@ -176,7 +177,8 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
 cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st);
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st);
-int tlag_chunks(int K, int lag);   // output chunks per residue class for a segment of K steps
+int tlag_jc(int K, int lag, int nh);          // chunk length (outputs of one residue class) for segments of K steps
+int tlag_chunks(int K, int lag, int jc);      // output chunks per residue class for a segment of K steps
 
 // model preparation
 struct PrepArgs {

@@ -71,6 +71,9 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 #ifndef FWIME_PROP_MIN_BLOCKS
 #define FWIME_PROP_MIN_BLOCKS 1
 #endif
+#ifndef FWIME_PROP_MINB_PLAIN
+#define FWIME_PROP_MINB_PLAIN 3   // up to 128 registers: still 4 CTAs per SM, fewer rematerialised operands
+#endif
 constexpr int CUR_SLOTS = FWIME_PROP_CUR_SLOTS;   // q^n rows in flight: the queue reads row z+4 of slots
 constexpr int AUX_SLOTS = FWIME_PROP_AUX_SLOTS;   // pipeline depth of the q^{n-1}, c, local-source rows
 constexpr int CUR_ROW = STRIP + 8;
@@ -85,14 +88,35 @@ static_assert(CUR_SLOTS >= AUX_SLOTS + 4, "the q^n ring must hold rows z .. z+4+
 #ifndef FWIME_PROP_F32X2
 #define FWIME_PROP_F32X2 1
 #endif
-#if FWIME_PROP_F32X2
+#ifndef FWIME_PROP_F32X2_PLAIN
+#define FWIME_PROP_F32X2_PLAIN 1
+#endif
 // Packed two-lane FP32 (f32x2, see fwime_kernels.cuh) on columns (j, j + 1): half the floating-point
 // issue slots of the scalar form, with its rounding.
+// the packed coefficient operands
+struct PropK {
+    f32x2 axc, kx[5], kz[5], inv, a0, a1, a2;
+};
+__device__ __forceinline__ PropK prop_k(const PropArgs &a)
+{
+    PropK K;
+    K.axc = bits(a.axc2);
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        K.kx[k] = bits(a.kx2[k]);
+        K.kz[k] = bits(a.kz2[k]);
+    }
+    K.inv = bits(a.inv2);
+    K.a0 = bits(a.a02);
+    K.a1 = bits(a.a12);
+    K.a2 = bits(a.a22);
+    return K;
+}
 // columns (2 h, 2 h + 1) of a float4
 __device__ __forceinline__ f32x2 half2(const float4 &v, int h) { return h == 0 ? pk(v.x, v.y) : pk(v.z, v.w); }
 
 template <bool LOCAL, bool D2, bool SRC>
-__device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
+__device__ __forceinline__ void row_math_pk(const PropArgs &a, const PropK &K, const float4 &L, const float4 &Q0, const float4 &Q1,
                                          const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
                                          const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
                                          const float4 &pv, const float4 &cv, const float4 &lf0, const float4 &lf1,
@@ -106,21 +130,21 @@ __device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, con
     for (int h = 0; h < 2; ++h) {
         const int j = 2 * h;
         const f32x2 C0 = half2(Q4, h);
-        f32x2 lap = mul2(bits(a.axc2), C0);
-        lap = fma2(bits(a.kx2[1]), add2(pk(rr[j + 3], rr[j + 4]), pk(rr[j + 5], rr[j + 6])), lap);
-        lap = fma2(bits(a.kx2[2]), add2(pk(rr[j + 2], rr[j + 3]), pk(rr[j + 6], rr[j + 7])), lap);
-        lap = fma2(bits(a.kx2[3]), add2(pk(rr[j + 1], rr[j + 2]), pk(rr[j + 7], rr[j + 8])), lap);
-        lap = fma2(bits(a.kx2[4]), add2(pk(rr[j + 0], rr[j + 1]), pk(rr[j + 8], rr[j + 9])), lap);
-        lap = fma2(bits(a.kz2[1]), add2(half2(Q3, h), half2(Q5, h)), lap);
-        lap = fma2(bits(a.kz2[2]), add2(half2(Q2, h), half2(Q6, h)), lap);
-        lap = fma2(bits(a.kz2[3]), add2(half2(Q1, h), half2(Q7, h)), lap);
-        lap = fma2(bits(a.kz2[4]), add2(half2(Q0, h), half2(Q8, h)), lap);
+        f32x2 lap = mul2(K.axc, C0);
+        lap = fma2(K.kx[1], add2(pk(rr[j + 3], rr[j + 4]), pk(rr[j + 5], rr[j + 6])), lap);
+        lap = fma2(K.kx[2], add2(pk(rr[j + 2], rr[j + 3]), pk(rr[j + 6], rr[j + 7])), lap);
+        lap = fma2(K.kx[3], add2(pk(rr[j + 1], rr[j + 2]), pk(rr[j + 7], rr[j + 8])), lap);
+        lap = fma2(K.kx[4], add2(pk(rr[j + 0], rr[j + 1]), pk(rr[j + 8], rr[j + 9])), lap);
+        lap = fma2(K.kz[1], add2(half2(Q3, h), half2(Q5, h)), lap);
+        lap = fma2(K.kz[2], add2(half2(Q2, h), half2(Q6, h)), lap);
+        lap = fma2(K.kz[3], add2(half2(Q1, h), half2(Q7, h)), lap);
+        lap = fma2(K.kz[4], add2(half2(Q0, h), half2(Q8, h)), lap);
         if (LOCAL || SRC) {
             f32x2 sv = pk(0.f, 0.f);
             if (LOCAL) {
-                sv = fma2(bits(a.a02), half2(lf0, h), sv);
-                sv = fma2(bits(a.a12), half2(lf1, h), sv);
-                sv = fma2(bits(a.a22), half2(lf2, h), sv);
+                sv = fma2(K.a0, half2(lf0, h), sv);
+                sv = fma2(K.a1, half2(lf1, h), sv);
+                sv = fma2(K.a2, half2(lf2, h), sv);
                 sv = fma2(half2(lcf, h), half2(lfc, h), sv);
             }
             if (SRC) sv = add2(sv, pk(sj == j ? amp : 0.f, sj == j + 1 ? amp : 0.f));
@@ -133,16 +157,15 @@ __device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, con
         const f32x2 O = mul2(G, fma2(half2(cv, h), lap, fma2(NG, P, TC)));
         upk(O, ov[j], ov[j + 1]);
         if (D2) {
-            const f32x2 D = mul2(add2(sub2(O, TC), P), bits(a.inv2));
+            const f32x2 D = mul2(add2(sub2(O, TC), P), K.inv);
             upk(D, dv[j], dv[j + 1]);
         }
     }
     o = make_float4(ov[0], ov[1], ov[2], ov[3]);
     if (D2) d2 = make_float4(dv[0], dv[1], dv[2], dv[3]);
 }
-#else
 template <bool LOCAL, bool D2, bool SRC>
-__device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
+__device__ __forceinline__ void row_math_sc(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
                                          const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
                                          const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
                                          const float4 &pv, const float4 &cv, const float4 &lf0, const float4 &lf1,
@@ -184,7 +207,23 @@ __device__ __forceinline__ void row_math(const PropArgs &a, const float4 &L, con
     o = make_float4(ov[0], ov[1], ov[2], ov[3]);
     if (D2) d2 = make_float4(dv[0], dv[1], dv[2], dv[3]);
 }
-#endif
+// the packed form where it measured faster: the variants with dense local sources always; the
+// plain ones (point source, D2t) only under FWIME_PROP_F32X2_PLAIN
+template <bool LOCAL, bool D2, bool SRC>
+__device__ __forceinline__ void row_math(const PropArgs &a, const PropK &K, const float4 &L, const float4 &Q0, const float4 &Q1,
+                                         const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
+                                         const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
+                                         const float4 &pv, const float4 &cv, const float4 &lf0, const float4 &lf1,
+                                         const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
+                                         const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
+{
+    if constexpr (FWIME_PROP_F32X2 && (LOCAL || FWIME_PROP_F32X2_PLAIN))
+        row_math_pk<LOCAL, D2, SRC>(a, K, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
+                                    gxv, sj, amp, o, d2);
+    else
+        row_math_sc<LOCAL, D2, SRC>(a, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
+                                    gxv, sj, amp, o, d2);
+}
 
 // The time step of one warp's work item (strip, chunk) of shot `shot`; wsm is the warp's shared
 // memory (CUR_SLOTS x CUR_ROW + AUX_SLOTS x naux_max x STRIP floats).
@@ -254,6 +293,7 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
     }
     for (int g = AUX_SLOTS; g < 4; ++g) issue_cur(z0 + g);   // (only when the depth is below 4)
     const float4 gxv = xin ? ldg4(a.gx + x) : f4zero();
+
     long long soff = -1;
     float amp = 0.f;
     if (SRC) {
@@ -290,7 +330,7 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
             sj = (sd >= 0 && sd < 4) ? (int)sd : -1;                                                         \
         }                                                                                                    \
         float4 o, d2;                                                                                        \
-        row_math<LOCAL, D2, SRC>(a, L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
+        row_math<LOCAL, D2, SRC>(a, prop_k(a), L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
                                  q[(4 + (R)) % 9], q[(5 + (R)) % 9], q[(6 + (R)) % 9], q[(7 + (R)) % 9],      \
                                  q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
         if (xin) {                                                                                           \
@@ -318,7 +358,7 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
 }
 
 template <bool LOCAL, bool D2, bool SRC>
-__global__ void __launch_bounds__(PROP_WARPS * 32, LOCAL ? FWIME_PROP_MIN_BLOCKS : 4) k_prop(const PropArgs a)
+__global__ void __launch_bounds__(PROP_WARPS * 32, LOCAL ? FWIME_PROP_MIN_BLOCKS : FWIME_PROP_MINB_PLAIN) k_prop(const PropArgs a)
 {
     extern __shared__ float4 smem4[];
     const int wic = threadIdx.x >> 5;

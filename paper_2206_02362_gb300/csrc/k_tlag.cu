@@ -24,8 +24,12 @@ namespace fwk {
 #ifndef FWIME_TL_IMG_F32X2
 #define FWIME_TL_IMG_F32X2 1
 #endif
+#ifndef FWIME_TL_SC_IOUTER
+#define FWIME_TL_SC_IOUTER 0
+#endif
 constexpr int TL_TX = 128;      // threads per CTA (consecutive columns)
-constexpr int TL_JC = 16;       // outputs of one residue class per thread
+// JC, the outputs of one residue class a thread handles (one chunk), is 16, 24 or 32, chosen per
+// segment by tlag_jc so that the chunks cover the class's outputs with the fewest wasted window loads
 
 // element offset of time step m in ring r (m >= 0)
 __device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
@@ -49,17 +53,17 @@ __device__ __forceinline__ int tl_next(const RingRef &r, int idx, int inc)
 }
 
 // blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue, chunk)
-template <int NH, int SIGMA>
+template <int NH, int SIGMA, int JC>
 __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
 {
-    constexpr int HM = (NH - 1) / 2, NW = TL_JC + 2 * HM;
+    constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const int Z = a.z_lo + blockIdx.y;
     int q = blockIdx.z;
     const int chunk = q % a.nchunk; q /= a.nchunk;
     const int r = q % (2 * a.lag), s = q / (2 * a.lag);
-    const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;   // output j of this thread: base + 2 L j
+    const int base = a.n0 + r + 2 * a.lag * JC * chunk;   // output j of this thread: base + 2 L j
     if (base >= a.n1) return;
     const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
     const int step = 2 * a.lag;
@@ -83,41 +87,41 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
     // Packed form: output j reads win[j - i + 2 HM] at lag i.  For even i the output pairs (2p, 2p + 1)
     // read the aligned sample pairs (k, k + 1), k even; for odd i the pairs (2p + 1, 2p + 2) do, and
     // outputs 0 and JC - 1 stay scalar.  Each output sums its even-i and odd-i products separately.
-    static_assert(TL_JC % 2 == 0, "pairs of outputs");
-    f32x2 pe[TL_JC / 2], po[TL_JC / 2 - 1];
+    static_assert(JC % 2 == 0, "pairs of outputs");
+    f32x2 pe[JC / 2], po[JC / 2 - 1];
     float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-    for (int p = 0; p < TL_JC / 2; ++p) pe[p] = pk(0.f, 0.f);
+    for (int p = 0; p < JC / 2; ++p) pe[p] = pk(0.f, 0.f);
 #pragma unroll
-    for (int p = 0; p < TL_JC / 2 - 1; ++p) po[p] = pk(0.f, 0.f);
+    for (int p = 0; p < JC / 2 - 1; ++p) po[p] = pk(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
         const f32x2 wb = pk(Wr[i], Wr[i]);
         if (i % 2 == 0) {
 #pragma unroll
-            for (int p = 0; p < TL_JC / 2; ++p) {
+            for (int p = 0; p < JC / 2; ++p) {
                 const int k = 2 * p - i + 2 * HM;
                 pe[p] = fma2(wb, pk(win[k], win[k + 1]), pe[p]);
             }
         } else {
 #pragma unroll
-            for (int p = 0; p < TL_JC / 2 - 1; ++p) {
+            for (int p = 0; p < JC / 2 - 1; ++p) {
                 const int k = 2 * p + 1 - i + 2 * HM;
                 po[p] = fma2(wb, pk(win[k], win[k + 1]), po[p]);
             }
             o0 = fmaf(Wr[i], win[-i + 2 * HM], o0);
-            o1 = fmaf(Wr[i], win[TL_JC - 1 - i + 2 * HM], o1);
+            o1 = fmaf(Wr[i], win[JC - 1 - i + 2 * HM], o1);
         }
     }
-    float ev[TL_JC], od[TL_JC];
+    float ev[JC], od[JC];
 #pragma unroll
-    for (int p = 0; p < TL_JC / 2; ++p) upk(pe[p], ev[2 * p], ev[2 * p + 1]);
+    for (int p = 0; p < JC / 2; ++p) upk(pe[p], ev[2 * p], ev[2 * p + 1]);
 #pragma unroll
-    for (int p = 0; p < TL_JC / 2 - 1; ++p) upk(po[p], od[2 * p + 1], od[2 * p + 2]);
+    for (int p = 0; p < JC / 2 - 1; ++p) upk(po[p], od[2 * p + 1], od[2 * p + 2]);
     od[0] = o0;
-    od[TL_JC - 1] = o1;
+    od[JC - 1] = o1;
 #pragma unroll
-    for (int j = 0; j < TL_JC; ++j) {
+    for (int j = 0; j < JC; ++j) {
         if (base + step * j < a.n1) {
             const float acc = ev[j] + od[j];
             float *o = ob + (long long)ei * a.E.slot_stride;
@@ -126,14 +130,25 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
         ei = tl_next(a.E, ei, se);
     }
 #else
+    float acc[JC];
 #pragma unroll
-    for (int j = 0; j < TL_JC; ++j) {
+    for (int j = 0; j < JC; ++j) acc[j] = 0.f;
+#if FWIME_TL_SC_IOUTER
+#pragma unroll
+    for (int i = 0; i < NH; ++i)                  // every output sums over i in the same order
+#pragma unroll
+        for (int j = 0; j < JC; ++j) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
+#else
+#pragma unroll
+    for (int j = 0; j < JC; ++j)
+#pragma unroll
+        for (int i = 0; i < NH; ++i) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
+#endif
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
         if (base + step * j < a.n1) {
-            float acc = 0.f;
-#pragma unroll
-            for (int i = 0; i < NH; ++i) acc = fmaf(Wr[i], win[j - i + 2 * HM], acc);
             float *o = ob + (long long)ei * a.E.slot_stride;
-            *o = a.accumulate ? *o + acc : acc;
+            *o = a.accumulate ? *o + acc[j] : acc[j];
         }
         ei = tl_next(a.E, ei, se);
     }
@@ -150,9 +165,9 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
     const int chunk = q % a.nchunk; q /= a.nchunk;
     const int r = q % (2 * a.lag), s = q / (2 * a.lag);
     const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
-    const int base = a.n0 + r + 2 * a.lag * TL_JC * chunk;
+    const int base = a.n0 + r + 2 * a.lag * a.jc * chunk;
     const int hm = (a.nh - 1) / 2;
-    for (int j = 0; j < TL_JC; ++j) {
+    for (int j = 0; j < a.jc; ++j) {
         const int n = base + 2 * a.lag * j;
         if (n >= a.n1) break;
         float acc = 0.f;
@@ -168,10 +183,10 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
 
 // blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks.  The samples of
 // the next (residue, chunk) are loaded before the current products are formed (two register windows).
-template <int NH>
+template <int NH, int JC>
 __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
 {
-    constexpr int HM = (NH - 1) / 2, NW = TL_JC + 2 * HM;
+    constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const int Z = a.z_lo + blockIdx.y;
@@ -197,8 +212,8 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
 #pragma unroll 1
         for (int r = 0; r < step; ++r) {
 #pragma unroll 1
-            for (int base = a.n0 + r; base < a.n1; base += step * TL_JC) {
-                float win[NW], lv[TL_JC];
+            for (int base = a.n0 + r; base < a.n1; base += step * JC) {
+                float win[NW], lv[JC];
                 const int m0 = base - step * HM;
                 int di = tl_index(a.D, m0), li = tl_index(a.L, base);
 #pragma unroll
@@ -208,13 +223,13 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
                     di = tl_next(a.D, di, sd);
                 }
 #pragma unroll
-                for (int j = 0; j < TL_JC; ++j) {
+                for (int j = 0; j < JC; ++j) {
                     lv[j] = base + step * j < a.n1 ? __ldg(a.L.base + (long long)li * a.L.slot_stride + off) : 0.f;
                     li = tl_next(a.L, li, sl);
                 }
 #if FWIME_TL_IMG_F32X2
 #pragma unroll
-                for (int j = 0; j < TL_JC; ++j) {
+                for (int j = 0; j < JC; ++j) {
                     const f32x2 lb = pk(lv[j], lv[j]);
                     if (j % 2 == 0) {
 #pragma unroll
@@ -236,7 +251,7 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
 #pragma unroll
                 for (int i = 0; i < NH; ++i)
 #pragma unroll
-                    for (int j = 0; j < TL_JC; ++j) acc[i] = fmaf(win[j - i + 2 * HM], lv[j], acc[i]);
+                    for (int j = 0; j < JC; ++j) acc[i] = fmaf(win[j - i + 2 * HM], lv[j], acc[i]);
 #endif
             }
         }
@@ -280,40 +295,78 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image_gen(const TlagArgs a)
     }
 }
 
+template <int NH, int JC>
+static void launch_tlag_scatter_jc(const TlagArgs &a, dim3 grid, cudaStream_t st)
+{
+    if (a.sigma > 0) k_tlag_scatter<NH, 1, JC><<<grid, TL_TX, 0, st>>>(a);
+    else k_tlag_scatter<NH, -1, JC><<<grid, TL_TX, 0, st>>>(a);
+}
+template <int NH>
+static void launch_tlag_scatter_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
+{
+    if (a.jc == 24) launch_tlag_scatter_jc<NH, 24>(a, grid, st);
+    else if (a.jc == 32) launch_tlag_scatter_jc<NH, 32>(a, grid, st);
+    else launch_tlag_scatter_jc<NH, 16>(a, grid, st);
+}
+
 cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
+    if (a.jc != 16 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
     dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag * a.nchunk);
-#define FWIME_TL_SC(NH)                                                                    \
-    case NH:                                                                               \
-        if (a.sigma > 0) k_tlag_scatter<NH, 1><<<grid, TL_TX, 0, st>>>(a);                 \
-        else k_tlag_scatter<NH, -1><<<grid, TL_TX, 0, st>>>(a);                            \
-        break;
     switch (a.nh) {
-        FWIME_TL_SC(1) FWIME_TL_SC(3) FWIME_TL_SC(5) FWIME_TL_SC(11) FWIME_TL_SC(21) FWIME_TL_SC(31) FWIME_TL_SC(41)
+    case 1: launch_tlag_scatter_nh<1>(a, grid, st); break;
+    case 3: launch_tlag_scatter_nh<3>(a, grid, st); break;
+    case 5: launch_tlag_scatter_nh<5>(a, grid, st); break;
+    case 11: launch_tlag_scatter_nh<11>(a, grid, st); break;
+    case 21: launch_tlag_scatter_nh<21>(a, grid, st); break;
+    case 31: launch_tlag_scatter_nh<31>(a, grid, st); break;
+    case 41: launch_tlag_scatter_nh<41>(a, grid, st); break;
     default: k_tlag_scatter_gen<<<grid, TL_TX, 0, st>>>(a);
     }
-#undef FWIME_TL_SC
     return cudaGetLastError();
+}
+
+template <int NH>
+static void launch_tlag_image_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
+{
+    if (a.jc == 24) k_tlag_image<NH, 24><<<grid, TL_TX, 0, st>>>(a);
+    else if (a.jc == 32) k_tlag_image<NH, 32><<<grid, TL_TX, 0, st>>>(a);
+    else k_tlag_image<NH, 16><<<grid, TL_TX, 0, st>>>(a);
 }
 
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
+    if (a.jc != 16 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
     dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo);
     switch (a.nh) {
-    case 1: k_tlag_image<1><<<grid, TL_TX, 0, st>>>(a); break;
-    case 3: k_tlag_image<3><<<grid, TL_TX, 0, st>>>(a); break;
-    case 5: k_tlag_image<5><<<grid, TL_TX, 0, st>>>(a); break;
-    case 11: k_tlag_image<11><<<grid, TL_TX, 0, st>>>(a); break;
-    case 21: k_tlag_image<21><<<grid, TL_TX, 0, st>>>(a); break;
-    case 31: k_tlag_image<31><<<grid, TL_TX, 0, st>>>(a); break;
-    case 41: k_tlag_image<41><<<grid, TL_TX, 0, st>>>(a); break;
+    case 1: launch_tlag_image_nh<1>(a, grid, st); break;
+    case 3: launch_tlag_image_nh<3>(a, grid, st); break;
+    case 5: launch_tlag_image_nh<5>(a, grid, st); break;
+    case 11: launch_tlag_image_nh<11>(a, grid, st); break;
+    case 21: launch_tlag_image_nh<21>(a, grid, st); break;
+    case 31: launch_tlag_image_nh<31>(a, grid, st); break;
+    case 41: launch_tlag_image_nh<41>(a, grid, st); break;
     default: k_tlag_image_gen<<<grid, TL_TX, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
 
-int tlag_chunks(int K, int lag) { return (K + 2 * lag * TL_JC - 1) / (2 * lag * TL_JC); }
+// A segment of K steps holds at most c = ceil(K / 2L) outputs of one residue class.  With chunks of JC
+// outputs a class costs about ceil(c / JC) (2 JC + 2 hm) loads and stores (window JC + 2 hm, outputs JC):
+// the JC of least cost, ties to the smaller.
+int tlag_jc(int K, int lag, int nh)
+{
+    const int c = (K + 2 * lag - 1) / (2 * lag), hm = (nh - 1) / 2;
+    int best = 16;
+    long long bc = -1;
+    for (const int jc : {16, 24, 32}) {
+        const long long cost = (long long)((c + jc - 1) / jc) * (2 * jc + 2 * hm);
+        if (bc < 0 || cost < bc) { bc = cost; best = jc; }
+    }
+    return best;
+}
+int tlag_chunks(int K, int lag, int jc) { return (K + 2 * lag * jc - 1) / (2 * lag * jc); }
 
 }  // namespace fwk
