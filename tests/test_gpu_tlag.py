@@ -50,6 +50,11 @@ def rel(a, b):
     (11, 4, dict(segment=13)),
     (7, 2, {}),                                     # generic lag count
     (1, 1, {}),
+    # chunk lengths (outputs of one residue class per thread): 32 (30 per class), 24 in two chunks
+    # (45 per class), and the generic kernel with 32 (28 per class)
+    (5, 1, dict(segment=60)),
+    (3, 1, dict(segment=90)),
+    (7, 1, dict(segment=56)),
 ])
 def test_time_lag_born_and_adjoint_match_oracle(nh, lag, opts):
     assert torch.cuda.is_available()
