@@ -159,7 +159,7 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #define FWIME_SC_STAGES 8
 #endif
 #ifndef FWIME_SC_MINB
-#define FWIME_SC_MINB 1
+#define FWIME_SC_MINB 3   // at most 168 registers: 3 CTAs per SM for every nh (nh 31 transposed: 229 -> 168, -3.5 %)
 #endif
 #ifndef FWIME_IMG_MINB
 #define FWIME_IMG_MINB 1
@@ -175,9 +175,6 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #endif
 #ifndef FWIME_IMG_F32X2
 #define FWIME_IMG_F32X2 1
-#endif
-#ifndef FWIME_SC_CHAINS
-#define FWIME_SC_CHAINS 1
 #endif
 constexpr int SC_WARPS = FWIME_SC_WARPS;     // warps per CTA (independent pipelines)
 constexpr int SC_STAGES = FWIME_SC_STAGES;   // cp.async ring depth per warp
@@ -293,46 +290,29 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
         st_c = st_c + Sh::STG == NS * Sh::STG ? 0 : st_c + Sh::STG;
         float e[A];
         if constexpr (PACK) {
-            // C independent chains per accumulator (offsets alternate between them), summed at the end
-            constexpr int C = FWIME_SC_CHAINS;
-            f32x2 ae[C][A / 2], ao[C];
-            float ao0[C], ao3[C];
+            f32x2 ae[A / 2], ao = pk(0.f, 0.f);
+            float ao0 = 0.f, ao3 = 0.f;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                ao[c] = pk(0.f, 0.f);
-                ao0[c] = ao3[c] = 0.f;
-#pragma unroll
-                for (int q = 0; q < A / 2; ++q) ae[c][q] = pk(0.f, 0.f);
-            }
+            for (int q = 0; q < A / 2; ++q) ae[q] = pk(0.f, 0.f);
 #pragma unroll
             for (int m = 0; m < NH; ++m) {             // offsets in the order of their samples
                 const int ih = SIGMA > 0 ? NH - 1 - m : m;
                 const int o = HM - SIGMA * (ih - HM);
-                const int c = (m / 2) % C;
                 if (ih % 2 == 0) {
 #pragma unroll
-                    for (int q = 0; q < A / 2; ++q)
-                        ae[c][q] = fma2(WE[ih / 2][q], pk(dv[o + 2 * q], dv[o + 2 * q + 1]), ae[c][q]);
+                    for (int q = 0; q < A / 2; ++q) ae[q] = fma2(WE[ih / 2][q], pk(dv[o + 2 * q], dv[o + 2 * q + 1]), ae[q]);
                 } else {
-                    if (A == 4) ao[c] = fma2(WO[ih / 2], pk(dv[o + 1], dv[o + 2]), ao[c]);
-                    ao0[c] = fmaf(WO0[ih / 2], dv[o], ao0[c]);
-                    ao3[c] = fmaf(WO3[ih / 2], dv[o + A - 1], ao3[c]);
+                    if (A == 4) ao = fma2(WO[ih / 2], pk(dv[o + 1], dv[o + 2]), ao);
+                    ao0 = fmaf(WO0[ih / 2], dv[o], ao0);
+                    ao3 = fmaf(WO3[ih / 2], dv[o + A - 1], ao3);
                 }
-            }
-#pragma unroll
-            for (int c = 1; c < C; ++c) {
-                ao[0] = add2(ao[0], ao[c]);
-                ao0[0] += ao0[c];
-                ao3[0] += ao3[c];
-#pragma unroll
-                for (int q = 0; q < A / 2; ++q) ae[0][q] = add2(ae[0][q], ae[c][q]);
             }
             float el[A], ol[A];
 #pragma unroll
-            for (int q = 0; q < A / 2; ++q) upk(ae[0][q], el[2 * q], el[2 * q + 1]);
-            ol[0] = ao0[0];
-            ol[A - 1] = ao3[0];
-            if (A == 4) upk(ao[0], ol[1], ol[A - 2]);
+            for (int q = 0; q < A / 2; ++q) upk(ae[q], el[2 * q], el[2 * q + 1]);
+            ol[0] = ao0;
+            ol[A - 1] = ao3;
+            if (A == 4) upk(ao, ol[1], ol[A - 2]);
 #pragma unroll
             for (int j = 0; j < A; ++j) e[j] = el[j] + ol[j];
         } else {
