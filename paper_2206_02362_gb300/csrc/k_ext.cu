@@ -1044,10 +1044,15 @@ __global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
 
 // pointwise (h = 0) accumulation: G += sum_pairs D (alpha L + M2) + Ds L, four independent
 // pairs in flight per thread (coalesced: consecutive threads, consecutive points).
-__global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
+// Local imaging: a thread owns 4 consecutive columns (16-byte loads) of one row, a CTA 512 columns, so
+// every (step, shot) pair is read as long contiguous row segments; columns start at x_lo rounded down to
+// a multiple of 4 and only [x_lo, x_hi) is accumulated.
+constexpr int LOC_TX = 128;
+__device__ __forceinline__ float4 ldg4e(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__global__ void __launch_bounds__(LOC_TX) k_image_local(const ImgArgs a, int xa)
 {
     const int Z = a.z_lo + blockIdx.y;
-    const int X = a.x_lo + blockIdx.x * EXT_TX + threadIdx.x;
+    const int X = xa + 4 * (blockIdx.x * LOC_TX + threadIdx.x);
     if (X >= a.x_hi) return;
     const long long off = (long long)Z * a.NXP + X;
     RingIt itd, itl, itm, its;
@@ -1055,24 +1060,35 @@ __global__ void __launch_bounds__(EXT_TX) k_image_local(const ImgArgs a)
     itl.init(a.L, a.n0, a.S, a.P, off);
     if (a.M2.base) itm.init(a.M2, a.n0, a.S, a.P, off);
     if (a.Ds.base) its.init(a.Ds, a.n0, a.S, a.P, off);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[4][4] = {};
     for (int p = 0; p < a.npair; p += 4) {
         // four independent pairs per iteration: their loads are all in flight together
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (p + u < a.npair) {
-                const float l = __ldg(itl.ptr());
-                float tt = a.alpha * l;
-                if (a.M2.base) { tt += __ldg(itm.ptr()); itm.next(); }
-                float r = __ldg(itd.ptr()) * tt;
-                if (a.Ds.base) { r = fmaf(__ldg(its.ptr()), l, r); its.next(); }
-                acc[u] += r;
+                const float4 l = ldg4e(itl.ptr());
+                const float4 d = ldg4e(itd.ptr());
+                float4 m2 = make_float4(0.f, 0.f, 0.f, 0.f), ds = m2;
+                if (a.M2.base) { m2 = ldg4e(itm.ptr()); itm.next(); }
+                if (a.Ds.base) { ds = ldg4e(its.ptr()); its.next(); }
+                const float lv[4] = {l.x, l.y, l.z, l.w}, dv[4] = {d.x, d.y, d.z, d.w};
+                const float mv[4] = {m2.x, m2.y, m2.z, m2.w}, sv[4] = {ds.x, ds.y, ds.z, ds.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float tt = a.alpha * lv[c];
+                    if (a.M2.base) tt += mv[c];
+                    float r = dv[c] * tt;
+                    if (a.Ds.base) r = fmaf(sv[c], lv[c], r);
+                    acc[c][u] += r;
+                }
                 itd.next();
                 itl.next();
             }
         }
     }
-    a.img[off] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (X + c >= a.x_lo && X + c < a.x_hi) a.img[off + c] += (acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3]);
 }
 
 template <int MODE>
@@ -1160,8 +1176,9 @@ cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     if (mode == IMG_LOCAL) {
-        dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
-        k_image_local<<<grid, EXT_TX, 0, st>>>(a);
+        const int xa = a.x_lo - a.x_lo % 4;   // 16-byte aligned: rows are NXP (a multiple of 32) floats apart
+        dim3 grid((a.x_hi - xa + 4 * LOC_TX - 1) / (4 * LOC_TX), a.z_hi - a.z_lo);
+        k_image_local<<<grid, LOC_TX, 0, st>>>(a, xa);
         return cudaGetLastError();
     }
     if (mode == IMG_EXT) return launch_image_mode<IMG_EXT>(a, st);
