@@ -430,9 +430,9 @@ def main():
                 "time_share": {k: round(p["ms"] / kern_ms, 4) for k, p in prof.items()} if kern_ms else None,
                 "family_gbs": {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items()
                                if p["ms"] > 0},
-                "bytes_rule": "12 B per shot-point (q^n, q^n-1 in, q^n+1 out) + 4 B per output field "
-                              "(D2t, local sources) + 4 B per grid point per launch for c (shared by all shots); "
-                              "padded NZ x NX points"}
+                "bytes_rule": "12 B per shot-point (q^n, q^n-1 in, q^n+1 out) over the padded NZ x NX points "
+                              "+ 4 B per grid point per launch for c (shared by all shots) + 4 B per shot-point "
+                              "per D2t or local-source field over the physical rows (nz x NX points)"}
     shots_per_s = wl.nshot * world / (ms_step * 1e-3)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -464,6 +464,7 @@ static void init_run(fwime_ctx *x, Run &r, int S)
     }
     a.inv_dt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
     a.src_scale = (float)(1.0 / ((double)x->g.dx * x->g.dz));
+    a.zs_lo = x->o; a.zs_hi = x->o + x->g.nz;
 }
 
 static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out, float *d2, const float *wsrc,
@@ -480,12 +481,12 @@ static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out,
         a.src_stride = x->g.nt;
     }
     a.f0 = f0; a.a0 = a0; a.f1 = f1; a.a1 = a1; a.f2 = f2; a.a2 = a2; a.coef = coef; a.fc = fc;
-    // compulsory bytes: per shot-point read q^n, q^{n-1}, write q^{n+1} (+ D2t out, + local
-    // source fields); per point once per launch the shared c (and coef)
-    const double pts = (double)x->NZ * x->NX;
-    const double per = 12.0 + (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) +
-                       (fc ? 4 : 0);
-    LAUNCH(FWIME_K_PROP, pts * (Sb * per + 4.0 + (coef ? 4.0 : 0.0)), launch_prop(a, Sb, x->st));
+    // compulsory bytes: per shot-point read q^n, q^{n-1}, write q^{n+1}, and per point once per launch
+    // the shared c, over the padded grid; D2t out and the local source fields (and coef) over the
+    // physical rows only (zero elsewhere, not needed there)
+    const double pts = (double)x->NZ * x->NX, spts = (double)x->g.nz * x->NX;
+    const double srcb = (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) + (fc ? 4 : 0);
+    LAUNCH(FWIME_K_PROP, pts * (Sb * 12.0 + 4.0) + spts * (Sb * srcb + (coef ? 4.0 : 0.0)), launch_prop(a, Sb, x->st));
     if (x->opt_fs)
         LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * (d2 ? 44.0 : 40.0),
                launch_free_surface(out, d2, Sb, x->P, x->NXP, x->o, x->st));

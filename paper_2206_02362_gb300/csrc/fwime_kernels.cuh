@@ -47,6 +47,10 @@ struct PropArgs {
     const float *f0, *f1, *f2;
     float a0, a1, a2;
     const float *coef, *fc;
+    // rows [zs_lo, zs_hi) (the physical rows): the only rows where the local sources may be nonzero
+    // (read there only, zero elsewhere) and where D2t is written (its readers, the extension and
+    // imaging kernels, read physical rows only)
+    int zs_lo, zs_hi;
     int naux_max;                  // rows per aux stage (set by launch_prop)
     // each scalar twice, the operands of the packed two-lane (f32x2) arithmetic (set by prop_pairs)
     float2 kx2[5], kz2[5], axc2, inv2, a02, a12, a22;

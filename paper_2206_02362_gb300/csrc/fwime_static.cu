@@ -167,6 +167,7 @@ extern "C" int fwime_forward_static(const fwime_grid *g, const fwime_geom *geo, 
     a.inv_dt2 = (float)(1.0 / ((double)g->dt * g->dt));
     a.src_scale = (float)(1.0 / ((double)g->dx * g->dz));
     a.c = c; a.gz = gz; a.gx = gx;
+    a.zs_lo = o; a.zs_hi = o + g->nz;
     a.src_off = offs;
     a.src_stride = nt;
     PointsArgs r{};

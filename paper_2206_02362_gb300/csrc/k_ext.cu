@@ -176,6 +176,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_IMG_F32X2
 #define FWIME_IMG_F32X2 1
 #endif
+#ifndef FWIME_SC_PACK_MAX
+#define FWIME_SC_PACK_MAX 96   // largest nh * A whose weights are packed (more spills)
+#endif
 constexpr int SC_WARPS = FWIME_SC_WARPS;     // warps per CTA (independent pipelines)
 constexpr int SC_STAGES = FWIME_SC_STAGES;   // cp.async ring depth per warp
 
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
         }
     }
     // packed two-lane arithmetic where the weights leave room for their pairs (no spills)
-    constexpr bool PACK = FWIME_SC_F32X2 && NH * A <= 96;
+    constexpr bool PACK = FWIME_SC_F32X2 && NH * A <= FWIME_SC_PACK_MAX;
     // Packed form: output j reads dv[j + o] at offset ih, o = HM - SIGMA (ih - HM), and o has the
     // parity of ih.  For even o the pairs of outputs (0, 1) and (2, 3) read the aligned register
     // pairs (dv[o], dv[o + 1]), (dv[o + 2], dv[o + 3]); for odd o the pair (1, 2) reads the aligned

@@ -269,12 +269,14 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         cp16(dst, prev + o2, xin);
         cp16(dst + STRIP, a.c + o2, xin);
         if (LOCAL) {
-            if (a.f0) cp16(dst + i_f0 * STRIP, a.f0 + so + o2, xin);
-            if (a.f1) cp16(dst + i_f1 * STRIP, a.f1 + so + o2, xin);
-            if (a.f2) cp16(dst + i_f2 * STRIP, a.f2 + so + o2, xin);
+            // local sources vanish outside the source rows: zero-filled there, not read
+            const bool lin = xin && zr >= a.zs_lo && zr < a.zs_hi;
+            if (a.f0) cp16(dst + i_f0 * STRIP, a.f0 + so + o2, lin);
+            if (a.f1) cp16(dst + i_f1 * STRIP, a.f1 + so + o2, lin);
+            if (a.f2) cp16(dst + i_f2 * STRIP, a.f2 + so + o2, lin);
             if (a.fc) {
-                cp16(dst + i_cf * STRIP, a.coef + o2, xin);
-                cp16(dst + (i_cf + 1) * STRIP, a.fc + so + o2, xin);
+                cp16(dst + i_cf * STRIP, a.coef + o2, lin);
+                cp16(dst + (i_cf + 1) * STRIP, a.fc + so + o2, lin);
             }
         }
     };
@@ -335,7 +337,7 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
                                  q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
         if (xin) {                                                                                           \
             st4(out + idx, o);                                                                               \
-            if (D2) st4(a.d2 + so + idx, d2);                                                                \
+            if (D2 && zz >= a.zs_lo && zz < a.zs_hi) st4(a.d2 + so + idx, d2);                               \
         }                                                                                                    \
         __syncwarp(); /* every lane is done with this row's slots before they are refilled */              \
         issue_cur(zz + 4 + AUX_SLOTS);                                                                       \
