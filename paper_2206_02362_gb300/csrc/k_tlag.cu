@@ -24,6 +24,9 @@ namespace fwk {
 #ifndef FWIME_TL_IMG_F32X2
 #define FWIME_TL_IMG_F32X2 1
 #endif
+#ifndef FWIME_TL_IMG_MINB
+#define FWIME_TL_IMG_MINB 4   // resident CTAs the imaging kernel is compiled for (up to 21 lags, JC <= 24; spills beyond)
+#endif
 #ifndef FWIME_TL_SC_IOUTER
 #define FWIME_TL_SC_IOUTER 0
 #endif
@@ -37,52 +40,47 @@ __device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
     return (long long)((r.mod > 0 ? (m + r.shift) % r.mod : m + r.shift)) * r.slot_stride;
 }
 
-// slot index of step m in ring r (any m, for incremental stepping), and the step by `inc` steps
-__device__ __forceinline__ int tl_index(const RingRef &r, int m)
-{
-    if (r.mod <= 0) return m + r.shift;
-    const int q = (m + r.shift) % r.mod;
-    return q < 0 ? q + r.mod : q;
-}
-// inc must be reduced first (tl_inc) so that one wrap suffices
-__device__ __forceinline__ int tl_inc(const RingRef &r, int inc) { return r.mod > 0 ? inc % r.mod : inc; }
-__device__ __forceinline__ int tl_next(const RingRef &r, int idx, int inc)
-{
-    idx += inc;
-    return (r.mod > 0 && idx >= r.mod) ? idx - r.mod : idx;
-}
 
 // blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue, chunk)
 template <int NH, int SIGMA, int JC>
 __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
 {
     constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
-    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
-    if (X >= a.x_hi) return;
+    // ring offsets of the window samples and of the outputs (-1: outside the record / the segment): the
+    // same for every thread of the CTA, computed once into shared memory
+    __shared__ long long s_doff[NW], s_eoff[JC];
     const int Z = a.z_lo + blockIdx.y;
     int q = blockIdx.z;
     const int chunk = q % a.nchunk; q /= a.nchunk;
     const int r = q % (2 * a.lag), s = q / (2 * a.lag);
     const int base = a.n0 + r + 2 * a.lag * JC * chunk;   // output j of this thread: base + 2 L j
-    if (base >= a.n1) return;
-    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    if (base >= a.n1) return;                             // the whole CTA
     const int step = 2 * a.lag;
+    const int m0 = base - step * HM;                      // window sample k is step m0 + k (2 L)
+    for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
+        if (k < NW) {
+            const int m = m0 + step * k;
+            s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
+        } else {
+            const int n = base + step * (k - NW);
+            s_eoff[k - NW] = n < a.n1 ? tl_slot(a.E, n - a.n0) : -1;
+        }
+    }
+    __syncthreads();
+    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    if (X >= a.x_hi) return;
+    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
     float Wr[NH];   // sigma = -1 reads lag i at m + 2 s_i = m - 2 s_(nh-1-i): the weights reversed
 #pragma unroll
     for (int i = 0; i < NH; ++i) Wr[i] = __ldg(a.W + (SIGMA > 0 ? i : NH - 1 - i) * a.P + pp);
-    const int m0 = base - step * HM;                      // window sample k is step m0 + k (2 L)
     float win[NW];
     const float *db = a.D.base + off;
-    int di = tl_index(a.D, m0);
-    const int sd = tl_inc(a.D, step), se = tl_inc(a.E, step);
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
-        const int m = m0 + step * k;
-        win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(db + (long long)di * a.D.slot_stride) : 0.f;
-        di = tl_next(a.D, di, sd);
+        const long long o = s_doff[k];
+        win[k] = o >= 0 ? __ldg(db + o) : 0.f;
     }
     float *ob = const_cast<float *>(a.E.base) + off;
-    int ei = tl_index(a.E, base - a.n0);
 #if FWIME_TL_SC_F32X2
     // Packed form: output j reads win[j - i + 2 HM] at lag i.  For even i the output pairs (2p, 2p + 1)
     // read the aligned sample pairs (k, k + 1), k even; for odd i the pairs (2p + 1, 2p + 2) do, and
@@ -122,12 +120,12 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
     od[JC - 1] = o1;
 #pragma unroll
     for (int j = 0; j < JC; ++j) {
-        if (base + step * j < a.n1) {
+        const long long eo = s_eoff[j];
+        if (eo >= 0) {
             const float acc = ev[j] + od[j];
-            float *o = ob + (long long)ei * a.E.slot_stride;
+            float *o = ob + eo;
             *o = a.accumulate ? *o + acc : acc;
         }
-        ei = tl_next(a.E, ei, se);
     }
 #else
     float acc[JC];
@@ -146,11 +144,11 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
 #endif
 #pragma unroll
     for (int j = 0; j < JC; ++j) {
-        if (base + step * j < a.n1) {
-            float *o = ob + (long long)ei * a.E.slot_stride;
+        const long long eo = s_eoff[j];
+        if (eo >= 0) {
+            float *o = ob + eo;
             *o = a.accumulate ? *o + acc[j] : acc[j];
         }
-        ei = tl_next(a.E, ei, se);
     }
 #endif
 }
@@ -181,18 +179,19 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
     }
 }
 
-// blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks.  The samples of
-// the next (residue, chunk) are loaded before the current products are formed (two register windows).
+// blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks.  The ring
+// offsets of a (residue, chunk)'s window and receiver-side samples are the same for every thread of the
+// CTA: computed once per iteration into shared memory.
 template <int NH, int JC>
-__global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
+__global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_MINB : 1) k_tlag_image(const TlagArgs a)
 {
     constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
+    __shared__ long long s_doff[NW], s_loff[JC];
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
-    if (X >= a.x_hi) return;
+    const bool act = X < a.x_hi;                          // no early exit: the CTA shares barriers
     const int Z = a.z_lo + blockIdx.y;
-    const long long pp = (long long)Z * a.NXP + X;
+    const long long pp = (long long)Z * a.NXP + (act ? X : a.x_lo);
     const int step = 2 * a.lag;
-    const int sd = tl_inc(a.D, step), sl = tl_inc(a.L, step);
     float acc[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) acc[i] = 0.f;
@@ -213,19 +212,30 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
         for (int r = 0; r < step; ++r) {
 #pragma unroll 1
             for (int base = a.n0 + r; base < a.n1; base += step * JC) {
-                float win[NW], lv[JC];
                 const int m0 = base - step * HM;
-                int di = tl_index(a.D, m0), li = tl_index(a.L, base);
+                __syncthreads();                          // every thread is done with the previous tables
+                for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
+                    if (k < NW) {
+                        const int m = m0 + step * k;
+                        s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
+                    } else {
+                        const int n = base + step * (k - NW);
+                        s_loff[k - NW] = n < a.n1 ? tl_slot(a.L, n) : -1;
+                    }
+                }
+                __syncthreads();
+                if (!act) continue;
+                float win[NW], lv[JC];
+                const float *db = a.D.base + off, *lb0 = a.L.base + off;
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                    const int m = m0 + step * k;
-                    win[k] = (m >= 0 && m <= a.nt - 2) ? __ldg(a.D.base + (long long)di * a.D.slot_stride + off) : 0.f;
-                    di = tl_next(a.D, di, sd);
+                    const long long o = s_doff[k];
+                    win[k] = o >= 0 ? __ldg(db + o) : 0.f;
                 }
 #pragma unroll
                 for (int j = 0; j < JC; ++j) {
-                    lv[j] = base + step * j < a.n1 ? __ldg(a.L.base + (long long)li * a.L.slot_stride + off) : 0.f;
-                    li = tl_next(a.L, li, sl);
+                    const long long o = s_loff[j];
+                    lv[j] = o >= 0 ? __ldg(lb0 + o) : 0.f;
                 }
 #if FWIME_TL_IMG_F32X2
 #pragma unroll
@@ -270,6 +280,7 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_image(const TlagArgs a)
         for (int i = 0; i < NH; ++i) acc[i] = ve[i] + vo[i];
     }
 #endif
+    if (!act) return;
 #pragma unroll
     for (int i = 0; i < NH; ++i) a.img[i * a.P + pp] += acc[i];
 }
