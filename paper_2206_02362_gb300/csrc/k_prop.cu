@@ -83,6 +83,9 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 #ifndef FWIME_PROP_PRED
 #define FWIME_PROP_PRED 1   // halo copies predicated, not branched (-0.5 %)
 #endif
+#ifndef FWIME_PROP_MINB_LOC1
+#define FWIME_PROP_MINB_LOC1 3   // one local source: up to 128 registers, 4 CTAs per SM like the plain variants
+#endif
 #ifndef FWIME_PROP_MINB_PLAIN
 #define FWIME_PROP_MINB_PLAIN 3   // up to 128 registers: still 4 CTAs per SM, fewer rematerialised operands
 #endif
@@ -127,7 +130,7 @@ __device__ __forceinline__ PropK prop_k(const PropArgs &a)
 // columns (2 h, 2 h + 1) of a float4
 __device__ __forceinline__ f32x2 half2(const float4 &v, int h) { return h == 0 ? pk(v.x, v.y) : pk(v.z, v.w); }
 
-template <bool LOCAL, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC>
 __device__ __forceinline__ void row_math_pk(const PropArgs &a, const PropK &K, const float4 &L, const float4 &Q0, const float4 &Q1,
                                          const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
                                          const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
@@ -135,6 +138,7 @@ __device__ __forceinline__ void row_math_pk(const PropArgs &a, const PropK &K, c
                                          const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
                                          const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
 {
+    constexpr bool LOCAL = LOC > 0;
     const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};
     const f32x2 GZ = pk(gzz, gzz), NGZ = pk(-gzz, -gzz);
     float ov[4], dv[4];
@@ -155,9 +159,11 @@ __device__ __forceinline__ void row_math_pk(const PropArgs &a, const PropK &K, c
             f32x2 sv = pk(0.f, 0.f);
             if (LOCAL) {
                 sv = fma2(K.a0, half2(lf0, h), sv);
-                sv = fma2(K.a1, half2(lf1, h), sv);
-                sv = fma2(K.a2, half2(lf2, h), sv);
-                sv = fma2(half2(lcf, h), half2(lfc, h), sv);
+                if (LOC == 2) {
+                    sv = fma2(K.a1, half2(lf1, h), sv);
+                    sv = fma2(K.a2, half2(lf2, h), sv);
+                    sv = fma2(half2(lcf, h), half2(lfc, h), sv);
+                }
             }
             if (SRC) sv = add2(sv, pk(sj == j ? amp : 0.f, sj == j + 1 ? amp : 0.f));
             lap = add2(lap, sv);
@@ -176,7 +182,7 @@ __device__ __forceinline__ void row_math_pk(const PropArgs &a, const PropK &K, c
     o = make_float4(ov[0], ov[1], ov[2], ov[3]);
     if (D2) d2 = make_float4(dv[0], dv[1], dv[2], dv[3]);
 }
-template <bool LOCAL, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC>
 __device__ __forceinline__ void row_math_sc(const PropArgs &a, const float4 &L, const float4 &Q0, const float4 &Q1,
                                          const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
                                          const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
@@ -184,6 +190,7 @@ __device__ __forceinline__ void row_math_sc(const PropArgs &a, const float4 &L, 
                                          const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
                                          const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
 {
+    constexpr bool LOCAL = LOC > 0;
     const float rr[12] = {L.x, L.y, L.z, L.w, Q4.x, Q4.y, Q4.z, Q4.w, Rr.x, Rr.y, Rr.z, Rr.w};
     const float axc = a.ax[0] + a.az[0];
     float ov[4], dv[4];
@@ -203,9 +210,11 @@ __device__ __forceinline__ void row_math_sc(const PropArgs &a, const float4 &L, 
             float sv = 0.f;
             if (LOCAL) {
                 sv = fmaf(a.a0, cmp(lf0, j), sv);
-                sv = fmaf(a.a1, cmp(lf1, j), sv);
-                sv = fmaf(a.a2, cmp(lf2, j), sv);
-                sv = fmaf(cmp(lcf, j), cmp(lfc, j), sv);
+                if (LOC == 2) {
+                    sv = fmaf(a.a1, cmp(lf1, j), sv);
+                    sv = fmaf(a.a2, cmp(lf2, j), sv);
+                    sv = fmaf(cmp(lcf, j), cmp(lfc, j), sv);
+                }
             }
             if (SRC) sv += sj == j ? amp : 0.f;
             lap += sv;
@@ -221,7 +230,7 @@ __device__ __forceinline__ void row_math_sc(const PropArgs &a, const float4 &L, 
 }
 // the packed form where it measured faster: the variants with dense local sources always; the
 // plain ones (point source, D2t) only under FWIME_PROP_F32X2_PLAIN
-template <bool LOCAL, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC>
 __device__ __forceinline__ void row_math(const PropArgs &a, const PropK &K, const float4 &L, const float4 &Q0, const float4 &Q1,
                                          const float4 &Q2, const float4 &Q3, const float4 &Q4, const float4 &Q5,
                                          const float4 &Q6, const float4 &Q7, const float4 &Q8, const float4 &Rr,
@@ -229,19 +238,21 @@ __device__ __forceinline__ void row_math(const PropArgs &a, const PropK &K, cons
                                          const float4 &lf2, const float4 &lcf, const float4 &lfc, float gzz,
                                          const float4 &gxv, int sj, float amp, float4 &o, float4 &d2)
 {
+    constexpr bool LOCAL = LOC > 0;
     if constexpr (FWIME_PROP_F32X2 && (LOCAL || FWIME_PROP_F32X2_PLAIN))
-        row_math_pk<LOCAL, D2, SRC>(a, K, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
+        row_math_pk<LOC, D2, SRC>(a, K, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
                                     gxv, sj, amp, o, d2);
     else
-        row_math_sc<LOCAL, D2, SRC>(a, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
+        row_math_sc<LOC, D2, SRC>(a, L, Q0, Q1, Q2, Q3, Q4, Q5, Q6, Q7, Q8, Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz,
                                     gxv, sj, amp, o, d2);
 }
 
 // The time step of one warp's work item (strip, chunk) of shot `shot`; wsm is the warp's shared
 // memory (CUR_SLOTS x CUR_ROW + AUX_SLOTS x naux_max x STRIP floats).
-template <bool LOCAL, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC>
 __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, const int shot, float *wsm)
 {
+    constexpr bool LOCAL = LOC > 0;
     const int lane = threadIdx.x & 31;
     const int strip = wid % a.nstrip, chunk = wid / a.nstrip;
     const int x0 = strip * STRIP;
@@ -258,7 +269,8 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
     // aux row layout: [prev][c][f0?][f1?][f2?][coef, fc?]
     const int i_f0 = 2, i_f1 = i_f0 + (a.f0 != nullptr), i_f2 = i_f1 + (a.f1 != nullptr),
               i_cf = i_f2 + (a.f2 != nullptr);
-    const int naux = LOCAL ? i_cf + (a.fc != nullptr ? 2 : 0) : 2;
+    // LOC 1: exactly one local source, f0 (weight a0)
+    const int naux = LOC == 2 ? i_cf + (a.fc != nullptr ? 2 : 0) : (LOC == 1 ? 3 : 2);
     float *curR = wsm;
     float *auxR = wsm + CUR_SLOTS * CUR_ROW;
 
@@ -287,12 +299,16 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         if (LOCAL) {
             // local sources vanish outside the source rows: zero-filled there, not read
             const bool lin = xin && zr >= a.zs_lo && zr < a.zs_hi;
-            if (a.f0) cp16(dst + i_f0 * STRIP, a.f0 + so + o2, lin);
-            if (a.f1) cp16(dst + i_f1 * STRIP, a.f1 + so + o2, lin);
-            if (a.f2) cp16(dst + i_f2 * STRIP, a.f2 + so + o2, lin);
-            if (a.fc) {
-                cp16(dst + i_cf * STRIP, a.coef + o2, lin);
-                cp16(dst + (i_cf + 1) * STRIP, a.fc + so + o2, lin);
+            if (LOC == 1) {
+                cp16(dst + i_f0 * STRIP, a.f0 + so + o2, lin);
+            } else {
+                if (a.f0) cp16(dst + i_f0 * STRIP, a.f0 + so + o2, lin);
+                if (a.f1) cp16(dst + i_f1 * STRIP, a.f1 + so + o2, lin);
+                if (a.f2) cp16(dst + i_f2 * STRIP, a.f2 + so + o2, lin);
+                if (a.fc) {
+                    cp16(dst + i_cf * STRIP, a.coef + o2, lin);
+                    cp16(dst + (i_cf + 1) * STRIP, a.fc + so + o2, lin);
+                }
             }
         }
     };
@@ -334,7 +350,9 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         const float4 pv = lds4(arow);                                                                        \
         const float4 cv = lds4(arow + STRIP);                                                                \
         float4 lf0 = f4zero(), lf1 = f4zero(), lf2 = f4zero(), lcf = f4zero(), lfc = f4zero();               \
-        if (LOCAL) {                                                                                         \
+        if (LOC == 1) {                                                                                      \
+            lf0 = lds4(arow + i_f0 * STRIP);                                                                 \
+        } else if (LOC == 2) {                                                                               \
             if (a.f0) lf0 = lds4(arow + i_f0 * STRIP);                                                       \
             if (a.f1) lf1 = lds4(arow + i_f1 * STRIP);                                                       \
             if (a.f2) lf2 = lds4(arow + i_f2 * STRIP);                                                       \
@@ -348,7 +366,7 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
             sj = (sd >= 0 && sd < 4) ? (int)sd : -1;                                                         \
         }                                                                                                    \
         float4 o, d2;                                                                                        \
-        row_math<LOCAL, D2, SRC>(a, prop_k(a), L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
+        row_math<LOC, D2, SRC>(a, prop_k(a), L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
                                  q[(4 + (R)) % 9], q[(5 + (R)) % 9], q[(6 + (R)) % 9], q[(7 + (R)) % 9],      \
                                  q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
         if (xin) {                                                                                           \
@@ -375,15 +393,15 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
     cp_wait<0>();
 }
 
-template <bool LOCAL, bool D2, bool SRC>
-__global__ void __launch_bounds__(PROP_WARPS * 32, LOCAL ? FWIME_PROP_MIN_BLOCKS : FWIME_PROP_MINB_PLAIN) k_prop(const PropArgs a)
+template <int LOC, bool D2, bool SRC>
+__global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN)) k_prop(const PropArgs a)
 {
     extern __shared__ float4 smem4[];
     const int wic = threadIdx.x >> 5;
     const int wid = blockIdx.x * PROP_WARPS + wic;
     if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
     float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP);
-    prop_body<LOCAL, D2, SRC>(a, wid, blockIdx.y, wsm);
+    prop_body<LOC, D2, SRC>(a, wid, blockIdx.y, wsm);
 }
 
 // ------------------------------------------------------------- grouped forward
@@ -412,7 +430,7 @@ __global__ void __launch_bounds__(PROP_WARPS * 32, 4) k_prop_group(const GroupMe
     const int wid = (local - shot * cps) * PROP_WARPS + wic;
     if (wid >= sa.nstrip * sa.nchunk) return;   // warp-uniform
     float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * 2 * STRIP);
-    prop_body<false, false, true>(sa, wid, shot, wsm);
+    prop_body<0, false, true>(sa, wid, shot, wsm);
 }
 
 // after step n the new field q^{n+1} of a member is in buffer B for even n, A for odd n
@@ -444,22 +462,22 @@ cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const
     return cudaGetLastError();
 }
 
-template <bool LOCAL, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC>
 static void launch_prop_t(const PropArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_prop<LOCAL, D2, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_prop<LOC, D2, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr = true;
     }
-    k_prop<LOCAL, D2, SRC><<<grid, block, smem, st>>>(a);
+    k_prop<LOC, D2, SRC><<<grid, block, smem, st>>>(a);
 }
 
 // Resident CTAs per SM of the plain (no local source) variant with the smem it launches with.
 cudaError_t prop_occupancy(int *blocks_per_sm)
 {
     const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * 2 * STRIP) * sizeof(float);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_prop<false, false, false>, PROP_WARPS * 32,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_prop<0, false, false>, PROP_WARPS * 32,
                                                          smem);
 }
 
@@ -475,16 +493,21 @@ cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
     const bool src = a.src_off != nullptr;
     a.naux_max = 2 + (local ? (a.f0 != nullptr) + (a.f1 != nullptr) + (a.f2 != nullptr) + (a.fc ? 2 : 0) : 0);
     const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP) * sizeof(float);
-    const int key = (local ? 4 : 0) | (d2 ? 2 : 0) | (src ? 1 : 0);
+    const int loc = !local ? 0 : (a.f1 || a.f2 || a.fc || !a.f0) ? 2 : 1;
+    const int key = loc * 4 + (d2 ? 2 : 0) + (src ? 1 : 0);
     switch (key) {
-    case 0: launch_prop_t<false, false, false>(a, grid, block, smem, st); break;
-    case 1: launch_prop_t<false, false, true>(a, grid, block, smem, st); break;
-    case 2: launch_prop_t<false, true, false>(a, grid, block, smem, st); break;
-    case 3: launch_prop_t<false, true, true>(a, grid, block, smem, st); break;
-    case 4: launch_prop_t<true, false, false>(a, grid, block, smem, st); break;
-    case 5: launch_prop_t<true, false, true>(a, grid, block, smem, st); break;
-    case 6: launch_prop_t<true, true, false>(a, grid, block, smem, st); break;
-    default: launch_prop_t<true, true, true>(a, grid, block, smem, st); break;
+    case 0: launch_prop_t<0, false, false>(a, grid, block, smem, st); break;
+    case 1: launch_prop_t<0, false, true>(a, grid, block, smem, st); break;
+    case 2: launch_prop_t<0, true, false>(a, grid, block, smem, st); break;
+    case 3: launch_prop_t<0, true, true>(a, grid, block, smem, st); break;
+    case 4: launch_prop_t<1, false, false>(a, grid, block, smem, st); break;
+    case 5: launch_prop_t<1, false, true>(a, grid, block, smem, st); break;
+    case 6: launch_prop_t<1, true, false>(a, grid, block, smem, st); break;
+    case 7: launch_prop_t<1, true, true>(a, grid, block, smem, st); break;
+    case 8: launch_prop_t<2, false, false>(a, grid, block, smem, st); break;
+    case 9: launch_prop_t<2, false, true>(a, grid, block, smem, st); break;
+    case 10: launch_prop_t<2, true, false>(a, grid, block, smem, st); break;
+    default: launch_prop_t<2, true, true>(a, grid, block, smem, st); break;
     }
     return cudaGetLastError();
 }
