@@ -77,8 +77,11 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 #ifndef FWIME_PROP_AUX_SLOTS
 #define FWIME_PROP_AUX_SLOTS 4
 #endif
+// Variants k_prop<LOC, D2, SRC>: LOC = 0 no dense local source, 1 exactly one (f0, weight a0), 2 the
+// general sum a0 f0 + a1 f1 + a2 f2 + coef fc; D2 writes D2t; SRC adds the point source.  Register
+// bounds (minimum resident CTAs) per kind:
 #ifndef FWIME_PROP_MIN_BLOCKS
-#define FWIME_PROP_MIN_BLOCKS 1
+#define FWIME_PROP_MIN_BLOCKS 1   // general local sources (up to five extra rows per stage)
 #endif
 #ifndef FWIME_PROP_PRED
 #define FWIME_PROP_PRED 1   // halo copies predicated, not branched (-0.5 %)
@@ -107,8 +110,7 @@ static_assert(CUR_SLOTS >= AUX_SLOTS + 4, "the q^n ring must hold rows z .. z+4+
 #define FWIME_PROP_F32X2_PLAIN 1
 #endif
 // Packed two-lane FP32 (f32x2, see fwime_kernels.cuh) on columns (j, j + 1): half the floating-point
-// issue slots of the scalar form, with its rounding.
-// the packed coefficient operands
+// issue slots of the scalar form, with its rounding.  The coefficient operands as register pairs:
 struct PropK {
     f32x2 axc, kx[5], kz[5], inv, a0, a1, a2;
 };
