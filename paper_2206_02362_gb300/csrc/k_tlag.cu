@@ -17,7 +17,7 @@
 namespace fwk {
 
 // packed two-lane FP32 forms (f32x2): measured faster for the imaging kernel (-3.7 % at nh 21) and
-// slower for the scatter (+8.7 %), whose scalar form keeps 16 independent chains per thread
+// slower for the scatter (+8.7 %), whose scalar form keeps JC independent chains per thread
 #ifndef FWIME_TL_SC_F32X2
 #define FWIME_TL_SC_F32X2 0
 #endif
