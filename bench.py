@@ -149,10 +149,37 @@ def oracle_sample(wl, nt_sample: int, nshot_sample: int, threads: int):
     return upd / dt / 1e9, dt, f"{nshot_sample} shots x nt={nt_sample} of the {wl.name} grid (B~ + B~*)"
 
 
+# The oracle's CPU sample: B~ + B~* over nt = ORACLE_NT steps of the bench grid, one shot per host core
+# (OpenMP over shots), bounded by the host memory its full FP64 histories take.
+ORACLE_NT = 32
+
+
+def oracle_plan(wl):
+    """(shots, threads, host cores) of the oracle sample: every host core runs one shot, as long as
+    the shots' histories (about 8 padded FP64 fields x nt per shot) fit in half the available memory."""
+    try:
+        cores = len(os.sched_getaffinity(0))      # the cores this process may run on (nproc)
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    NZ, NX = wl.padded
+    per_shot = 8 * NZ * NX * ORACLE_NT * 8
+    avail = None
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                avail = int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    n = min(cores, wl.nshot)
+    if avail:
+        n = max(1, min(n, int(0.5 * avail // per_shot)))
+    return n, n, cores
+
+
 def cpu_baseline(wl):
-    threads = max(1, min(os.cpu_count() or 1, 8))
-    val, dt, sample = oracle_sample(wl, 32, threads, threads)
-    return {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+    nshot, threads, cores = oracle_plan(wl)
+    val, dt, sample = oracle_sample(wl, ORACLE_NT, nshot, threads)
+    return {"value": val, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle", "sample": sample,
             "seconds": round(dt, 2)}
 
 
@@ -162,10 +189,10 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args)
-    threads = max(1, min(os.cpu_count() or 1, 8))
+    nshot, threads, cores = oracle_plan(wl)
     vals = []
     for i in range(args.warmup + args.steps):
-        val, dt, sample = oracle_sample(wl, 16, threads, threads)
+        val, dt, sample = oracle_sample(wl, ORACLE_NT, nshot, threads)
         if i >= args.warmup:
             vals.append((val, dt))
     value = statistics.mean(v for v, _ in vals)
@@ -174,7 +201,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": config(wl, args, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

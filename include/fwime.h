@@ -109,13 +109,6 @@ enum {
                                        the odd mirror of the 4 rows below after every step (forward and
                                        adjoint); receivers on the surface row record 0.  Not available in
                                        fwime_forward_group. */
-    FWIME_OPT_TWO_STEP = 14        /* 1: the forward, background and scattered propagations of f, B~ and
-                                       the adjoints' recomputations advance two time steps per stencil
-                                       launch (temporal blocking: 16 instead of 24 bytes per two updates;
-                                       identical arithmetic); 0 (default): one step per launch, which
-                                       measures faster on GB300 (the one-step stencil is issue-bound, not
-                                       byte-bound).  Not used with the free surface, the plain path or
-                                       time lags. */
 };
 
 /* Kernel families, for fwime_profile_read. */
@@ -248,19 +241,23 @@ int fwime_last_error_detail(fwime_ctx *ctx, char *buf, size_t n);
  * For callers that cannot call cudaMalloc (inside another allocator or memory
  * pool, with device memory reserved up front, or on a thread that must not
  * enter the driver's allocator): f(m) of fwime_forward with no context and no
- * allocation.  Its scratch (padded model, sponge tables, offsets, two
- * wavefields per shot) is one file-scope device array of
+ * allocation.  Its scratch (padded model, sponge tables, offsets, a status
+ * word, two wavefields per shot) is one file-scope device array of
  * FWIME_STATIC_SCRATCH_BYTES held by every GPU that loads the library until
  * the process exits.  v[nz][nx], w[nshot][nt] and d[nshot][nt][nrec] are
  * caller-owned DEVICE pointers; work is enqueued on cuda_stream (NULL = legacy
- * default stream).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it: make that first call before
- * any stream capture.  Every call shares the array and leaves its contents
- * behind (wavefields are cleared at the start of a call); calls whose work
- * overlaps on the GPU race on it and must be serialised by the caller.
- * Returns FWIME_ENOMEM, with a message for fwime_static_last_error, when the
- * problem needs more than FWIME_STATIC_SCRATCH_BYTES (see
- * fwime_static_scratch_bytes), FWIME_EINVAL for a bad grid or geometry. */
+ * default stream).  Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing), copies the source
+ * and receiver offsets in from host memory and waits for the model check on
+ * its stream; the time steps are then enqueued and the call returns without
+ * waiting for them.  Every call shares the array and leaves its contents
+ * behind (wavefields and status are cleared at the start of a call); calls
+ * whose work overlaps on the GPU race on it and must be serialised by the
+ * caller.  Returns FWIME_ECFL (d untouched, no time step run) for a velocity
+ * that is not positive or breaks the stability bound of FWIME_ECFL;
+ * FWIME_ENOMEM when the problem needs more than FWIME_STATIC_SCRATCH_BYTES
+ * (see fwime_static_scratch_bytes); FWIME_EINVAL for a bad grid or geometry;
+ * each with a message for fwime_static_last_error. */
 #define FWIME_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 size_t fwime_static_scratch_bytes(const fwime_grid *g, const fwime_geom *geo);
 int fwime_forward_static(const fwime_grid *g, const fwime_geom *geo, const float *v, const float *w,

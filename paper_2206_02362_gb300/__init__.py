@@ -31,7 +31,6 @@ OPT_REUSE_BACKGROUND = 10
 OPT_BACKGROUND_REUSED = 11
 OPT_TIME_LAG = 12
 OPT_FREE_SURFACE = 13
-OPT_TWO_STEP = 14
 K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
 KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 (OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
@@ -228,8 +227,7 @@ class Context:
 
     _OPTS = {"shots_per_batch": OPT_SHOTS_PER_BATCH, "segment": OPT_SEGMENT, "plain": OPT_PLAIN,
              "graph": OPT_GRAPH, "host_io": OPT_HOST_IO, "zchunk": OPT_ZCHUNK, "profile": OPT_PROFILE,
-             "reuse_background": OPT_REUSE_BACKGROUND, "time_lag": OPT_TIME_LAG, "free_surface": OPT_FREE_SURFACE,
-             "two_step": OPT_TWO_STEP}
+             "reuse_background": OPT_REUSE_BACKGROUND, "time_lag": OPT_TIME_LAG, "free_surface": OPT_FREE_SURFACE}
 
     def set_option(self, name, value):
         opt = self._OPTS[name] if isinstance(name, str) else int(name)

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfwime.so")
-SOURCES = ["fwime_api.cu", "k_prop.cu", "k_prop2.cu", "k_ext.cu", "k_misc.cu", "k_spline.cu", "k_tlag.cu", "fwime_static.cu"]
+SOURCES = ["fwime_api.cu", "k_prop.cu", "k_ext.cu", "k_misc.cu", "k_spline.cu", "k_tlag.cu", "fwime_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

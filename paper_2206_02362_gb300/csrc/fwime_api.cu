@@ -37,8 +37,6 @@ using namespace fwk;
 
 namespace {
 
-const double LAMBDA_MAX = 6.5015873015873;   // max eigenvalue of -D2 (8th order) times h^2
-
 struct Graph {
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;
@@ -59,7 +57,6 @@ struct fwime_ctx {
     int opt_S = 0, opt_K = 0, opt_plain = 0, opt_graph = 0, opt_host_io = 0, opt_zchunk = 0, opt_reuse_bg = 0;
     int opt_tlag = 0;               // > 0: B~ / B~* extend with time lags spaced opt_tlag steps
     int opt_fs = 0;                 // 1: free surface at the top physical row
-    int opt_two = 0;                // 1: two time steps per stencil launch where the schedule allows
     // background-wavefield checkpoints of every shot, [nseg][2][nshot][P], written by B and B~ and
     // read by B* and B~* on the same v, w (FWIME_OPT_REUSE_BACKGROUND)
     struct BgCache {
@@ -237,11 +234,11 @@ static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int
     s.model = al(P) * 2 + al(NZ) + al(NXP);   // c, bpad, gz, gx
     size_t f = 0;
     switch (op) {
-    case FWIME_OP_FORWARD: f = 4; break;   // 2 + 2 output fields of the two-step stencil
+    case FWIME_OP_FORWARD: f = 2; break;
     case FWIME_OP_BORN: s.model += al(P); f = 5; break;
-    case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 8 + 2 * K; break;
-    case FWIME_OP_BORN_ADJ: s.model += al(P); f = 4 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
-    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 4 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
+    case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 4 + 2 * K; break;
+    case FWIME_OP_BORN_ADJ: s.model += al(P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
+    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
     case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
     case FWIME_OP_TOMO_ADJ:
     case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + 4 * nseg; break;
@@ -400,11 +397,11 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
         return FWIME_OK;
     }
     switch (op) {
-    case FWIME_OP_FORWARD: nf = 4; break;
+    case FWIME_OP_FORWARD: nf = 2; break;
     case FWIME_OP_BORN: nf = 5; break;
-    case FWIME_OP_BORN_EXT: nf = 8; nk = 2; break;
+    case FWIME_OP_BORN_EXT: nf = 4; nk = 2; break;
     case FWIME_OP_BORN_ADJ:
-    case FWIME_OP_BORN_EXT_ADJ: nf = 4; nk = 1; nr = 1; nck = no_ckpt ? 0 : 2; break;
+    case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = no_ckpt ? 0 : 2; break;
     case FWIME_OP_TOMO: nf = 8; nk = 4; break;
     case FWIME_OP_OBJECTIVE: nf = 4; nk = 2; break;
     default: nf = 4; nk = 3; nr = 3; nck = 4; break;
@@ -424,7 +421,6 @@ struct Run {
     fwime_ctx *x;
     WS w;
     int zchunk, nstrip, nchunk;
-    int z2chunk, n2strip, n2chunk;   // decomposition of the two-step stencil
     PropArgs base{};
 };
 
@@ -443,17 +439,6 @@ static void init_run(fwime_ctx *x, Run &r, int S)
     }
     r.zchunk = zc;
     r.nchunk = (rows + zc - 1) / zc;
-    // two-step stencil: 120 owned columns per warp; a chunk recomputes 8 halo rows of the first step, so
-    // chunks stay long (at least 48 rows) and the grid aims at about 12 resident warps per SM
-    r.n2strip = prop2_strips(x->NXP);
-    {
-        const long long target = 152LL * 12;
-        const long long per = (long long)r.n2strip * std::max(S, 1);
-        const long long nchunk_t = std::max<long long>(1, (target + per - 1) / per);
-        int z2 = (int)((rows + nchunk_t - 1) / nchunk_t);
-        r.z2chunk = std::min(std::max(z2, 48), rows);
-        r.n2chunk = (rows + r.z2chunk - 1) / r.z2chunk;
-    }
     PropArgs &a = r.base;
     std::memset(&a, 0, sizeof(a));
     a.NZ = x->NZ; a.NXP = x->NXP; a.zchunk = r.zchunk; a.nstrip = r.nstrip; a.nchunk = r.nchunk; a.P = x->P;
@@ -490,33 +475,6 @@ static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out,
     if (x->opt_fs)
         LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * (d2 ? 44.0 : 40.0),
                launch_free_surface(out, d2, Sb, x->P, x->NXP, x->o, x->st));
-    return FWIME_OK;
-}
-
-static bool two_step(const fwime_ctx *x) { return x->opt_two && !x->opt_fs && !x->opt_plain; }
-
-// two steps n, n+1 in one launch: q^{n+1} -> out1, q^{n+2} -> out2 (both distinct from cur and prev),
-// optional D2t of both steps, point-source amplitudes wsrc[0], wsrc[1], local sources f0 (n) and f1 (n+1)
-static int prop2(Run &r, int Sb, const float *cur, const float *prev, float *out1, float *out2, float *d2a,
-                 float *d2b, const float *wsrc, int src_shot0, const float *f0 = nullptr, const float *f1 = nullptr,
-                 float a0 = 0.f)
-{
-    fwime_ctx *x = r.x;
-    Prop2Args a{};
-    a.NZ = x->NZ; a.NXP = x->NXP; a.zchunk = r.z2chunk; a.nstrip = r.n2strip; a.nchunk = r.n2chunk; a.P = x->P;
-    for (int k = 0; k < 5; ++k) { a.ax[k] = r.base.ax[k]; a.az[k] = r.base.az[k]; }
-    a.inv_dt2 = r.base.inv_dt2; a.src_scale = r.base.src_scale;
-    a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx;
-    a.cur = cur; a.prev = prev; a.out1 = out1; a.out2 = out2; a.d2a = d2a; a.d2b = d2b;
-    if (wsrc) {
-        a.src_off = x->d_src_off + src_shot0;
-        a.src_amp = wsrc;
-        a.src_stride = x->g.nt;
-    }
-    a.f0 = f0; a.f1 = f1; a.a0 = a0;
-    const double pts = (double)x->NZ * x->NX;
-    const double per = 16.0 + (d2a ? 8 : 0) + (f0 ? 8 : 0);   // two updates: q^n, q^{n-1} in, two fields out
-    LAUNCH(FWIME_K_PROP, pts * (Sb * per + 8.0), launch_prop2(a, Sb, x->st));
     return FWIME_OK;
 }
 
@@ -606,9 +564,7 @@ static int prep_model(fwime_ctx *x, Run &r, const float *v)
     PrepArgs a{};
     a.nz = x->g.nz; a.nx = x->g.nx; a.o = x->o; a.NZ = x->NZ; a.NX = x->NX; a.NXP = x->NXP; a.W = x->g.sponge;
     a.dt = x->g.dt;
-    const double lim = 2.0 / ((double)x->g.dt *
-                              std::sqrt(LAMBDA_MAX * (1.0 / ((double)x->g.dx * x->g.dx) + 1.0 / ((double)x->g.dz * x->g.dz))));
-    a.cfl_limit2 = (float)(lim * lim);
+    a.cfl_limit2 = cfl_vmax2(x->g.dt, x->g.dx, x->g.dz);
     a.v = v; a.c = r.w.c; a.gz = r.w.gz; a.gx = r.w.gx; a.bpad = r.w.bpad; a.status = x->d_status;
     a.fs = x->opt_fs;
     LAUNCH(FWIME_K_OTHER, 12.0 * x->NZ * x->NXP, launch_prep(a, x->st));
@@ -672,21 +628,12 @@ static int run_forward(fwime_ctx *x, Run &r, const float *v, const float *w, flo
     const size_t nd = (size_t)nt * x->nrec;
     for (int s0 = 0; s0 < x->nshot; s0 += S) {
         const int Sb = std::min(S, x->nshot - s0);
-        float *cur = r.w.f[0], *prv = r.w.f[1], *t1 = r.w.f[2], *t2 = r.w.f[3];
-        // all four: the stencil never writes the inactive rows and columns, which must read as zero
-        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
+        float *cur = r.w.f[0], *prv = r.w.f[1];
+        // both: the stencil never writes the inactive rows and columns, which must read as zero
+        for (int i = 0; i < 2; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
         float *db = d + s0 * nd;
         TRY(zero(x, db, sizeof(float) * Sb * nd));
-        int n = 0;
-        if (two_step(x))
-            for (; n + 2 < nt; n += 2) {
-                TRY(prop2(r, Sb, cur, prv, t1, t2, nullptr, nullptr, w + (size_t)s0 * nt + n, s0));
-                TRY(record(r, Sb, t1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
-                TRY(record(r, Sb, t2, nullptr, db + (size_t)(n + 2) * x->nrec, 0));
-                std::swap(cur, t2);
-                std::swap(prv, t1);
-            }
-        for (; n + 1 < nt; ++n) {
+        for (int n = 0; n + 1 < nt; ++n) {
             TRY(prop(r, Sb, cur, prv, prv, nullptr, w + (size_t)s0 * nt + n, s0));
             TRY(record(r, Sb, prv, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
             std::swap(cur, prv);
@@ -737,42 +684,22 @@ static int run_born_ext(fwime_ctx *x, Run &r, const float *v, const float *w, co
     for (int s0 = 0; s0 < x->nshot; s0 += S) {
         const int Sb = std::min(S, x->nshot - s0);
         float *c0 = r.w.f[0], *p0 = r.w.f[1], *c1 = r.w.f[2], *p1 = r.w.f[3];
-        float *u0 = r.w.f[4], *v0 = r.w.f[5], *u1 = r.w.f[6], *v1 = r.w.f[7];   // two-step outputs
-        // all eight: the stencil never writes the inactive rows and columns, which must read as zero
-        for (int i = 0; i < 8; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
+        // all four: the stencil never writes the inactive rows and columns, which must read as zero
+        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
         float *db = d + s0 * nd;
         TRY(zero(x, db, sizeof(float) * Sb * nd));
-        const bool two = two_step(x);
         for (int n0 = 0; n0 < nt - 1; n0 += K) {
             const int n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
             if (x->bg_written) {
                 TRY(copyf(x, bg_slot(x, n0 / K, 0, s0), c0, (size_t)Sb * x->P));
                 TRY(copyf(x, bg_slot(x, n0 / K, 1, s0), p0, (size_t)Sb * x->P));
             }
-            int n = n0;
-            if (two)
-                for (; n + 1 < n1; n += 2) {
-                    TRY(prop2(r, Sb, c0, p0, u0, v0, Dr + (n - n0) * SP, Dr + (n + 1 - n0) * SP,
-                              w + (size_t)s0 * nt + n, s0));
-                    std::swap(c0, v0);
-                    std::swap(p0, u0);
-                }
-            for (; n < n1; ++n) {
+            for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, c0, p0, p0, Dr + (n - n0) * SP, w + (size_t)s0 * nt + n, s0));
                 std::swap(c0, p0);
             }
             TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Dr, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
-            n = n0;
-            if (two)
-                for (; n + 1 < n1; n += 2) {
-                    TRY(prop2(r, Sb, c1, p1, u1, v1, nullptr, nullptr, nullptr, 0, Er + (n - n0) * SP,
-                              Er + (n + 1 - n0) * SP, 1.f));
-                    TRY(record(r, Sb, u1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
-                    TRY(record(r, Sb, v1, nullptr, db + (size_t)(n + 2) * x->nrec, 0));
-                    std::swap(c1, v1);
-                    std::swap(p1, u1);
-                }
-            for (; n < n1; ++n) {
+            for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
                 TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
                 std::swap(c1, p1);
@@ -795,9 +722,9 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
     for (int s0 = 0; s0 < x->nshot; s0 += S) {
         const int Sb = std::min(S, x->nshot - s0);
         const size_t fb = sizeof(float) * (size_t)Sb * x->P;
-        float *cur = r.w.f[0], *prv = r.w.f[1], *t1 = r.w.f[2], *t2 = r.w.f[3];   // t1, t2: two-step outputs
-        // all four: the stencil never writes the inactive rows and columns, which must read as zero
-        for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], fb));
+        float *cur = r.w.f[0], *prv = r.w.f[1];
+        // both: the stencil never writes the inactive rows and columns, which must read as zero
+        for (int i = 0; i < 2; ++i) TRY(zero(x, r.w.f[i], fb));
         TRY(zero(x, Mu, sizeof(float) * R * SP));
         const float *ws = w + (size_t)s0 * nt;
         // checkpoint (q^{n0}, q^{n0-1}) at every segment start: from the background cache, or a forward sweep
@@ -816,14 +743,7 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
             const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
             TRY(copyf(x, cur, ckp(j, 0), (size_t)Sb * x->P));
             TRY(copyf(x, prv, ckp(j, 1), (size_t)Sb * x->P));
-            int n = n0;
-            if (two_step(x))
-                for (; n + 1 < n1; n += 2) {
-                    TRY(prop2(r, Sb, cur, prv, t1, t2, Dr + (n - n0) * SP, Dr + (n + 1 - n0) * SP, ws + n, s0));
-                    std::swap(cur, t2);
-                    std::swap(prv, t1);
-                }
-            for (; n < n1; ++n) {
+            for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, cur, prv, prv, Dr + (n - n0) * SP, ws + n, s0));
                 std::swap(cur, prv);
             }
@@ -1436,7 +1356,7 @@ static int run_call(fwime_ctx *x, const Call &c)
     snprintf(key, sizeof(key), "%d|%p|%p|%p|%p|%p|%d|%a|%d|%d|%d|%d%d|%p|%d", c.op, (const void *)c.v, (const void *)c.w,
              (const void *)c.in1, (const void *)c.in2, (void *)c.out, c.accumulate, (double)c.eps, x->opt_S, x->opt_K,
              x->opt_zchunk, use_bg ? 1 : 0, write_bg ? 1 : 0, (const void *)(use_bg || write_bg ? x->bg.buf : nullptr),
-             x->opt_tlag * 4 + x->opt_fs * 2 + x->opt_two);
+             x->opt_tlag * 2 + x->opt_fs);
     auto it = x->graphs.find(key);
     if (it == x->graphs.end()) {
         CK(cudaStreamBeginCapture(x->st, cudaStreamCaptureModeThreadLocal));
@@ -1618,7 +1538,6 @@ int fwime_set_option(fwime_ctx *x, int option, long long value)
     case FWIME_OPT_HOST_IO: x->opt_host_io = value != 0; return FWIME_OK;
     case FWIME_OPT_ZCHUNK: if (value < 0 || value > 4096) break; x->opt_zchunk = (int)value; return FWIME_OK;
     case FWIME_OPT_PROFILE: x->opt_profile = value != 0; return FWIME_OK;
-    case FWIME_OPT_TWO_STEP: x->opt_two = value != 0; return FWIME_OK;
     case FWIME_OPT_FREE_SURFACE:
         x->opt_fs = value != 0;
         x->bg.valid = false;
@@ -1658,7 +1577,6 @@ int fwime_get_option(fwime_ctx *x, int option, long long *value)
     case FWIME_OPT_BACKGROUND_REUSED: *value = x->bg_used; return FWIME_OK;
     case FWIME_OPT_TIME_LAG: *value = x->opt_tlag; return FWIME_OK;
     case FWIME_OPT_FREE_SURFACE: *value = x->opt_fs; return FWIME_OK;
-    case FWIME_OPT_TWO_STEP: *value = x->opt_two; return FWIME_OK;
     }
     return fail(x, FWIME_EINVAL, "bad option %d", option);
 }

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace fwk {
 
 constexpr int STRIP = 128;      // x-points per warp in the stencil kernel (32 lanes x float4)
@@ -27,6 +29,18 @@ constexpr int EXT_STAGES = FWIME_EXT_STAGES;   // cp.async pipeline depth of the
 // status bits latched by kernels
 constexpr int ST_CFL = 1;
 constexpr int ST_BADV = 2;
+
+// Largest eigenvalue of -h^2 D2 for the 8th-order second-derivative stencil (its symbol at the Nyquist
+// wavenumber: 205/72 + 2 (8/5 + 1/5 + 8/315 + 1/560)).  The leapfrog scheme is stable while
+// dt v sqrt(LAMBDA_MAX (1/dx^2 + 1/dz^2)) < 2.
+constexpr double LAMBDA_MAX = 6.5015873015873;
+
+// Square of the largest velocity the scheme accepts at (dt, dx, dz), compared against v^2 by k_prep.
+inline float cfl_vmax2(float dt, float dx, float dz)
+{
+    const double lim = 2.0 / ((double)dt * std::sqrt(LAMBDA_MAX * (1.0 / ((double)dx * dx) + 1.0 / ((double)dz * dz))));
+    return (float)(lim * lim);
+}
 
 struct PropArgs {
     int NZ, NXP, zchunk, nstrip, nchunk;
@@ -70,24 +84,6 @@ inline void prop_pairs(PropArgs &a)
     a.a12 = make_float2(a.a1, a.a1);
     a.a22 = make_float2(a.a2, a.a2);
 }
-
-// two time steps per launch (k_prop2): q^{n+1} -> out1, q^{n+2} -> out2 (both distinct from cur, prev)
-struct Prop2Args {
-    int NZ, NXP, zchunk, nstrip, nchunk;
-    long long P;
-    float ax[5], az[5];
-    float inv_dt2;
-    const float *c, *gz, *gx;
-    const float *cur, *prev;       // q^n, q^{n-1}
-    float *out1, *out2;            // q^{n+1}, q^{n+2}
-    float *d2a, *d2b;              // optional D2t of steps n and n+1
-    const int *src_off;            // optional point source; amplitudes of steps n, n+1 at src_amp[s*stride + 0, 1]
-    const float *src_amp;
-    long long src_stride;
-    float src_scale;
-    const float *f0, *f1;          // optional dense local source of steps n and n+1 (weight a0)
-    float a0;
-};
 
 // grouped forward: one member = one shot batch on its own grid
 struct GroupMember {
@@ -171,8 +167,6 @@ struct TlagArgs {
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_prop(const PropArgs &a, int nshot, cudaStream_t st);
-cudaError_t launch_prop2(const Prop2Args &a, int nshot, cudaStream_t st);
-int prop2_strips(int NXP);         // warps per row of a two-step launch (120 owned columns each)
 cudaError_t prop_occupancy(int *blocks_per_sm);
 cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const GroupRec *g, int nrec_threads,
                               int step, cudaStream_t st, bool record);

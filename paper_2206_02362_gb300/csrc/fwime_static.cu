@@ -6,23 +6,29 @@
 // reserved up front, or a host thread that must never block on the driver's
 // allocator.  For them this entry point takes no context (creating one
 // allocates) and allocates nothing: its scratch -- the padded model c, b, the
-// sponge tables, the receiver/source offsets and two wavefields per shot --
-// lives in one file-scope __device__ array of FWIME_STATIC_SCRATCH_BYTES that
-// every GPU loading the library holds until the process exits.  The caller
-// still passes the inputs (v, w) and the output (d) as device pointers.
+// sponge tables, the receiver/source offsets, a status word and two wavefields
+// per shot -- lives in one file-scope __device__ array of
+// FWIME_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+// process exits.  The caller still passes the inputs (v, w) and the output (d)
+// as device pointers.
 //
-// The array's host-side name is only a stand-in, not a device address, so its
-// address is looked up once per device with cudaGetSymbolAddress (on the first
-// call made with that device current) and cached.  Every call shares the array
-// and leaves its contents behind; the wavefields are cleared at the start of
-// each call.  Calls whose work overlaps on the GPU (two streams, or two host
-// threads) race on the array and must be serialised by the caller.
+// The array's host-side name is only a stand-in, not a device address.  Every
+// call looks the address up with cudaGetSymbolAddress on the device that is
+// current at the time (the lookup allocates nothing), so the address is never
+// stale after a device reset or under another context.  Every call shares the
+// array and leaves its contents behind; the wavefields and the status word are
+// cleared at the start of each call.  Calls whose work overlaps on the GPU (two
+// streams, or two host threads) race on the array and must be serialised by
+// the caller.
+//
+// The model check (positive velocity below the stability bound) runs on the
+// device; the call copies the offsets in from host memory, waits for the check
+// on its stream and returns FWIME_ECFL before any time step when it fails.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "../../include/fwime.h"
@@ -34,33 +40,21 @@ static constexpr size_t SCRATCH_FLOATS = FWIME_STATIC_SCRATCH_BYTES / sizeof(flo
 static __device__ __align__(256) float g_scratch[SCRATCH_FLOATS];
 
 namespace {
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-float *g_addr[MAX_DEVICES] = {nullptr};
 thread_local char g_err[256] = {0};
 
 size_t al(size_t n) { return (n + 63) & ~(size_t)63; }   // 256-byte granules
 
+// Device address of the scratch array on the current device (looked up on every call).
 int scratch_ptr(float **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
-        snprintf(g_err, sizeof(g_err), "fwime_forward_static: no usable current device");
+        snprintf(g_err, sizeof(g_err), "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
         return FWIME_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            snprintf(g_err, sizeof(g_err), "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-            return FWIME_ECUDA;
-        }
-        g_addr[dev] = static_cast<float *>(p);
-    }
-    *out = g_addr[dev];
+    *out = static_cast<float *>(p);
     return FWIME_OK;
 }
 }  // namespace
@@ -124,7 +118,8 @@ extern "C" int fwime_forward_static(const fwime_grid *g, const fwime_geom *geo, 
     int *offs = reinterpret_cast<int *>(p);
     int *status = offs + nshot + nrec;
 
-    // offsets (host -> scratch); the host buffer is pinned by nobody, so the copy is synchronous
+    // offsets and a cleared status word (host -> scratch), model preparation with its check, and the
+    // status back; h and st_h are locals, so the call waits for the stream before it uses them again
     std::vector<int> h(nshot + nrec + 1, 0);
     for (int s = 0; s < nshot; ++s) h[s] = (geo->src_iz[s] + o) * NXP + geo->src_ix[s] + o;
     for (int r = 0; r < nrec; ++r) h[nshot + r] = (geo->rec_iz[r] + o) * NXP + geo->rec_ix[r] + o;
@@ -137,18 +132,23 @@ extern "C" int fwime_forward_static(const fwime_grid *g, const fwime_geom *geo, 
         }                                                                                            \
     } while (0)
     CKS(cudaMemcpyAsync(offs, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    CKS(cudaStreamSynchronize(st));   // h is a local vector: it must outlive the copy
+    PrepArgs pa{};
+    pa.nz = g->nz; pa.nx = g->nx; pa.o = o; pa.NZ = NZ; pa.NX = NX; pa.NXP = NXP; pa.W = g->sponge; pa.dt = g->dt;
+    pa.cfl_limit2 = cfl_vmax2(g->dt, g->dx, g->dz);
+    pa.v = v; pa.c = c; pa.gz = gz; pa.gx = gx; pa.bpad = bpad; pa.status = status;
+    CKS(launch_prep(pa, st));
+    int st_h = 0;
+    CKS(cudaMemcpyAsync(&st_h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKS(cudaStreamSynchronize(st));
+    if (st_h & ST_CFL) {
+        snprintf(g_err, sizeof(g_err),
+                 "fwime_forward_static: velocity violates the CFL bound (vmax < %.6g m/s) or is not positive",
+                 std::sqrt((double)pa.cfl_limit2));
+        return FWIME_ECFL;
+    }
     CKS(cudaMemsetAsync(fa, 0, sizeof(float) * P * nshot, st));
     CKS(cudaMemsetAsync(fb, 0, sizeof(float) * P * nshot, st));
     CKS(cudaMemsetAsync(d, 0, sizeof(float) * (size_t)nshot * nt * nrec, st));
-
-    PrepArgs pa{};
-    pa.nz = g->nz; pa.nx = g->nx; pa.o = o; pa.NZ = NZ; pa.NX = NX; pa.NXP = NXP; pa.W = g->sponge; pa.dt = g->dt;
-    const double lim = 2.0 / ((double)g->dt * std::sqrt(6.5015873015873 * (1.0 / ((double)g->dx * g->dx) +
-                                                                          1.0 / ((double)g->dz * g->dz))));
-    pa.cfl_limit2 = (float)(lim * lim);
-    pa.v = v; pa.c = c; pa.gz = gz; pa.gx = gx; pa.bpad = bpad; pa.status = status;
-    CKS(launch_prep(pa, st));
 
     PropArgs a;
     std::memset(&a, 0, sizeof(a));

@@ -51,12 +51,7 @@ struct RingIt {
     }
 };
 
-// ---- asynchronous global -> shared copies (LDGSTS); src_bytes = 0 zero-fills the 16 bytes
-__device__ __forceinline__ void cpa16(float *dst, const float *src, bool valid)
-{
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
-}
+// ---- asynchronous global -> shared copies (LDGSTS)
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -104,24 +99,8 @@ struct PairRow {
     }
 };
 
-// Copies the row segment [wal, wal + 4 * nchunk) of `src` (16-byte chunks, zero outside [0, NXP))
-// into `dst`; wal is a multiple of 4.
-__device__ __forceinline__ void copy_window(float *dst, const float *src, int wal, int nchunk, int NXP)
-{
-    for (int k = threadIdx.x; k < nchunk; k += EXT_TX) {
-        const int col = wal + 4 * k;
-        const bool ok = col >= 0 && col + 4 <= NXP;
-        cpa16(dst + 4 * k, ok ? src + col : src, ok);
-    }
-}
-
 // ------------------------------------------------------------------ scatter
 
-// Register-blocked scatter: a thread owns PY outputs y_j = ybase + 2j (j < PY), so the D
-// samples they need, y_j - 2 sigma h, fall on the NH + PY - 1 even-spaced positions
-// ybase + 2m: one shared-memory load per position serves up to PY multiply-adds.  The
-// thread's PY x NH weights stay in registers for the whole segment.  Outputs are staged
-// through shared memory and stored coalesced.
 // Vector loads from shared memory: VW = 4 (16-byte, LDS.128) or 2 (8-byte, LDS.64) consecutive floats.
 template <int VW, int N>
 __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
@@ -371,107 +350,6 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     cpa_wait<0>();
 }
 
-#if FWIME_EXT_RB
-// Register-blocked scatter: a thread owns PY consecutive outputs y_j = yb + j; the D samples
-// they need, y_j - 2 sigma h, lie in the 4 HM + PY consecutive positions [yb - 2HM, yb + PY + 2HM),
-// read with conflict-free vector loads (the column range is aligned so that the CTA's window
-// starts on a 16-byte boundary).  The PY x NH weights stay in registers for the whole segment.
-// The (step, shot) pairs stream through an EXT_STAGES-deep cp.async ring, one barrier per pair.
-template <int NH, int PY, int SIGMA>
-__global__ void __launch_bounds__(EXT_TX) k_scatter_rb(const ExtArgs a)
-{
-    extern __shared__ float4 sm4[];
-    float *sm = reinterpret_cast<float *>(sm4);
-    constexpr int HM = (NH - 1) / 2;
-    constexpr int TXS = EXT_TX * PY;               // outputs per CTA
-    constexpr int SPAN = TXS + 4 * HM;             // D window, starting at y0 - 2 HM (16-byte aligned)
-    constexpr int NCH = (SPAN + 3) / 4;
-    constexpr int STG = 4 * NCH + 4;
-    constexpr int NS = EXT_STAGES;
-    constexpr int NM = PY + 4 * HM;                // samples per thread
-    constexpr int VW = (PY % 4 == 0) ? 4 : 2;
-    constexpr int NMV = (NM + VW - 1) / VW * VW;
-    const int Z = a.z_lo + blockIdx.y;
-    const int y0 = a.x_lo + blockIdx.x * TXS;
-    const int t = threadIdx.x;
-    const int yb = y0 + PY * t;
-    const long long rowoff = (long long)Z * a.NXP;
-    const int wal = y0 - 2 * HM;                   // multiple of 4 by the launcher's choice of x_lo
-
-    float Wr[PY][NH];
-#pragma unroll
-    for (int j = 0; j < PY; ++j) {
-        const int y = yb + j;
-#pragma unroll
-        for (int ih = 0; ih < NH; ++ih) {
-            const int xs = y - SIGMA * (ih - HM);
-            Wr[j][ih] = (y < a.x_hi && xs >= 0 && xs < a.NXP) ? __ldg(a.W + ih * a.P + rowoff + xs) : 0.f;
-        }
-    }
-    RingIt itin, itout;
-    itin.init(a.in, a.n0, a.S, a.P, rowoff);
-    itout.init(a.outr, a.n0, a.S, a.P, rowoff + yb);
-    int stage_in = 0, stage_c = 0;
-    auto issue = [&](int p) {
-        if (p < a.npair) {
-            copy_window(sm + stage_in * STG, itin.ptr(), wal, NCH, a.NXP);
-            itin.next();
-        }
-        stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
-        cpa_commit();
-    };
-    auto compute = [&](const float *stg, float *o) {
-        float dv[NMV];                   // dv[k] = D(yb - 2 HM + k): stage index PY t + k
-        lds_vec<VW>(dv, stg + PY * t);
-        float acc[PY];
-#pragma unroll
-        for (int j = 0; j < PY; ++j) acc[j] = 0.f;
-#pragma unroll
-        for (int ih = 0; ih < NH; ++ih)      // offsets outer: the PY sums are independent chains
-#pragma unroll
-            for (int j = 0; j < PY; ++j)     // D(y_j - 2 SIGMA h) = dv[j - 2 SIGMA (ih - HM) + 2 HM]
-                acc[j] = fmaf(Wr[j][ih], dv[j - 2 * SIGMA * (ih - HM) + 2 * HM], acc[j]);
-#pragma unroll
-        for (int j = 0; j < PY; j += 2) {
-            if (yb + j + 1 < a.x_hi) {
-                float2 v = make_float2(acc[j], acc[j + 1]);
-                if (a.accumulate) {
-                    const float2 old = *reinterpret_cast<const float2 *>(o + j);
-                    v.x += old.x; v.y += old.y;
-                }
-                *reinterpret_cast<float2 *>(o + j) = v;
-            } else if (yb + j < a.x_hi) {
-                o[j] = a.accumulate ? o[j] + acc[j] : acc[j];
-            }
-        }
-    };
-    // two pairs per barrier.  The prologue fills NS - 2 stages; iteration p waits for pairs p and
-    // p+1 (at most NS - 4 younger groups pending), then refills the stages of pairs p-2 and p-1,
-    // which every thread finished in the previous iteration (the barrier orders it).
-#pragma unroll
-    for (int q = 0; q < NS - 2; ++q) issue(q);
-    for (int p = 0; p < a.npair; p += 2) {
-        cpa_wait<NS - 4>();
-        __syncthreads();
-        issue(p + NS - 2);
-        issue(p + NS - 1);
-        const float *st0 = sm + stage_c * STG;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
-        const float *st1 = sm + stage_c * STG;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
-        float *o0 = const_cast<float *>(itout.ptr());
-        itout.next();
-        compute(st0, o0);
-        if (p + 1 < a.npair) {
-            float *o1 = const_cast<float *>(itout.ptr());
-            itout.next();
-            compute(st1, o1);
-        }
-    }
-    cpa_wait<0>();
-}
-
-#endif  // FWIME_EXT_RB
 
 // Generic-nh fallback (weights re-read per pair): any odd nh up to MAX_NH.
 __global__ void __launch_bounds__(EXT_TX) k_scatter_gen(const ExtArgs a)
@@ -509,27 +387,6 @@ __global__ void __launch_bounds__(EXT_TX) k_scatter_gen(const ExtArgs a)
     }
 }
 
-#if FWIME_EXT_RB
-template <int NH, int PY>
-static void launch_scatter_nh(ExtArgs a, cudaStream_t st)
-{
-    constexpr int HM = (NH - 1) / 2;
-    constexpr int TXS = EXT_TX * PY;
-    constexpr int STG = 4 * ((TXS + 4 * HM + 3) / 4) + 4;
-    const size_t smem = EXT_STAGES * STG * sizeof(float);
-    a.x_lo -= (((a.x_lo - 2 * HM) % 4) + 4) % 4;   // window start on a 16-byte boundary
-    dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
-    static bool attr = false;      // once per instantiation, before any launch (and any capture)
-    if (!attr) {
-        cudaFuncSetAttribute(k_scatter_rb<NH, PY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_scatter_rb<NH, PY, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    if (a.sigma > 0) k_scatter_rb<NH, PY, 1><<<grid, EXT_TX, smem, st>>>(a);
-    else k_scatter_rb<NH, PY, -1><<<grid, EXT_TX, smem, st>>>(a);
-}
-#define FWIME_SCATTER(NH, PY, A) launch_scatter_nh<NH, PY>(a, st)
-#else
 template <int NH, int A>
 static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
 {
@@ -547,20 +404,18 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
     if (a.sigma > 0) k_scatter_ps<NH, A, 1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
     else k_scatter_ps<NH, A, -1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
 }
-#define FWIME_SCATTER(NH, PY, A) launch_scatter_ps<NH, A>(a, st)
-#endif
 
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     switch (a.nh) {
-    case 1: FWIME_SCATTER(1, 8, 4); break;
-    case 3: FWIME_SCATTER(3, 8, 4); break;
-    case 5: FWIME_SCATTER(5, 8, 4); break;
-    case 11: FWIME_SCATTER(11, 8, 4); break;
-    case 21: FWIME_SCATTER(21, 4, FWIME_SC_A21); break;
-    case 31: FWIME_SCATTER(31, 2, 4); break;
-    case 41: FWIME_SCATTER(41, 2, 2); break;
+    case 1: launch_scatter_ps<1, 4>(a, st); break;
+    case 3: launch_scatter_ps<3, 4>(a, st); break;
+    case 5: launch_scatter_ps<5, 4>(a, st); break;
+    case 11: launch_scatter_ps<11, 4>(a, st); break;
+    case 21: launch_scatter_ps<21, FWIME_SC_A21>(a, st); break;
+    case 31: launch_scatter_ps<31, 4>(a, st); break;
+    case 41: launch_scatter_ps<41, 2>(a, st); break;
     default: {
         dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
         const int hm = (a.nh - 1) / 2;
@@ -569,7 +424,6 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
     }
     return cudaGetLastError();
 }
-#undef FWIME_SCATTER
 
 // ------------------------------------------------------------------ imaging
 
@@ -898,109 +752,6 @@ __global__ void __launch_bounds__(ImgShape<NH>::TX, FWIME_IMG_MINB) k_image_ps(c
     if constexpr (ImgShape<NH>::NT > 4) if (warp == 4) img_task_run<NH, 4 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
 }
 
-#if FWIME_EXT_RB
-// Register-blocked imaging: a thread owns PX consecutive points x_i = xb + i and, for
-// IMG_EXT, their PX x NH image accumulators (IMG_CONTRACT: PX x NH weights p~ and PX
-// accumulators) for the whole segment.  D(x_i - h) and L(x_i + h) come from PX + NH - 1
-// window samples each, so a shared-memory load serves up to PX multiply-adds.
-template <int NH, int PX, int MODE>
-__global__ void __launch_bounds__(EXT_TX) k_image_rb(const ImgArgs a)
-{
-    extern __shared__ float4 sm4[];
-    float *sm = reinterpret_cast<float *>(sm4);
-    constexpr int HM = (NH - 1) / 2;
-    constexpr int TXS = EXT_TX * PX;
-    constexpr int SPAN = TXS + 2 * HM;
-    constexpr int NCH = (SPAN + 3) / 4;
-    constexpr int WIN = 4 * NCH + 4;
-    constexpr int STG = 2 * WIN;                   // D window, then L window
-    constexpr int NS = EXT_STAGES;
-    constexpr int NW = PX + NH - 1;
-    constexpr int VW = (PX % 4 == 0) ? 4 : 2;
-    constexpr int NWV = (NW + VW - 1) / VW * VW;
-    const int Z = a.z_lo + blockIdx.y;
-    const int x0 = a.x_lo + blockIdx.x * TXS;
-    const int t = threadIdx.x;
-    const int xb = x0 + PX * t;
-    const int wal = x0 - HM;                       // multiple of 4 by the launcher's choice of x_lo
-    const long long rowoff = (long long)Z * a.NXP;
-
-    constexpr int NA = MODE == IMG_EXT ? PX * NH : PX;
-    float acc[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
-    float ptr[MODE == IMG_CONTRACT ? PX * NH : 1];
-    if (MODE == IMG_CONTRACT) {
-#pragma unroll
-        for (int i = 0; i < PX; ++i)
-#pragma unroll
-            for (int ih = 0; ih < NH; ++ih)
-                ptr[i * NH + ih] = (xb + i < a.x_hi) ? __ldg(a.pt + ih * a.P + rowoff + xb + i) : 0.f;
-    }
-    RingIt itd, itl;
-    itd.init(a.D, a.n0, a.S, a.P, rowoff);
-    itl.init(a.L, a.n0, a.S, a.P, rowoff);
-    int stage_in = 0, stage_c = 0;
-    auto issue = [&](int p) {
-        if (p < a.npair) {
-            float *st = sm + stage_in * STG;
-            copy_window(st, itd.ptr(), wal, NCH, a.NXP);
-            copy_window(st + WIN, itl.ptr(), wal, NCH, a.NXP);
-            itd.next();
-            itl.next();
-        }
-        stage_in = stage_in + 1 == NS ? 0 : stage_in + 1;
-        cpa_commit();
-    };
-    auto compute = [&](const float *stg) {
-        // dv[k] = D(xb - HM + k), lv[k] = L(xb - HM + k): stage index PX t + k (conflict-free vector loads)
-        const float *bd = stg + PX * t;
-        float dv[NWV], lv[NWV];
-        lds_vec<VW>(dv, bd);
-        lds_vec<VW>(lv, bd + WIN);
-#pragma unroll
-        for (int i = 0; i < PX; ++i) {
-            if (MODE == IMG_EXT) {
-#pragma unroll
-                for (int ih = 0; ih < NH; ++ih)   // D(x_i - h) = dv[i - ih + 2 HM], L(x_i + h) = lv[i + ih]
-                    acc[i * NH + ih] = fmaf(dv[i - ih + 2 * HM], lv[i + ih], acc[i * NH + ih]);
-            } else {
-                float s = 0.f;
-#pragma unroll
-                for (int ih = 0; ih < NH; ++ih) s = fmaf(ptr[i * NH + ih] * dv[i - ih + 2 * HM], lv[i + ih], s);
-                acc[MODE == IMG_EXT ? 0 : i] += s;
-            }
-        }
-    };
-    // two pairs per barrier (same stage accounting as the scatter kernel)
-#pragma unroll
-    for (int q = 0; q < NS - 2; ++q) issue(q);
-    for (int p = 0; p < a.npair; p += 2) {
-        cpa_wait<NS - 4>();
-        __syncthreads();
-        issue(p + NS - 2);
-        issue(p + NS - 1);
-        const float *st0 = sm + stage_c * STG;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
-        const float *st1 = sm + stage_c * STG;
-        stage_c = stage_c + 1 == NS ? 0 : stage_c + 1;
-        compute(st0);
-        if (p + 1 < a.npair) compute(st1);
-    }
-    cpa_wait<0>();
-#pragma unroll
-    for (int i = 0; i < PX; ++i) {
-        if (xb + i >= a.x_hi) continue;
-        if (MODE == IMG_EXT) {
-#pragma unroll
-            for (int ih = 0; ih < NH; ++ih) a.img[ih * a.P + rowoff + xb + i] += acc[i * NH + ih];
-        } else {
-            a.img[rowoff + xb + i] += acc[MODE == IMG_EXT ? 0 : i];
-        }
-    }
-}
-
-#endif  // FWIME_EXT_RB
 
 // Generic-nh fallback: one point per thread, accumulators in shared memory.
 template <int MODE>
@@ -1108,40 +859,6 @@ static cudaError_t launch_image_gen(const ImgArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-#if FWIME_EXT_RB
-template <int NH, int PX, int MODE>
-static void launch_image_rb(ImgArgs a, cudaStream_t st)
-{
-    constexpr int HM = (NH - 1) / 2;
-    constexpr int TXS = EXT_TX * PX;
-    constexpr int STG = 2 * (4 * ((TXS + 2 * HM + 3) / 4) + 4);
-    const size_t smem = EXT_STAGES * STG * sizeof(float);
-    a.x_lo -= (((a.x_lo - HM) % 4) + 4) % 4;   // windows start on a 16-byte boundary
-    dim3 grid((a.x_hi - a.x_lo + TXS - 1) / TXS, a.z_hi - a.z_lo);
-    static bool attr = false;      // once per instantiation, before any launch (and any capture)
-    if (!attr) {
-        cudaFuncSetAttribute(k_image_rb<NH, PX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    k_image_rb<NH, PX, MODE><<<grid, EXT_TX, smem, st>>>(a);
-}
-
-template <int MODE>
-static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
-{
-    switch (a.nh) {
-    case 1: launch_image_rb<1, 8, MODE>(a, st); break;
-    case 3: launch_image_rb<3, 8, MODE>(a, st); break;
-    case 5: launch_image_rb<5, 8, MODE>(a, st); break;
-    case 11: launch_image_rb<11, 8, MODE>(a, st); break;
-    case 21: launch_image_rb<21, 4, MODE>(a, st); break;
-    case 31: launch_image_rb<31, 2, MODE>(a, st); break;
-    case 41: launch_image_rb<41, 2, MODE>(a, st); break;
-    default: return launch_image_gen<MODE>(a, st);
-    }
-    return cudaGetLastError();
-}
-#else
 template <int NH>
 static void launch_image_ps(const ImgArgs &a, cudaStream_t st)
 {
@@ -1173,7 +890,6 @@ static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
     }
     return cudaGetLastError();
 }
-#endif
 
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st)
 {

@@ -61,7 +61,7 @@ def test_workspace_bytes_grows_with_shots_and_operator():
     f3 = fw.workspace_bytes(g, gm, fw.OP_FORWARD, 3)
     assert f3 > f1
     NZ, NXP = 20 + 2 * 10, 64
-    assert f3 - f1 == 2 * 4 * NZ * NXP * 4          # four wavefields per extra shot (two-step stencil: 2 in, 2 out)
+    assert f3 - f1 == 2 * 2 * NZ * NXP * 4          # two wavefields (q^n, q^n-1) per extra shot
     assert fw.workspace_bytes(g, gm, fw.OP_GRADIENT, 1) > fw.workspace_bytes(g, gm, fw.OP_BORN_EXT_ADJ, 1)
     # checkpoint count follows the segment length
     a = fw.workspace_bytes(g, gm, fw.OP_BORN_EXT_ADJ, 1, 7)

@@ -74,17 +74,18 @@ def test_marmousi2_full_grid_sampled_shots_against_oracle(marm):
     geom = fw.Geometry(wl.src_iz[idx], wl.src_ix[idx], wl.rec_iz, wl.rec_ix)
     w = np.stack([wl.w[:nt]] * 2).astype(np.float32)
     pt = rng.standard_normal((wl.nh, wl.nz, wl.nx)).astype(np.float32)
+    og = oracle.Grid(nz=wl.nz, nx=wl.nx, W=wl.W, nt=nt, dt=wl.dt, dx=wl.dx, nh=wl.nh)
+    ogeo = oracle.Geometry(wl.src_iz[idx], wl.src_ix[idx], wl.rec_iz, wl.rec_ix)
+    d_ref = oracle.born_ext(og, wl.v.astype(np.float64), ogeo, w.astype(np.float64), pt.astype(np.float64))
+    d_in = d_ref.astype(np.float32)            # the adjoint's input: the oracle's traces, as both sides see them
     d = torch.zeros((2, nt, wl.nrec), device="cuda")
     img = torch.zeros((wl.nh, wl.nz, wl.nx), device="cuda")
     with fw.Context(grid, geom) as ctx:
         ctx.born_ext(cu(wl.v), cu(w), cu(pt), d)
-        ctx.born_ext_adj(cu(wl.v), cu(w), d, img)
-    og = oracle.Grid(nz=wl.nz, nx=wl.nx, W=wl.W, nt=nt, dt=wl.dt, dx=wl.dx, nh=wl.nh)
-    ogeo = oracle.Geometry(wl.src_iz[idx], wl.src_ix[idx], wl.rec_iz, wl.rec_ix)
+        ctx.born_ext_adj(cu(wl.v), cu(w), cu(d_in), img)
     dg = d.double().cpu().numpy()
-    d_ref = oracle.born_ext(og, wl.v.astype(np.float64), ogeo, w.astype(np.float64), pt.astype(np.float64))
     assert np.linalg.norm(dg - d_ref) / np.linalg.norm(d_ref) <= 1e-4
-    i_ref = oracle.born_ext_adj(og, wl.v.astype(np.float64), ogeo, w.astype(np.float64), dg)
+    i_ref = oracle.born_ext_adj(og, wl.v.astype(np.float64), ogeo, w.astype(np.float64), d_in.astype(np.float64))
     ig = img.double().cpu().numpy()
     assert np.linalg.norm(ig - i_ref) / np.linalg.norm(i_ref) <= 1e-4
 

@@ -385,6 +385,30 @@ def test_dso_penalty_closed_form():
     assert rel(oracle.dso_penalty(g, pt, 0.5), 0.5 * 0.25 * 27 * g.nz * g.nx) < 1e-14
 
 
+@pytest.mark.parametrize("nh", [1, 5, 21, 41])
+def test_dso_operator_properties(nh):
+    """The paper asks only that D be an invertible, modified DSO operator (Theory, Eq. 1): a penalty
+    that vanishes nowhere, treats +h and -h alike and grows away from zero offset.  Probe the oracle's
+    C arithmetic one offset plane at a time (a unit spike on plane ih gives 1/2 D(ih)^2 at eps = 1):
+    D > 0, symmetric in h, smallest at h = 0 and strictly increasing in |h| -- a shifted centre, a
+    zero weight or a sign slip fails one of these."""
+    g = small_grid(nh=nh)
+    hm = (nh - 1) // 2
+    d = []
+    for ih in range(nh):
+        pt = np.zeros((g.nh, g.nz, g.nx))
+        pt[ih, g.nz // 2, g.nx // 3] = 1.0
+        d.append(np.sqrt(2.0 * oracle.dso_penalty(g, pt, 1.0)))
+    d = np.array(d)
+    assert np.all(d > 0.0)
+    assert np.array_equal(d, d[::-1])
+    assert np.argmin(d) == hm and np.sum(d == d.min()) == 1
+    assert np.all(np.diff(d[hm:]) > 0.0)
+    # linear in p~ planes: the penalty of a sum over planes is the sum of the planes' penalties
+    pt = np.ones((g.nh, g.nz, g.nx))
+    assert rel(oracle.dso_penalty(g, pt, 1.0), 0.5 * float(np.sum(d ** 2)) * g.nz * g.nx) < 1e-12
+
+
 # ------------------------------------------------------------- cost table
 
 def test_cost_table_matches_paper():

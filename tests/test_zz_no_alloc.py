@@ -4,13 +4,17 @@ It exists for callers that cannot allocate device memory (running inside another
 allocator or memory pool, or on a thread that must not enter the driver's
 allocator): it needs no context and takes its scratch from a static device
 array.  Called through the C ABI twice in a row (two different models), its
-output must match fwime_forward's within the parity tolerance; a problem larger
-than the static array must be refused with FWIME_ENOMEM and a message."""
+output must match fwime_forward's within the parity tolerance and the FP64
+oracle's f(m) within the same tolerance; a problem larger than the static array
+must be refused with FWIME_ENOMEM and a message; a velocity that breaks the
+stability bound or is not positive must be refused with FWIME_ECFL (output
+untouched) and the next valid call must still be right."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -64,6 +68,10 @@ def test_forward_static_matches_forward_on_two_calls_in_a_row():
         a, b = out.double().cpu().numpy(), ref.double().cpu().numpy()
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL
         assert np.all(a[:, 0, :] == 0.0)
+        og = oracle.Grid(nz=grid.nz, nx=grid.nx, W=grid.sponge, nt=grid.nt, dt=grid.dt, dx=grid.dx)
+        ogeo = oracle.Geometry(geom.src_iz, geom.src_ix, geom.rec_iz, geom.rec_ix)
+        d_ref = oracle.forward(og, v.astype(np.float64), ogeo, w.astype(np.float64))
+        assert np.linalg.norm(a - d_ref) / np.linalg.norm(d_ref) <= TOL
 
 
 def test_forward_static_refuses_problems_beyond_its_scratch():
@@ -81,3 +89,41 @@ def test_forward_static_refuses_problems_beyond_its_scratch():
     buf = ctypes.create_string_buffer(256)
     lib.fwime_static_last_error(buf, 256)
     assert b"scratch" in buf.value
+
+
+def _static_call(lib, grid, geom, vd, wd, out):
+    gc = grid.c()
+    gm, keep = geom.c()
+    rc = lib.fwime_forward_static(ctypes.byref(gc), ctypes.byref(gm), vd.data_ptr(), wd.data_ptr(), out.data_ptr(),
+                                  None)
+    torch.cuda.synchronize()
+    return rc
+
+
+@pytest.mark.parametrize("bad", ["cfl", "negative", "zero"])
+def test_forward_static_refuses_unstable_or_non_positive_velocity(bad):
+    lib = _lib()
+    grid, geom, v, w = _case(0)
+    vbad = v.copy()
+    if bad == "cfl":
+        # dt v sqrt(6.5016 (2 / dx^2)) >= 2 above v = 5547 m/s at dt = 1 ms, dx = 10 m
+        vbad[20, 70] = 5600.0
+    elif bad == "negative":
+        vbad[5, 5] = -1800.0
+    else:
+        vbad[30, 140] = 0.0
+    out = torch.full((geom.nshot, grid.nt, geom.nrec), 7.0, device="cuda")
+    rc = _static_call(lib, grid, geom, torch.from_numpy(vbad).cuda(), torch.from_numpy(w).cuda(), out)
+    assert rc == fw.FWIME_ECFL
+    buf = ctypes.create_string_buffer(256)
+    lib.fwime_static_last_error(buf, 256)
+    assert b"CFL" in buf.value
+    assert torch.all(out == 7.0)                     # no time step ran, the output is untouched
+    # the next call with a valid model is unaffected by the refused one
+    ref = torch.zeros_like(out)
+    vd, wd = torch.from_numpy(v).cuda(), torch.from_numpy(w).cuda()
+    with fw.Context(grid, geom) as ctx:
+        ctx.forward(vd, wd, ref)
+    assert _static_call(lib, grid, geom, vd, wd, out) == fw.FWIME_OK
+    a, b = out.double().cpu().numpy(), ref.double().cpu().numpy()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL
