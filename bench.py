@@ -370,7 +370,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2206_02362_gb300 as fw
-    from paper_2206_02362_gb300.shard import allreduce_model
+    from paper_2206_02362_gb300.shard import rank_step
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,14 +399,18 @@ def main():
 
     reused = [0]
 
-    def step(c, vv, ww, pp, dd, ii):
-        c.born_ext(vv, ww, pp, dd, sync=False)
-        n = c.launches
-        c.born_ext_adj(vv, ww, dd, ii, sync=False)
-        reused[0] = c.get_option("background_reused")
-        launches[0] += n + c.launches
-        if world > 1:
-            allreduce_model(ii)        # images summed over the shots of all ranks
+    def step(c, vv, ww, pp, dd, ii, ranks=world):
+        # weak scaling: wl.nshot shots per rank; shard.rank_step hands this rank its block of the
+        # ranks x wl.nshot shots (the context's own shots) and sums the images over all ranks
+        def apply(a, b):
+            assert b - a == c.geom.nshot
+            c.born_ext(vv, ww, pp, dd, sync=False)
+            n = c.launches
+            c.born_ext_adj(vv, ww, dd, ii, sync=False)
+            reused[0] = c.get_option("background_reused")
+            launches[0] += n + c.launches
+            return ii
+        rank_step(apply, c.geom.nshot * ranks, ranks, rank if ranks > 1 else 0)
 
     for _ in range(args.warmup):
         step(ctx, v, w, pt, d, img)
@@ -497,11 +501,11 @@ def main():
         geom2 = fw.Geometry(wl.src_iz[:nps], wl.src_ix[:nps], wl.rec_iz, wl.rec_ix)
         with fw.Context(grid, geom2, plain=1, reuse_background=reuse) as cp:
             d2 = torch.zeros((nps, wl.nt, wl.nrec), device=dev)
-            step(cp, v, w[:nps].contiguous(), pt, d2, img)
+            step(cp, v, w[:nps].contiguous(), pt, d2, img, ranks=1)
             cp.sync()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            step(cp, v, w[:nps].contiguous(), pt, d2, img)
+            step(cp, v, w[:nps].contiguous(), pt, d2, img, ranks=1)
             cp.sync()
             tp = time.perf_counter() - t0
         line["plain"] = {"shots_per_s": nps / tp, "sample": f"{nps} shots, one shot per launch, no graph"}

@@ -49,6 +49,7 @@
 #define FWIME_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -97,7 +98,9 @@ enum {
                                        checkpointing sweep (one propagation fewer).  The caller guarantees
                                        that v and w are not modified in between; any other operator call
                                        drops the states.  0 (default) frees them. */
-    FWIME_OPT_BACKGROUND_REUSED = 11, /* read-only: 1 if the last call started from those states */
+    FWIME_OPT_BACKGROUND_REUSED = 11, /* read-only: 1 if the last call started from states an earlier call
+                                         kept (the background states above, or the state of
+                                         fwime_gradient_forward) */
     FWIME_OPT_TIME_LAG = 12,        /* 0 (default): B~ / B~* extend with nh horizontal subsurface offsets;
                                        L > 0: with nh time lags tau_i = (i - (nh-1)/2) L dt, the symmetric
                                        convention (source side at t - tau, receiver side at t + tau):
@@ -183,6 +186,25 @@ int fwime_gradient(fwime_ctx *ctx, const float *v, const float *w, const float *
 int fwime_objective(fwime_ctx *ctx, const float *v, const float *w, const float *pt,
                     const float *dobs, float eps, double *objective);
 
+/* The FWIME gradient of fwime_gradient in two calls, for reverse-mode differentiation (Eqs. 1, 7-9):
+ *
+ * fwime_gradient_forward runs the forward sweep only -- f + B~ p~, the residual r = f + B~ p~ - d_obs and
+ * Phi (*objective, host double, written at the next fwime_sync) -- and keeps what the adjoint sweep needs in
+ * the context: the background and scattered wavefields' states at every segment start for every shot
+ * (4 nseg nshot padded fields) and r (nshot nt nrec floats).  No adjoint kernel runs.  When that state does
+ * not fit in device memory next to the adjoint sweep's workspace (or with FWIME_OPT_TIME_LAG or the plain
+ * path), only Phi is computed and nothing is kept.
+ *
+ * fwime_gradient_backward runs the adjoint sweep -- B* r + T* r into grad[nz][nx] (=, or += when
+ * accumulate) -- from that state when it was kept for the same v, w and pt pointers (the caller guarantees
+ * that their contents did not change in between), and releases it; otherwise it runs the whole gradient
+ * (the forward sweep again, then the adjoint sweep), which needs dobs and eps.  FWIME_OPT_BACKGROUND_REUSED
+ * reads 1 after a backward call that started from the kept state.  Device pointers only. */
+int fwime_gradient_forward(fwime_ctx *ctx, const float *v, const float *w, const float *pt, const float *dobs,
+                           float eps, double *objective);
+int fwime_gradient_backward(fwime_ctx *ctx, const float *v, const float *w, const float *pt, const float *dobs,
+                            float eps, float *grad, int accumulate);
+
 /* Variable projection step (Theory section, Eqs. 2-5): approximately minimises
  *   Phi_eps,m(p~) = 1/2 ||B~(m) p~ - dres||^2 + eps^2/2 ||D p~||^2
  * with `niter` iterations of linear conjugate gradients on the normal
@@ -206,6 +228,16 @@ int fwime_vp_solve(fwime_ctx *ctx, const float *v, const float *w, const float *
 int fwime_spline(fwime_ctx *ctx, int nzs, const float *zs, int nxs, const float *xs, const float *in, float *out,
                  int adjoint, int accumulate);
 
+/* Model-space multiscale step (Theory section, the model-space multi-scale workflow after Eq. 9: the model
+ * inverted on one spline grid is the starting model on a finer one; the Marmousi2 example halves the spline
+ * spacing whenever the step-length search fails).  mf[nzf][nxf] = the linear spline of mc[nzc][nxc] on the
+ * coarse nodes zc x xc (the S of fwime_spline) evaluated at the fine nodes zf x xf.  When every coarse node
+ * is also a fine node, S on the fine nodes applied to mf equals S on the coarse nodes applied to mc.  Node
+ * arrays are host memory (metres, strictly increasing, finite; else FWIME_EINVAL); mc and mf are device
+ * pointers.  Asynchronous on the context's stream. */
+int fwime_spline_refine(fwime_ctx *ctx, int nzc, const float *zc, int nxc, const float *xc, const float *mc, int nzf,
+                        const float *zf, int nxf, const float *xf, float *mf);
+
 /* f(m) for a group of contexts at once (Eq. 1; the Computational-aspects
  * section's shots are independent): ctxs[i] has its own grid, record length
  * and shots, with model v[i], wavelets w[i] and output d[i] (device pointers,
@@ -223,6 +255,70 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
  * CUDA events and keeps the fastest (FWIME_OPT_ZCHUNK).  Synchronous.  Returns
  * the chosen chunking and its time per launch (either pointer may be NULL). */
 int fwime_autotune(fwime_ctx *ctx, int op, int *zchunk, float *us_per_launch);
+
+/* ---- Request server (continuous batching; Computational aspects: shots are independent modelling
+ * tasks that a host layer dispatches to the GPU) ----
+ *
+ * A server is a context created by fwime_server_create; it takes requests, not operator calls.  Each
+ * request is one forward-modelling job f(m) (Eq. 1) or one FWIME-gradient job (Phi and B* r + T* r at a
+ * fixed p~, Eqs. 1, 7-9) with its own grid, geometry, record length and nh.  fwime_submit copies the
+ * request's grid and geometry, checks it and queues it; it returns at once with a ticket.  A dispatcher
+ * thread admits queued requests in submission order as soon as the request's device memory
+ * (fwime_request_bytes: the operator's workspace with all its shots in one batch, as fwime_workspace_bytes
+ * plans it, plus staging when host_io = 1) fits under memory_budget and fewer than max_active requests are
+ * in flight -- while earlier requests are still running.  Each admitted request runs on a context and a
+ * CUDA stream of its own, so admitted requests overlap on the GPU; forward requests admitted together
+ * share one launch per time step (as fwime_forward_group).  Completion is detected with CUDA events; the
+ * request's memory then returns to the budget.  fwime_poll (non-blocking) and fwime_wait (blocking)
+ * collect a finished request's result once; the ticket is then forgotten.
+ *
+ * Buffers: with host_io = 0 every pointer is a DEVICE pointer; with host_io = 1 they are host pointers
+ * (pinned memory recommended) that the server stages through device memory counted in the admission.
+ * Either way they are the caller's and must stay valid and unchanged until the request is collected.
+ * Layouts as for fwime_forward (v, w, d) and fwime_gradient (pt, dobs, grad).
+ *
+ * Errors: fwime_submit returns FWIME_EINVAL for a bad request (unknown kind, grid, geometry, missing
+ * buffer) and FWIME_ENOMEM when the request alone needs more than the budget (it could never be
+ * admitted); a message is then available from fwime_server_last_error (per calling thread).  A request
+ * that fails on the GPU side is collected with its error code in fwime_result.status.  fwime_sync on a
+ * server context waits until every submitted request has finished; fwime_destroy waits for them too,
+ * then stops the server's threads. */
+enum { FWIME_REQ_FORWARD = 0, FWIME_REQ_GRADIENT = 1 };
+#define FWIME_SERVE_PLAIN 1   /* fwime_server_create option: one request at a time, one shot per launch,
+                                 host-driven steps (the comparison path) */
+
+typedef struct {
+    int kind;                      /* FWIME_REQ_FORWARD or FWIME_REQ_GRADIENT */
+    fwime_grid grid;
+    fwime_geom geom;               /* host arrays, copied by fwime_submit */
+    int host_io;                   /* 1: the buffers below are host memory */
+    const float *v, *w;            /* v[nz][nx], w[nshot][nt] */
+    const float *pt, *dobs;        /* gradient: p~[nh][nz][nx], d_obs[nshot][nt][nrec] */
+    float *d;                      /* forward output d[nshot][nt][nrec] */
+    float *grad;                   /* gradient output grad[nz][nx] */
+    float eps;                     /* gradient: DSO weight of Phi */
+} fwime_request;
+
+typedef struct {
+    int done;                      /* 1: finished, outputs written (result collected) */
+    int status;                    /* FWIME_OK or the request's error code */
+    double objective;              /* gradient requests: Phi */
+    double queued_s;               /* submission to admission, seconds */
+    double latency_s;              /* submission to completion seen by the server, seconds */
+} fwime_result;
+
+/* memory_budget: device bytes the admitted requests may hold together (0 = 80 % of the free memory now);
+ * max_active: requests in flight at most (1..1024); options: 0 or FWIME_SERVE_PLAIN. */
+int fwime_server_create(fwime_ctx **out, size_t memory_budget, int max_active, int options);
+/* Device bytes the server admits a request with (workspace + staging). */
+int fwime_request_bytes(const fwime_request *req, size_t *bytes);
+int fwime_submit(fwime_ctx *server, const fwime_request *req, uint64_t *ticket);
+/* Non-blocking: res->done = 0 while the request runs; on 1 the result is collected and the ticket freed.
+ * FWIME_EINVAL for an unknown (or already collected) ticket. */
+int fwime_poll(fwime_ctx *server, uint64_t ticket, fwime_result *res);
+/* Blocks until the request has finished, then collects it as fwime_poll does. */
+int fwime_wait(fwime_ctx *server, uint64_t ticket, fwime_result *res);
+int fwime_server_last_error(char *buf, size_t n);
 
 /* Waits for the context's stream and returns the latched device status
  * (FWIME_OK, FWIME_ECFL, FWIME_ETIMEOUT) or FWIME_ECUDA; clears the latch. */

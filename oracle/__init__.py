@@ -12,6 +12,7 @@ Operators (Barnier et al., Theory section): ``forward`` = f(m) (Eq. 1),
 ``gradient`` = (Phi at fixed p~, B* r + T* r) (Eqs. 1, 7-9), ``vp_solve`` =
 linear conjugate gradients for the variable projection step (Eqs. 2-5),
 ``spline``/``spline_adj`` = the linear spline re-parametrisation S, S* (Eq. 1),
+``spline_refine`` = the model-space multiscale step (coarse to fine spline nodes),
 ``cost_fwime`` = Eq. 11.  Primitives (``lap``, ``step``, ``step_T``, ``prop``, ``prop_T``,
 ``d2t``, ``d2t_T``, ``scatter``, ``scatter_TD``, ``scatter_TW``) are exposed
 for dot-product pins.
@@ -380,3 +381,13 @@ def spline_adj(zs, xs, nz, nx, dz, dx, g):
     Az = spline_matrix(zs, np.arange(nz) * dz)
     Ax = spline_matrix(xs, np.arange(nx) * dx)
     return Az.T @ np.asarray(g, dtype=np.float64) @ Ax
+
+
+def spline_refine(zc, xc, mc, zf, xf):
+    """Model-space multiscale step (Theory section, the model-space multi-scale workflow after Eq. 9; the
+    Marmousi2 section halves the spline spacing when the step-length search fails): the model mc on the
+    coarse nodes zc x xc carried over to the fine nodes zf x xf as the coarse linear spline evaluated at
+    the fine nodes, Az(zf) mc Ax(xf)^T with the hat-function matrices of `spline_matrix`."""
+    Az = spline_matrix(zc, np.asarray(zf, dtype=np.float64))
+    Ax = spline_matrix(xc, np.asarray(xf, dtype=np.float64))
+    return Az @ np.asarray(mc, dtype=np.float64) @ Ax.T

@@ -38,9 +38,14 @@ KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 
 ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "fwime_get_option",
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
-                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_objective", "fwime_vp_solve", "fwime_spline",
+                 "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_gradient_forward", "fwime_gradient_backward",
+                 "fwime_objective", "fwime_vp_solve", "fwime_spline", "fwime_spline_refine",
                  "fwime_autotune", "fwime_forward_group", "fwime_sync", "fwime_profile_read",
-                 "fwime_last_error_detail", "fwime_strerror", "fwime_destroy")
+                 "fwime_last_error_detail", "fwime_strerror", "fwime_destroy",
+                 "fwime_server_create", "fwime_request_bytes", "fwime_submit", "fwime_poll", "fwime_wait",
+                 "fwime_server_last_error")
+REQ_FORWARD, REQ_GRADIENT = 0, 1
+SERVE_PLAIN = 1
 
 
 class FwimeError(RuntimeError):
@@ -61,6 +66,17 @@ class GeomC(ctypes.Structure):
     _fields_ = [("nshot", ctypes.c_int), ("src_iz", ctypes.POINTER(ctypes.c_int)),
                 ("src_ix", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
                 ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int))]
+
+
+class RequestC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("grid", GridC), ("geom", GeomC), ("host_io", ctypes.c_int),
+                ("v", ctypes.c_void_p), ("w", ctypes.c_void_p), ("pt", ctypes.c_void_p), ("dobs", ctypes.c_void_p),
+                ("d", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("eps", ctypes.c_float)]
+
+
+class ResultC(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("objective", ctypes.c_double),
+                ("queued_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -93,9 +109,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_tomo_adj.argtypes = [vp, fp, fp, fp, fp, fp, ip]
     lib.fwime_gradient.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_objective.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_gradient_forward.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.fwime_gradient_backward.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, fp, ip]
     lib.fwime_vp_solve.argtypes = [vp, fp, fp, fp, ctypes.c_float, ip, fp, ctypes.POINTER(ctypes.c_double)]
     lib.fwime_spline.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float), ip, ctypes.POINTER(ctypes.c_float), fp, fp,
                                  ip, ip]
+    fl = ctypes.POINTER(ctypes.c_float)
+    lib.fwime_spline_refine.argtypes = [vp, ip, fl, ip, fl, fp, ip, fl, ip, fl, fp]
     lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.fwime_forward_group.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
@@ -107,6 +127,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fwime_strerror.restype = ctypes.c_char_p
     lib.fwime_destroy.argtypes = [vp]
     lib.fwime_destroy.restype = None
+    lib.fwime_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ip, ip]
+    lib.fwime_request_bytes.argtypes = [ctypes.POINTER(RequestC), ctypes.POINTER(ctypes.c_size_t)]
+    lib.fwime_submit.argtypes = [vp, ctypes.POINTER(RequestC), ctypes.POINTER(ctypes.c_uint64)]
+    lib.fwime_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ResultC)]
+    lib.fwime_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ResultC)]
+    lib.fwime_server_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in ABI_FUNCTIONS:
         if name not in ("fwime_strerror", "fwime_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -313,6 +339,23 @@ class Context:
                                             _ptr(grad), ctypes.byref(self._J)), "fwime_gradient", sync)
         return float(self._J.value)
 
+    def gradient_forward(self, v, w, pt, dobs, eps=0.0, sync=True):
+        """Forward half of the gradient: Phi (valid once synced), with the adjoint sweep's state kept in the
+        context (fwime_gradient_forward); no adjoint kernel runs."""
+        self._J = ctypes.c_double(0.0)
+        self._done(self._lib.fwime_gradient_forward(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs),
+                                                    ctypes.c_float(eps), ctypes.byref(self._J)),
+                   "fwime_gradient_forward", sync)
+        return float(self._J.value)
+
+    def gradient_backward(self, v, w, pt, dobs, grad, eps=0.0, accumulate=False, sync=True):
+        """Adjoint half: grad (=, or +=) B* r + T* r from the state gradient_forward kept for the same v, w, pt
+        (else the whole gradient) (fwime_gradient_backward)."""
+        self._done(self._lib.fwime_gradient_backward(self._h, _ptr(v), _ptr(w), _ptr(pt), _ptr(dobs),
+                                                     ctypes.c_float(eps), _ptr(grad), int(bool(accumulate))),
+                   "fwime_gradient_backward", sync)
+        return grad
+
     def vp_solve(self, v, w, dres, pt, eps=0.0, niter=10, sync=True):
         """Variable projection (Eqs. 2-5): niter CG iterations on (B~*B~ + eps^2 D*D) p~ = B~* dres, in place on
         pt.  Returns the objective Phi_eps,m at every iterate (niter + 1 values): a list when sync, else the
@@ -333,6 +376,17 @@ class Context:
                                           _ptr(inp), _ptr(out), int(bool(adjoint)), int(bool(accumulate))),
                    "fwime_spline", sync)
         return out
+
+    def spline_refine(self, zc, xc, mc, zf, xf, mf, sync=True):
+        """Model-space multiscale step: mf on the fine nodes zf x xf = the coarse spline of mc (nodes zc x xc)
+        evaluated there (fwime_spline_refine)."""
+        P = ctypes.POINTER(ctypes.c_float)
+        a = [np.ascontiguousarray(n, dtype=np.float32) for n in (zc, xc, zf, xf)]
+        self._done(self._lib.fwime_spline_refine(self._h, len(a[0]), a[0].ctypes.data_as(P), len(a[1]),
+                                                 a[1].ctypes.data_as(P), _ptr(mc), len(a[2]), a[2].ctypes.data_as(P),
+                                                 len(a[3]), a[3].ctypes.data_as(P), _ptr(mf)),
+                   "fwime_spline_refine", sync)
+        return mf
 
     def autotune(self, op: int) -> tuple[int, float]:
         """Times the stencil kernel on this operator's batch for candidate chunkings; keeps the fastest.

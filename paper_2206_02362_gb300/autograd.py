@@ -1,12 +1,15 @@
 """The FWIME objective as a torch.autograd.Function (Barnier et al., Eq. 1 at a
 fixed extended perturbation p~, gradient Eqs. 7-9 with S = I).
 
-forward(v) runs libfwime's gradient schedule -- the forward sweep (f + B~ p~,
-residual, objective) followed by the hand-written adjoint kernels (Born adjoint
-B* r and tomographic adjoint T* r, with checkpointed recomputation of the
-source-side wavefields) -- in one call, because the adjoint sweep consumes the
-forward sweep's checkpoints; backward() returns grad_output * (B* r + T* r).
-When v does not require a gradient only the forward sweep runs.
+forward(v) runs libfwime's forward sweep only (fwime_gradient_forward): f +
+B~ p~, the residual and Phi, keeping the checkpoints of the source-side
+wavefields and the residual in the context.  backward() runs the hand-written
+adjoint kernels (fwime_gradient_backward: the Born adjoint B* r and the
+tomographic adjoint T* r, recomputing the source-side wavefields segment by
+segment from those checkpoints) and scales the result by the incoming
+gradient.  When v does not require a gradient only the objective is computed
+and nothing is kept.  p~ is held fixed (the variable-projection gradient, whose
+chain through p~_opt vanishes at the optimum), so no gradient flows to p~.
 """
 from __future__ import annotations
 
@@ -16,18 +19,22 @@ import torch
 class FwimeObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, v, context, w, pt, dobs, eps):
+        vd = v.detach().contiguous()
         if ctx.needs_input_grad[0]:
-            grad = torch.empty_like(v)
-            J = context.gradient(v.detach().contiguous(), w, pt, dobs, grad, eps=eps)
-            ctx.save_for_backward(grad)
+            J = context.gradient_forward(vd, w, pt, dobs, eps=eps)
+            # the adjoint half needs the same v, w and p~ memory that the forward half saw
+            ctx.save_for_backward(vd)
+            ctx.context, ctx.w, ctx.pt, ctx.dobs, ctx.eps = context, w, pt, dobs, eps
         else:
-            J = context.objective(v.detach().contiguous(), w, pt, dobs, eps=eps)
+            J = context.objective(vd, w, pt, dobs, eps=eps)
         return torch.tensor(J, dtype=torch.float64, device=v.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        (grad,) = ctx.saved_tensors
-        return (gJ.to(grad.dtype) * grad, None, None, None, None, None)
+        (vd,) = ctx.saved_tensors
+        grad = torch.empty_like(vd)
+        ctx.context.gradient_backward(vd, ctx.w, ctx.pt, ctx.dobs, grad, eps=ctx.eps)
+        return (gJ.reshape(()).to(grad.dtype) * grad, None, None, None, None, None)
 
 
 def fwime_objective(context, v, w, pt, dobs, eps: float = 0.0):

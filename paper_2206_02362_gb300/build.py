@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfwime.so")
-SOURCES = ["fwime_api.cu", "k_prop.cu", "k_ext.cu", "k_misc.cu", "k_spline.cu", "k_tlag.cu", "fwime_static.cu"]
+SOURCES = ["fwime_api.cu", "k_prop.cu", "k_ext.cu", "k_misc.cu", "k_spline.cu", "k_tlag.cu", "fwime_static.cu", "fwime_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -55,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
         finally:
             BUILD, LIB = saved
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "fwime_kernels.cuh"), os.path.join(ROOT, "include", "fwime.h")]
+    headers = [os.path.join(CSRC, "fwime_kernels.cuh"), os.path.join(CSRC, "fwime_internal.h"),
+               os.path.join(ROOT, "include", "fwime.h")]
     objs = []
     jobs = []
     for src in SOURCES:

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "../../include/fwime.h"
+#include "fwime_internal.h"
 #include "fwime_kernels.cuh"
 
 using namespace fwk;
@@ -67,6 +68,16 @@ struct fwime_ctx {
         int K = 0;
     } bg;
     bool bg_written = false;        // set by the last enqueued B / B~ that filled the cache
+    // state the forward half of the gradient leaves for its adjoint half (fwime_gradient_forward /
+    // fwime_gradient_backward): segment-start states of the background and scattered fields of every
+    // shot, [nseg][4][nshot][P], then the residual r = f + B~ p~ - d_obs, [nshot][nt][nrec]
+    struct GradState {
+        float *buf = nullptr;
+        size_t bytes = 0;
+        bool valid = false;
+        const float *v = nullptr, *w = nullptr, *pt = nullptr;
+        int K = 0;
+    } gs;
     bool bg_used = false;           // the last call started from the cache
     long long launches = 0;
     // persistent device memory
@@ -92,7 +103,24 @@ struct fwime_ctx {
     long long prof_n[5] = {0, 0, 0, 0, 0};
     int last_err = 0;
     char err[320] = {0};
+    Server *srv = nullptr;          // a server context (fwime_server_create): no grid, no operators
 };
+
+namespace fwk {
+fwime_ctx *ctx_for_server(Server *srv)
+{
+    fwime_ctx *x = new fwime_ctx();
+    x->srv = srv;
+    return x;
+}
+Server *ctx_server(const fwime_ctx *x) { return x ? x->srv : nullptr; }
+}  // namespace fwk
+
+// operator entry points refuse a server context
+#define NOT_SERVER(x)                                                                                  \
+    do {                                                                                               \
+        if ((x)->srv) return fail((x), FWIME_EINVAL, "a server context takes requests (fwime_submit), not operators"); \
+    } while (0)
 
 // ------------------------------------------------------------------ helpers
 
@@ -241,12 +269,13 @@ static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int
     case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
     case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
     case FWIME_OP_TOMO_ADJ:
-    case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + 4 * nseg; break;
+    case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + (no_ckpt ? 0 : 4 * nseg); break;
     case FWIME_OP_OBJECTIVE: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 2 * K; break;
     default: break;
     }
     s.per_shot = f * (size_t)P;
-    if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) s.per_shot += (size_t)g.nt * nrec;
+    // gradient and objective predict the data into the workspace, unless the context's gradient state holds it
+    if ((op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) && !no_ckpt) s.per_shot += (size_t)g.nt * nrec;
     if (host_io) {
         const size_t nd = (size_t)nshot * g.nt * nrec, nm = (size_t)g.nz * g.nx;
         s.staging = al(nm) + al((size_t)nshot * g.nt) + 2 * al(nd) + al(nh * nm) + al(nm) + al(nh * nm);
@@ -404,13 +433,14 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
     case FWIME_OP_BORN_EXT_ADJ: nf = 2; nk = 1; nr = 1; nck = no_ckpt ? 0 : 2; break;
     case FWIME_OP_TOMO: nf = 8; nk = 4; break;
     case FWIME_OP_OBJECTIVE: nf = 4; nk = 2; break;
-    default: nf = 4; nk = 3; nr = 3; nck = 4; break;
+    default: nf = 4; nk = 3; nr = 3; nck = no_ckpt ? 0 : 4; break;
     }
     for (int i = 0; i < nf; ++i) w.f[i] = take(SP);
     for (int i = 0; i < nk; ++i) w.ring[i] = take((size_t)w.K * SP);
     for (int i = 0; i < nr; ++i) w.ring[nk + i] = take((size_t)w.R * SP);
     if (nck) w.ckpt = take((size_t)w.nseg * nck * SP);
-    if (op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) w.pred = take((size_t)w.S * x->g.nt * x->nrec);
+    if ((op == FWIME_OP_GRADIENT || op == FWIME_OP_OBJECTIVE) && !no_ckpt)
+        w.pred = take((size_t)w.S * x->g.nt * x->nrec);
     if ((char *)p > x->ws + x->ws_bytes) return fail(x, FWIME_ENOMEM, "workspace layout overflow");
     return FWIME_OK;
 }
@@ -620,6 +650,46 @@ static bool bg_reserve(fwime_ctx *x, int K)
 static float *bg_slot(fwime_ctx *x, int j, int t, int s0)
 {
     return x->bg.buf + ((2LL * j + t) * x->nshot + s0) * x->P;
+}
+
+// ---------------------------------------------------------------- gradient state (split gradient)
+static size_t gs_bytes(const fwime_ctx *x, int K)
+{
+    const size_t nseg = (size_t)((x->g.nt - 1 + K - 1) / K);
+    return (4 * nseg * (size_t)x->nshot * (size_t)x->P + (size_t)x->nshot * x->g.nt * x->nrec) * sizeof(float);
+}
+
+static void gs_release(fwime_ctx *x)
+{
+    if (x->gs.buf) cudaFreeAsync(x->gs.buf, x->st);
+    x->gs = fwime_ctx::GradState{};
+}
+
+// Makes room for the state of every shot; false when it does not fit next to the adjoint sweep's own
+// workspace for one shot (the split gradient then recomputes the forward sweep in its adjoint half).
+static bool gs_reserve(fwime_ctx *x, int K)
+{
+    const size_t need = gs_bytes(x, K);
+    if (x->gs.buf && x->gs.bytes >= need) return true;
+    gs_release(x);
+    const int nseg = (x->g.nt - 1 + K - 1) / K;
+    const Sizes sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, FWIME_OP_GRADIENT, K, false, true);
+    const size_t one = (sz.model + sz.per_shot) * sizeof(float) + ((size_t)2 << 30);
+    (void)nseg;
+    if (x->max_ws && x->ws_bytes + need + one > x->max_ws) return false;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (need + one > fr + x->ws_bytes) return false;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&x->gs.buf), need, x->st) != cudaSuccess) {
+        cudaGetLastError();
+        x->gs.buf = nullptr;
+        return false;
+    }
+    x->gs.bytes = need;
+    return true;
 }
 
 static int run_forward(fwime_ctx *x, Run &r, const float *v, const float *w, float *d)
@@ -1142,19 +1212,30 @@ static int run_tomo(fwime_ctx *x, Run &r, const float *v, const float *w, const 
     return FWIME_OK;
 }
 
+// Phases of the FWIME gradient: both sweeps per batch (the self-contained call), the forward sweep alone
+// leaving its checkpoints and residual in the context's gradient state, or the adjoint sweep alone from it.
+enum { PH_BOTH = 0, PH_FORWARD = 1, PH_BACKWARD = 2 };
+
 // T* (mode 0, r = d), the FWIME gradient (mode 1, r = f + B~p~ - dobs) and the
-// objective alone (mode 2: forward sweep and residual norm, no adjoint sweep)
+// objective alone (mode 2: forward sweep and residual norm, no adjoint sweep).
+// With mode 1, `phase` splits the gradient into its forward sweep (checkpoints of the background and
+// scattered fields of every shot at every segment start, and the residual, written to x->gs) and its
+// adjoint sweep (read back from x->gs); PH_BOTH keeps both per batch in the workspace.
 static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const float *w, const float *pt,
-                        const float *d, float *out, int accumulate, float eps)
+                        const float *d, float *out, int accumulate, float eps, int phase = PH_BOTH)
 {
-    const bool grad = mode >= 1, objective_only = mode == 2;
+    const bool grad = mode >= 1, objective_only = mode == 2 || phase == PH_FORWARD;
+    const bool fwd = phase != PH_BACKWARD, bwd = !objective_only;
+    const bool state = phase != PH_BOTH;   // checkpoints and residual in x->gs
     const int nt = x->g.nt, S = r.w.S, K = r.w.K, R = r.w.R, nseg = r.w.nseg;
     const size_t nd = (size_t)nt * x->nrec;
     const long long SP = (long long)S * x->P;
     const size_t nhP = (size_t)x->g.nh * x->P;
     TRY(zero(x, r.w.W, sizeof(float) * nhP));
-    TRY(zero(x, r.w.acc1, sizeof(float) * x->P));
-    TRY(zero(x, r.w.acc2, sizeof(float) * nhP));   // extended image of the residual, contracted with p~ at the end
+    if (bwd) {
+        TRY(zero(x, r.w.acc1, sizeof(float) * x->P));
+        TRY(zero(x, r.w.acc2, sizeof(float) * nhP));   // extended image of the residual, contracted with p~ at the end
+    }
     const double nm = (double)x->g.nz * x->g.nx;
     LAUNCH(FWIME_K_OTHER, 12.0 * x->g.nh * nm,
            launch_ext_weights(pt, r.w.bpad, nullptr, nullptr, r.w.W, x->g.nh, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 0,
@@ -1163,61 +1244,69 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
     float *Mu = r.w.ring[3], *Zr = r.w.ring[4], *Mu2 = r.w.ring[5];
     float *ck = r.w.ckpt;
     TRY(zero(x, Er, sizeof(float) * K * SP));
-    if (grad) TRY(zero(x, x->d_J, sizeof(double)));
+    const bool report_J = grad && fwd;
+    if (report_J) TRY(zero(x, x->d_J, sizeof(double)));
     const int nred = 1024;
     const float idt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
+    float *res_state = state ? x->gs.buf + 4LL * nseg * x->nshot * x->P : nullptr;
     for (int s0 = 0; s0 < x->nshot; s0 += S) {
         const int Sb = std::min(S, x->nshot - s0);
         const size_t fb = sizeof(float) * (size_t)Sb * x->P;
+        const size_t fn = (size_t)Sb * x->P;
+        // checkpoint t (0, 1: q0^n0, q0^n0-1; 2, 3: the scattered field's) of segment j for this batch
+        auto ckp = [&](int j, int t) -> float * {
+            return state ? x->gs.buf + ((4LL * j + t) * x->nshot + s0) * x->P : ck + (4LL * j + t) * SP;
+        };
         float *q0c = r.w.f[0], *q0p = r.w.f[1], *qsc = r.w.f[2], *qsp = r.w.f[3];
         for (int i = 0; i < 4; ++i) TRY(zero(x, r.w.f[i], fb));
-        if (!objective_only) {
+        if (bwd) {
             TRY(zero(x, Mu, sizeof(float) * R * SP));
             TRY(zero(x, Zr, sizeof(float) * R * SP));
             TRY(zero(x, Mu2, sizeof(float) * R * SP));
         }
         const float *ws = w + (size_t)s0 * nt;
-        float *pred = r.w.pred;
-        if (grad) TRY(zero(x, pred, sizeof(float) * Sb * nd));
-        // forward sweep
-        for (int j = 0; j < nseg; ++j) {
-            const long long cb = 4LL * j * SP;
-            if (!objective_only) {
-                TRY(copyf(x, ck + cb, q0c, (size_t)Sb * x->P));
-                TRY(copyf(x, ck + cb + SP, q0p, (size_t)Sb * x->P));
-                TRY(copyf(x, ck + cb + 2 * SP, qsc, (size_t)Sb * x->P));
-                TRY(copyf(x, ck + cb + 3 * SP, qsp, (size_t)Sb * x->P));
-            }
-            if (!grad && j == nseg - 1) break;
-            const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
-            for (int n = n0; n < n1; ++n) {
-                TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
-                if (grad) TRY(record(r, Sb, q0p, nullptr, pred + (size_t)(n + 1) * x->nrec, 0));
-                std::swap(q0c, q0p);
-            }
-            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
-            for (int n = n0; n < n1; ++n) {
-                TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
-                if (grad) TRY(record(r, Sb, qsp, nullptr, pred + (size_t)(n + 1) * x->nrec, 1));
-                std::swap(qsc, qsp);
-            }
-        }
+        float *pred = state ? res_state + s0 * nd : r.w.pred;
         const float *rr = d + s0 * nd;
-        if (grad) {
-            LAUNCH(FWIME_K_OTHER, 12.0 * Sb * nd,
-                   launch_residual(pred, d + s0 * nd, pred, (long long)Sb * nd, x->d_part, nred, x->st));
-            LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
-            rr = pred;
+        if (fwd) {
+            const bool keep = bwd || state;   // checkpoints for an adjoint sweep
+            if (grad) TRY(zero(x, pred, sizeof(float) * Sb * nd));
+            // forward sweep
+            for (int j = 0; j < nseg; ++j) {
+                if (keep) {
+                    TRY(copyf(x, ckp(j, 0), q0c, fn));
+                    TRY(copyf(x, ckp(j, 1), q0p, fn));
+                    TRY(copyf(x, ckp(j, 2), qsc, fn));
+                    TRY(copyf(x, ckp(j, 3), qsp, fn));
+                }
+                if (!grad && j == nseg - 1) break;
+                const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+                for (int n = n0; n < n1; ++n) {
+                    TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
+                    if (grad) TRY(record(r, Sb, q0p, nullptr, pred + (size_t)(n + 1) * x->nrec, 0));
+                    std::swap(q0c, q0p);
+                }
+                TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
+                for (int n = n0; n < n1; ++n) {
+                    TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
+                    if (grad) TRY(record(r, Sb, qsp, nullptr, pred + (size_t)(n + 1) * x->nrec, 1));
+                    std::swap(qsc, qsp);
+                }
+            }
+            if (grad) {
+                LAUNCH(FWIME_K_OTHER, 12.0 * Sb * nd,
+                       launch_residual(pred, d + s0 * nd, pred, (long long)Sb * nd, x->d_part, nred, x->st));
+                LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
+            }
         }
-        if (objective_only) continue;
+        if (grad) rr = pred;
+        if (!bwd) continue;
         // backward sweep
         for (int j = nseg - 1; j >= 0; --j) {
             const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
-            const long long cb = 4LL * j * SP;
-            TRY(copyf(x, q0c, ck + cb, (size_t)Sb * x->P));
-            TRY(copyf(x, q0p, ck + cb + SP, (size_t)Sb * x->P));
-            TRY(copyf(x, qsc, ck + cb + 2 * SP, (size_t)Sb * x->P));
-            TRY(copyf(x, qsp, ck + cb + 3 * SP, (size_t)Sb * x->P));
+            TRY(copyf(x, q0c, ckp(j, 0), fn));
+            TRY(copyf(x, q0p, ckp(j, 1), fn));
+            TRY(copyf(x, qsc, ckp(j, 2), fn));
+            TRY(copyf(x, qsp, ckp(j, 3), fn));
             for (int n = n0; n < n1; ++n) {
                 TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
                 std::swap(q0c, q0p);
@@ -1247,11 +1336,11 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
                       ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, nullptr, r.w.acc2));
         }
     }
-    if (!objective_only)
+    if (bwd)
         LAUNCH(FWIME_K_OTHER, 20.0 * nm,
                launch_finalize(r.w.acc1, r.w.acc2, r.w.bpad, v, out, 1, x->g.nz, x->g.nx, x->o, x->NXP, x->P, 1,
                                accumulate, x->st, pt, x->g.nh));
-    if (grad) {
+    if (report_J) {
         LAUNCH(FWIME_K_OTHER, 4.0 * x->g.nh * nm,
                launch_dso(pt, x->g.nh, (long long)x->g.nz * x->g.nx, x->d_part, nred, x->st));
         LAUNCH(FWIME_K_OTHER, 8.0 * nred,
@@ -1270,6 +1359,9 @@ struct Call {
     int accumulate;
     float eps;
 };
+
+// internal operators of the split gradient (never passed through the C ABI)
+enum { OP_GRAD_FWD = 100, OP_GRAD_BWD = 101 };
 
 static bool is_bg_writer(int op) { return op == FWIME_OP_BORN || op == FWIME_OP_BORN_EXT; }
 static bool is_bg_reader(int op) { return op == FWIME_OP_BORN_ADJ || op == FWIME_OP_BORN_EXT_ADJ; }
@@ -1301,6 +1393,14 @@ static int enqueue(fwime_ctx *x, const Call &c)
     x->bg_used = use_bg;
     x->bg_written = is_bg_writer(c.op) && bg_applies(x, c.op) && x->opt_reuse_bg && bg_reserve(x, seg_K(x));
     if (x->bg_written) x->bg.valid = false;   // being overwritten
+    if (c.op == OP_GRAD_FWD || c.op == OP_GRAD_BWD) {
+        // the split gradient: checkpoints and residual live in the context's gradient state
+        TRY(plan(x, c.op == OP_GRAD_FWD ? FWIME_OP_OBJECTIVE : FWIME_OP_GRADIENT, r.w, true));
+        init_run(x, r, r.w.S);
+        TRY(prep_model(x, r, c.v));
+        return run_tomo_adj(x, r, 1, c.v, c.w, c.in1, c.in2, c.out, c.accumulate, c.eps,
+                            c.op == OP_GRAD_FWD ? PH_FORWARD : PH_BACKWARD);
+    }
     TRY(plan(x, c.op, r.w, use_bg));
     init_run(x, r, r.w.S);
     TRY(prep_model(x, r, c.v));
@@ -1322,7 +1422,7 @@ static int enqueue(fwime_ctx *x, const Call &c)
     case FWIME_OP_OBJECTIVE: {
         const int mode = c.op == FWIME_OP_TOMO_ADJ ? 0 : (c.op == FWIME_OP_GRADIENT ? 1 : 2);
         float *o = c.op == FWIME_OP_OBJECTIVE ? nullptr : c.out;
-        const int acc = c.op == FWIME_OP_TOMO_ADJ ? c.accumulate : 0;
+        const int acc = c.op == FWIME_OP_OBJECTIVE ? 0 : c.accumulate;
         const float e = c.op == FWIME_OP_TOMO_ADJ ? 0.f : c.eps;
         if (x->opt_tlag > 0) return run_tomo_adj_tlag(x, r, mode, c.v, c.w, c.in1, c.in2, o, acc, e);
         return run_tomo_adj(x, r, mode, c.v, c.w, c.in1, c.in2, o, acc, e);
@@ -1391,6 +1491,7 @@ enum { K_NONE = 0, K_DATA, K_MODEL, K_EXT };
 static int call_op(fwime_ctx *x, Call c, int kin1, int kin2, int kout)
 {
     if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
     if (!c.v || !c.w || (!c.out && c.op != FWIME_OP_OBJECTIVE)) return fail(x, FWIME_EINVAL, "null pointer argument");
     if (!x->opt_host_io) return run_call(x, c);
     // the staged v and w sit at the start of the arena: a B~* can reuse the background of the B~ before it
@@ -1514,6 +1615,11 @@ int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo, si
 void fwime_destroy(fwime_ctx *x)
 {
     if (!x) return;
+    if (x->srv) {
+        server_destroy(x->srv);
+        delete x;
+        return;
+    }
     if (x->st) cudaStreamSynchronize(x->st);
     else cudaDeviceSynchronize();
     for (auto &kv : x->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -1522,6 +1628,7 @@ void fwime_destroy(fwime_ctx *x)
     if (x->small) cudaFreeAsync(x->small, x->st);
     if (x->vp_hist_dev) cudaFreeAsync(x->vp_hist_dev, x->st);
     if (x->bg.buf) cudaFreeAsync(x->bg.buf, x->st);
+    if (x->gs.buf) cudaFreeAsync(x->gs.buf, x->st);
     cudaGetLastError();
     delete x;
 }
@@ -1529,6 +1636,7 @@ void fwime_destroy(fwime_ctx *x)
 int fwime_set_option(fwime_ctx *x, int option, long long value)
 {
     if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
     if (x->capturing) return FWIME_EBUSY;
     switch (option) {
     case FWIME_OPT_SHOTS_PER_BATCH: if (value < 0) break; x->opt_S = (int)value; return FWIME_OK;
@@ -1563,6 +1671,7 @@ int fwime_set_option(fwime_ctx *x, int option, long long value)
 int fwime_get_option(fwime_ctx *x, int option, long long *value)
 {
     if (!x || !value) return FWIME_EINVAL;
+    NOT_SERVER(x);
     switch (option) {
     case FWIME_OPT_SHOTS_PER_BATCH: *value = x->opt_S; return FWIME_OK;
     case FWIME_OPT_SEGMENT: *value = x->opt_K; return FWIME_OK;
@@ -1648,10 +1757,65 @@ int fwime_gradient(fwime_ctx *x, const float *v, const float *w, const float *pt
     return call_op(x, c, K_EXT, K_DATA, K_MODEL);
 }
 
+int fwime_gradient_forward(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
+                           double *objective)
+{
+    if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
+    if (!v || !w || !pt || !dobs || !objective) return fail(x, FWIME_EINVAL, "null argument");
+    if (!(eps >= 0.f)) return fail(x, FWIME_EINVAL, "eps must be >= 0");
+    if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "the split gradient takes device pointers, no capture");
+    x->launches = 0;
+    x->user_J = objective;
+    x->gs.valid = false;
+    const int K = seg_K(x);
+    if (x->opt_tlag > 0 || x->opt_plain || !gs_reserve(x, K)) {
+        // no room for the state (or a schedule that places its checkpoints otherwise): the objective alone;
+        // the adjoint half then runs the whole gradient
+        gs_release(x);
+        const int rc = enqueue_noted(x, Call{FWIME_OP_OBJECTIVE, v, w, pt, dobs, nullptr, 0, eps});
+        if (rc != FWIME_OK) x->user_J = nullptr;
+        return rc;
+    }
+    const int rc = enqueue_noted(x, Call{OP_GRAD_FWD, v, w, pt, dobs, nullptr, 0, eps});
+    if (rc != FWIME_OK) {
+        x->user_J = nullptr;
+        gs_release(x);
+        return rc;
+    }
+    x->gs.valid = true;
+    x->gs.v = v; x->gs.w = w; x->gs.pt = pt; x->gs.K = K;
+    return FWIME_OK;
+}
+
+int fwime_gradient_backward(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
+                            float *grad, int accumulate)
+{
+    if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
+    if (!v || !w || !pt || !dobs || !grad) return fail(x, FWIME_EINVAL, "null argument");
+    if (!(eps >= 0.f)) return fail(x, FWIME_EINVAL, "eps must be >= 0");
+    if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "the split gradient takes device pointers, no capture");
+    x->launches = 0;
+    const bool from_state = x->gs.valid && x->gs.buf && x->gs.v == v && x->gs.w == w && x->gs.pt == pt &&
+                            x->gs.K == seg_K(x) && x->opt_tlag == 0 && !x->opt_plain;
+    int rc;
+    if (from_state) {
+        rc = enqueue_noted(x, Call{OP_GRAD_BWD, v, w, pt, dobs, grad, accumulate ? 1 : 0, eps});
+    } else {
+        // the whole gradient (forward sweep recomputed); its objective is not reported
+        rc = enqueue_noted(x, Call{FWIME_OP_GRADIENT, v, w, pt, dobs, grad, accumulate ? 1 : 0, eps});
+    }
+    x->bg_used = from_state;
+    gs_release(x);   // stream-ordered: freed after the adjoint sweep that reads it
+    return rc;
+}
+
 int fwime_vp_solve(fwime_ctx *x, const float *v, const float *w, const float *dres, float eps, int niter, float *pt,
                    double *history)
 {
     if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
     if (!v || !w || !dres || !pt || niter < 0 || !(eps >= 0.f)) return fail(x, FWIME_EINVAL, "vp_solve arguments");
     if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "vp_solve takes device pointers, no capture");
     x->launches = 0;
@@ -1731,6 +1895,7 @@ int fwime_spline(fwime_ctx *x, int nzs, const float *zs, int nxs, const float *x
                  int adjoint, int accumulate)
 {
     if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
     if (nzs < 1 || nxs < 1 || !zs || !xs || !in || !out) return fail(x, FWIME_EINVAL, "spline arguments");
     if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "spline takes device pointers, no capture");
     for (int i = 0; i < nzs; ++i)
@@ -1758,6 +1923,44 @@ int fwime_spline(fwime_ctx *x, int nzs, const float *zs, int nxs, const float *x
     return rc;
 }
 
+int fwime_spline_refine(fwime_ctx *x, int nzc, const float *zc, int nxc, const float *xc, const float *mc, int nzf,
+                        const float *zf, int nxf, const float *xf, float *mf)
+{
+    if (!x) return FWIME_EINVAL;
+    NOT_SERVER(x);
+    if (nzc < 1 || nxc < 1 || nzf < 1 || nxf < 1 || !zc || !xc || !zf || !xf || !mc || !mf)
+        return fail(x, FWIME_EINVAL, "spline_refine arguments");
+    if (x->opt_host_io || x->capturing) return fail(x, FWIME_EINVAL, "spline_refine takes device pointers, no capture");
+    const int n[4] = {nzc, nxc, nzf, nxf};
+    const float *nodes[4] = {zc, xc, zf, xf};
+    for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < n[a]; ++i)
+            if (!std::isfinite(nodes[a][i]) || (i && !(nodes[a][i] > nodes[a][i - 1])))
+                return fail(x, FWIME_EINVAL, "spline nodes must be finite and increase");
+    x->launches = 0;
+    float *dn = nullptr;
+    const size_t nn = (size_t)nzc + nxc + nzf + nxf;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&dn), nn * sizeof(float), x->st));
+    int rc = FWIME_OK;
+    size_t off = 0;
+    for (int a = 0; a < 4 && rc == FWIME_OK; ++a) {
+        const cudaError_t e = cudaMemcpyAsync(dn + off, nodes[a], n[a] * sizeof(float), cudaMemcpyHostToDevice, x->st);
+        if (e != cudaSuccess) rc = fail(x, FWIME_ECUDA, "spline nodes: %s", cudaGetErrorString(e));
+        off += n[a];
+    }
+    if (rc == FWIME_OK) {
+        auto go = [&]() -> int {
+            LAUNCH(FWIME_K_OTHER, 4.0 * ((double)nzc * nxc + (double)nzf * nxf),
+                   launch_spline_refine(dn, nzc, dn + nzc, nxc, mc, dn + nzc + nxc, nzf, dn + nzc + nxc + nzf, nxf, mf,
+                                        x->st));
+            return FWIME_OK;
+        };
+        rc = go();
+    }
+    cudaFreeAsync(dn, x->st);   // (copies from pageable host memory return once the source has been staged)
+    return rc;
+}
+
 int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, const float *const *w, float *const *d)
 {
     if (!ctxs || !v || !w || !d || n < 1 || n > 4096) return FWIME_EINVAL;
@@ -1765,6 +1968,7 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
     if (!x) return FWIME_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !v[i] || !w[i] || !d[i]) return fail(x, FWIME_EINVAL, "null member %d", i);
+        if (ctxs[i]->srv) return fail(x, FWIME_EINVAL, "member %d is a server context", i);
         if (ctxs[i]->st != x->st) return fail(x, FWIME_EINVAL, "group members must share one stream");
         if (ctxs[i]->capturing || ctxs[i]->opt_host_io) return fail(x, FWIME_EINVAL, "member %d: capture/host I/O", i);
         if (ctxs[i]->opt_fs) return fail(x, FWIME_EINVAL, "member %d: the grouped forward has no free surface", i);
@@ -1842,6 +2046,7 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
 int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_out)
 {
     if (!x || op < 0 || op > FWIME_OP_OBJECTIVE) return FWIME_EINVAL;
+    NOT_SERVER(x);
     if (x->capturing) return FWIME_EBUSY;
     Run r;
     TRY(plan(x, op, r.w));
@@ -1916,6 +2121,7 @@ int fwime_objective(fwime_ctx *x, const float *v, const float *w, const float *p
 int fwime_sync(fwime_ctx *x)
 {
     if (!x) return FWIME_EINVAL;
+    if (x->srv) return server_sync(x->srv);
     CK(x->st ? cudaStreamSynchronize(x->st) : cudaDeviceSynchronize());
     TRY(prof_collect(x));
     CK(cudaMemcpyAsync(x->h_status, x->d_status, sizeof(int), cudaMemcpyDeviceToHost, x->st));
@@ -1939,6 +2145,7 @@ int fwime_sync(fwime_ctx *x)
 int fwime_profile_read(fwime_ctx *x, int kernel, double *ms, long long *launches, double *bytes, int reset)
 {
     if (!x || kernel < 0 || kernel > FWIME_K_OTHER) return FWIME_EINVAL;
+    NOT_SERVER(x);
     TRY(prof_collect(x));
     if (ms) *ms = x->prof_ms[kernel];
     if (launches) *launches = x->prof_n[kernel];

@@ -207,6 +207,9 @@ cudaError_t launch_copy_fields(float *dst, const float *src, long long n, cudaSt
 // linear spline re-parametrisation: out = S in (adjoint = 0) or S* in (tmp: nz * nxs floats)
 cudaError_t launch_spline(const float *zs, int nzs, const float *xs, int nxs, int nz, int nx, float dz, float dx,
                           const float *in, float *out, float *tmp, int adjoint, int accumulate, cudaStream_t st);
+// model-space multiscale step: the coarse spline mc [nzc][nxc] evaluated at the fine nodes, mf [nzf][nxf]
+cudaError_t launch_spline_refine(const float *zc, int nzc, const float *xc, int nxc, const float *mc, const float *zf,
+                                 int nzf, const float *xf, int nxf, float *mf, cudaStream_t st);
 // VP conjugate gradients (device scalars)
 cudaError_t launch_dot(const float *x, const float *y, long long n, double *partials, int nblocks, double *out,
                        int accumulate, double scale, cudaStream_t st);

@@ -95,6 +95,29 @@ __global__ void k_spline_adj_z(const float *zs, int nzs, int nxs, int nz, float 
     *o = accumulate ? *o + s : s;
 }
 
+// model-space multiscale step: mf[i][j] = the coarse linear spline of mc at the fine node (zf[i], xf[j])
+__global__ void k_spline_refine(const float *zc, int nzc, const float *xc, int nxc, const float *mc, const float *zf,
+                                int nzf, const float *xf, int nxf, float *mf)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= nxf) return;
+    int kz, kx;
+    float az, ax;
+    spline_locate(zc, nzc, zf[i], kz, az);
+    spline_locate(xc, nxc, xf[j], kx, ax);
+    const int kz1 = kz + 1 < nzc ? kz + 1 : kz, kx1 = kx + 1 < nxc ? kx + 1 : kx;
+    const float top = (1.f - ax) * mc[(long long)kz * nxc + kx] + ax * mc[(long long)kz * nxc + kx1];
+    const float bot = (1.f - ax) * mc[(long long)kz1 * nxc + kx] + ax * mc[(long long)kz1 * nxc + kx1];
+    mf[(long long)i * nxf + j] = (1.f - az) * top + az * bot;
+}
+
+cudaError_t launch_spline_refine(const float *zc, int nzc, const float *xc, int nxc, const float *mc, const float *zf,
+                                 int nzf, const float *xf, int nxf, float *mf, cudaStream_t st)
+{
+    k_spline_refine<<<dim3((nxf + 127) / 128, nzf), 128, 0, st>>>(zc, nzc, xc, nxc, mc, zf, nzf, xf, nxf, mf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spline(const float *zs, int nzs, const float *xs, int nxs, int nz, int nx, float dz, float dx,
                           const float *in, float *out, float *tmp, int adjoint, int accumulate, cudaStream_t st)
 {

@@ -1,30 +1,21 @@
-"""Continuous-batching request loop for FWIME shot requests on one GPU.
+"""Serving FWIME shot requests through libfwime's request server.
 
 A request is one forward-modelling shot (f, Eq. 1) or one FWIME-gradient shot
 (Phi and B* r + T* r at fixed p~, Eqs. 1, 7-9) on its own grid, nt and nh.
-Requests arrive over time; the loop
-
-  * admits a request as soon as its device memory (workspace from
-    fwime_workspace_bytes plus its inputs/outputs) fits the budget and an
-    in-flight slot is free -- while other requests are still running;
-  * keeps its model, wavelet, p~, data and wavefields resident on the device
-    for the life of the request, on a CUDA stream of its own, so the work of
-    all admitted requests overlaps on the GPU;
-  * enqueues each request's kernels from a worker thread (the C ABI releases
-    the GIL), detects completion with a CUDA event, returns the result to
-    pinned host memory and releases the memory for the next admissions;
-  * reports per-request latency (arrival -> result on the host), p50/p99 and
-    throughput.
-
-Device memory is stream-ordered (libfwime allocates with cudaMallocAsync on the
-request's stream), so finishing one request never synchronises the others.
+The continuous batching itself runs natively behind the C ABI
+(``fwime_server_create`` / ``fwime_submit`` / ``fwime_poll`` / ``fwime_wait``):
+admission by device memory (``fwime_request_bytes``) and in-flight slots while
+earlier requests run, one stream and context per request so admitted requests
+overlap, grouped launches for forward requests admitted together, completion by
+CUDA events.  This module only marshals: it pins each request's host buffers,
+submits requests at their arrival times, polls, and reports per-request latency
+(arrival -> result in host memory), p50/p99 and throughput.
 """
 from __future__ import annotations
 
-import collections
-import concurrent.futures as cf
+import ctypes
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -68,185 +59,152 @@ class ShotResult:
         return self.done - self.arrival
 
 
-@dataclass
-class _Active:
-    req: ShotRequest
-    ctx: object
-    stream: object
-    event: object
-    tensors: dict
-    host_out: object
-    nbytes: int
-    admitted: float
-    future: object = None
-    J: list = field(default_factory=list)
+class _Marshalled:
+    """A request's pinned host buffers and its fwime_request (kept alive until collected)."""
+
+    def __init__(self, req: ShotRequest):
+        import torch
+
+        import paper_2206_02362_gb300 as fw
+        self.req = req
+
+        def pin(a):
+            t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+            return t
+
+        nrec = len(req.rec_iz)
+        self.t = {"v": pin(req.v), "w": pin(np.asarray(req.w)[None])}
+        if req.kind == "forward":
+            self.t["d"] = torch.empty((1, req.nt, nrec), pin_memory=True)
+        else:
+            self.t["pt"] = pin(req.pt)
+            self.t["dobs"] = pin(np.asarray(req.dobs)[None])
+            self.t["g"] = torch.empty((req.nz, req.nx), pin_memory=True)
+        self.grid = fw.Grid(nz=req.nz, nx=req.nx, sponge=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
+        self.geom = fw.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
+        gm, self._keep = self.geom.c()
+        ptr = lambda k: self.t[k].data_ptr() if k in self.t else None  # noqa: E731
+        self.c = fw.RequestC(fw.REQ_FORWARD if req.kind == "forward" else fw.REQ_GRADIENT, self.grid.c(), gm, 1,
+                             ptr("v"), ptr("w"), ptr("pt"), ptr("dobs"), ptr("d"), ptr("g"),
+                             ctypes.c_float(req.eps))
 
 
 def request_bytes(req: ShotRequest) -> int:
-    """Device bytes a request holds while admitted: workspace + inputs + outputs."""
+    """Device bytes the server admits a request with: workspace + staging (fwime_request_bytes)."""
     import paper_2206_02362_gb300 as fw
     grid = fw.Grid(nz=req.nz, nx=req.nx, sponge=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
     geom = fw.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
-    op = fw.OP_FORWARD if req.kind == "forward" else fw.OP_GRADIENT
-    ws = fw.workspace_bytes(grid, geom, op, 1, 0)
-    io = 4 * (req.v.size + req.nt + req.nt * len(req.rec_iz))
-    if req.kind == "gradient":
-        io += 4 * (req.pt.size + req.v.size)
-    return ws + io + (1 << 20)
+    gm, keep = geom.c()
+    c = fw.RequestC(fw.REQ_FORWARD if req.kind == "forward" else fw.REQ_GRADIENT, grid.c(), gm, 1,
+                    None, None, None, None, None, None, ctypes.c_float(req.eps))
+    out = ctypes.c_size_t(0)
+    rc = fw.load().fwime_request_bytes(ctypes.byref(c), ctypes.byref(out))
+    if rc != fw.FWIME_OK:
+        raise fw.FwimeError(rc, "fwime_request_bytes")
+    return int(out.value)
 
 
 class Server:
-    """Memory-admitted, stream-overlapped request loop on one CUDA device."""
+    """libfwime's request server on the current CUDA device (fwime_server_create)."""
 
-    def __init__(self, memory_budget: int | None = None, max_active: int = 64, workers: int = 8, device: int = 0,
-                 plain: bool = False, group_forward: bool = True):
+    def __init__(self, memory_budget: int | None = None, max_active: int = 64, device: int = 0,
+                 plain: bool = False):
         import torch
-        self.torch = torch
-        self.device = torch.device("cuda", device)
-        torch.cuda.set_device(self.device)
+
+        import paper_2206_02362_gb300 as fw
+        self.fw = fw
+        torch.cuda.set_device(device)
         if memory_budget is None:
-            free, _ = torch.cuda.mem_get_info(self.device)
+            free, _ = torch.cuda.mem_get_info(device)
             memory_budget = int(0.8 * free)
         self.budget = memory_budget
-        self.max_active = max_active
-        self.plain = plain              # one shot per launch, host-driven steps (the comparison path)
-        # forward requests admitted together run as one group: one launch per time step for all of
-        # them, whatever their grid sizes and record lengths (fwime_forward_group)
-        self.group_forward = group_forward and not plain
-        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
+        self._lib = fw.load()
+        self._h = ctypes.c_void_p()
+        rc = self._lib.fwime_server_create(ctypes.byref(self._h), ctypes.c_size_t(memory_budget), int(max_active),
+                                           fw.SERVE_PLAIN if plain else 0)
+        if rc != fw.FWIME_OK:
+            raise fw.FwimeError(rc, "fwime_server_create")
 
-    # ---------------------------------------------------------------- one request
-    def _admit(self, req: ShotRequest, nbytes: int, now: float) -> _Active:
-        import paper_2206_02362_gb300 as fw
-        torch = self.torch
-        stream = torch.cuda.Stream(device=self.device)
-        grid = fw.Grid(nz=req.nz, nx=req.nx, sponge=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
-        geom = fw.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
-        nrec = len(req.rec_iz)
-        with torch.cuda.stream(stream):
-            t = {"v": torch.from_numpy(np.ascontiguousarray(req.v, dtype=np.float32)).pin_memory()
-                 .to(self.device, non_blocking=True),
-                 "w": torch.from_numpy(np.ascontiguousarray(req.w, dtype=np.float32)[None]).pin_memory()
-                 .to(self.device, non_blocking=True)}
-            if req.kind == "forward":
-                t["d"] = torch.empty((1, req.nt, nrec), device=self.device)
-                host_out = torch.empty((req.nt, nrec), pin_memory=True)
-            else:
-                t["pt"] = torch.from_numpy(np.ascontiguousarray(req.pt, dtype=np.float32)).pin_memory() \
-                    .to(self.device, non_blocking=True)
-                t["dobs"] = torch.from_numpy(np.ascontiguousarray(req.dobs, dtype=np.float32)[None]).pin_memory() \
-                    .to(self.device, non_blocking=True)
-                t["g"] = torch.empty((req.nz, req.nx), device=self.device)
-                host_out = torch.empty((req.nz, req.nx), pin_memory=True)
-        ctx = fw.Context(grid, geom, stream=stream, shots_per_batch=1, plain=int(self.plain))
-        act = _Active(req, ctx, stream, torch.cuda.Event(), t, host_out, nbytes, now)
+    def _error(self) -> str:
+        buf = ctypes.create_string_buffer(256)
+        self._lib.fwime_server_last_error(buf, 256)
+        return buf.value.decode(errors="replace")
 
-        def enqueue():
-            with torch.cuda.stream(stream):
-                if req.kind == "forward":
-                    ctx.forward(t["v"], t["w"], t["d"], sync=False)
-                    host_out.copy_(t["d"][0], non_blocking=True)
-                else:
-                    ctx.gradient(t["v"], t["w"], t["pt"], t["dobs"], t["g"], eps=req.eps, sync=False)
-                    host_out.copy_(t["g"], non_blocking=True)
-                act.event.record(stream)
+    def submit(self, m: _Marshalled) -> int:
+        t = ctypes.c_uint64(0)
+        rc = self._lib.fwime_submit(self._h, ctypes.byref(m.c), ctypes.byref(t))
+        if rc == self.fw.FWIME_ENOMEM:
+            raise ValueError(self._error())
+        if rc != self.fw.FWIME_OK:
+            raise self.fw.FwimeError(rc, "fwime_submit", self._error())
+        return int(t.value)
 
-        act.future = self.pool.submit(enqueue)
-        return act
+    def poll(self, ticket: int):
+        r = self.fw.ResultC()
+        rc = self._lib.fwime_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc != self.fw.FWIME_OK:
+            raise self.fw.FwimeError(rc, "fwime_poll")
+        return r if r.done else None
 
-    def _admit_forward_group(self, reqs: list, sizes: dict, now: float) -> list:
-        import paper_2206_02362_gb300 as fw
-        torch = self.torch
-        stream = torch.cuda.Stream(device=self.device)
-        acts, ctxs, vs, ws, ds = [], [], [], [], []
-        event = torch.cuda.Event()
-        with torch.cuda.stream(stream):
-            for req in reqs:
-                grid = fw.Grid(nz=req.nz, nx=req.nx, sponge=req.sponge, nt=req.nt, dt=req.dt, dx=req.dx, nh=req.nh)
-                geom = fw.Geometry(np.array([req.src[0]]), np.array([req.src[1]]), req.rec_iz, req.rec_ix)
-                t = {"v": torch.from_numpy(np.ascontiguousarray(req.v, dtype=np.float32)).pin_memory()
-                     .to(self.device, non_blocking=True),
-                     "w": torch.from_numpy(np.ascontiguousarray(req.w, dtype=np.float32)[None]).pin_memory()
-                     .to(self.device, non_blocking=True),
-                     "d": torch.empty((1, req.nt, len(req.rec_iz)), device=self.device)}
-                host_out = torch.empty((req.nt, len(req.rec_iz)), pin_memory=True)
-                ctx = fw.Context(grid, geom, stream=stream, shots_per_batch=1)
-                acts.append(_Active(req, ctx, stream, event, t, host_out, sizes[req.rid], now))
-                ctxs.append(ctx); vs.append(t["v"]); ws.append(t["w"]); ds.append(t["d"])
-
-        def enqueue():
-            with torch.cuda.stream(stream):
-                fw.forward_group(ctxs, vs, ws, ds, sync=False)
-                for a in acts:
-                    a.host_out.copy_(a.tensors["d"][0], non_blocking=True)
-                event.record(stream)
-
-        fut = self.pool.submit(enqueue)
-        for a in acts:
-            a.future = fut
-        return acts
-
-    def _finish(self, act: _Active, now: float) -> ShotResult:
-        act.ctx.sync()                       # already complete; reads the status word and the objective
-        r = ShotResult(act.req.rid, act.req.kind, act.req.arrival, act.admitted, now)
-        if act.req.kind == "forward":
-            r.data = act.host_out.numpy().copy()
-        else:
-            r.grad = act.host_out.numpy().copy()
-            r.objective = float(act.ctx._J.value)
-        act.ctx.close()
+    def wait(self, ticket: int):
+        r = self.fw.ResultC()
+        rc = self._lib.fwime_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc != self.fw.FWIME_OK:
+            raise self.fw.FwimeError(rc, "fwime_wait")
         return r
 
-    # ---------------------------------------------------------------- the loop
     def serve(self, requests: list[ShotRequest], realtime: bool = True) -> list[ShotResult]:
-        """Serves requests arriving at req.arrival seconds (realtime) or all at once; returns results in rid order."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        queue: collections.deque = collections.deque()
-        active: list[_Active] = []
-        used = 0
-        results = {}
-        sizes = {r.rid: request_bytes(r) for r in requests}
+        """Submits each request at req.arrival seconds (realtime) or all at once, collects every result;
+        returns the results in rid order."""
         for r in requests:
-            if sizes[r.rid] > self.budget:
-                raise ValueError(f"request {r.rid} needs {sizes[r.rid]} bytes, over the budget {self.budget}")
+            need = request_bytes(r)
+            if need > self.budget:
+                raise ValueError(f"request {r.rid} needs {need} bytes, over the budget {self.budget}")
+        marsh = {r.rid: _Marshalled(r) for r in requests}
+        pending = sorted(requests, key=lambda r: r.arrival)
+        inflight = {}                  # ticket -> (request, submit time)
+        results = {}
         t0 = time.perf_counter()
-        while pending or queue or active:
+        k = 0
+        while k < len(pending) or inflight:
             now = time.perf_counter() - t0
-            while pending and (not realtime or pending[0].arrival <= now):
-                req = pending.popleft()
+            while k < len(pending) and (not realtime or pending[k].arrival <= now):
+                req = pending[k]
+                k += 1
+                ts = time.perf_counter() - t0
                 if not realtime:
-                    req.arrival = now
-                queue.append(req)
-            # admission: FIFO, as memory and slots free up
-            admitted = []
-            while queue and len(active) + len(admitted) < self.max_active and \
-                    used + sizes[queue[0].rid] <= self.budget:
-                req = queue.popleft()
-                admitted.append(req)
-                used += sizes[req.rid]
-            fwd = [r for r in admitted if r.kind == "forward"] if self.group_forward else []
-            grouped = {r.rid for r in fwd} if len(fwd) > 1 else set()
-            if grouped:
-                active.extend(self._admit_forward_group(fwd, sizes, time.perf_counter() - t0))
-            for req in admitted:
-                if req.rid not in grouped:
-                    active.append(self._admit(req, sizes[req.rid], time.perf_counter() - t0))
-            # completion
-            still = []
-            for act in active:
-                if act.future.done() and act.event.query():
-                    act.future.result()
-                    results[act.req.rid] = self._finish(act, time.perf_counter() - t0)
-                    used -= act.nbytes
+                    req.arrival = ts
+                inflight[self.submit(marsh[req.rid])] = (req, ts)
+            for ticket in list(inflight):
+                res = self.poll(ticket)
+                if res is None:
+                    continue
+                req, ts = inflight.pop(ticket)
+                done = ts + res.latency_s          # the server's clock: completion of the copy to host memory
+                if res.status != self.fw.FWIME_OK:
+                    raise self.fw.FwimeError(res.status, f"request {req.rid}")
+                m = marsh[req.rid]
+                out = ShotResult(req.rid, req.kind, req.arrival, ts + res.queued_s, done)
+                if req.kind == "forward":
+                    out.data = m.t["d"][0].numpy().copy()
                 else:
-                    still.append(act)
-            active = still
-            if not (pending and pending[0].arrival <= time.perf_counter() - t0):
+                    out.grad = m.t["g"].numpy().copy()
+                    out.objective = float(res.objective)
+                results[req.rid] = out
+            if inflight and not (k < len(pending) and pending[k].arrival <= time.perf_counter() - t0):
                 time.sleep(2e-4)
-        return [results[k] for k in sorted(results)]
+        return [results[r] for r in sorted(results)]
 
     def close(self):
-        self.pool.shutdown(wait=True)
+        if self._h.value:
+            self._lib.fwime_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def summarize(results: list[ShotResult], wall: float | None = None) -> dict:

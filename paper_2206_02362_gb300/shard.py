@@ -24,3 +24,15 @@ def allreduce_model(tensor, group=None):
     if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
         dist.all_reduce(tensor, op=dist.ReduceOp.SUM, group=group)
     return tensor
+
+
+def rank_step(apply, nshot: int, world: int, rank: int, group=None):
+    """One data-parallel step of a model-space operator over `nshot` shots on `world` ranks: this rank
+    applies ``apply(start, stop)`` -- the operator (B~*, B*, T*, the gradient ...) over its contiguous
+    block of shots [start, stop) -- and the model-space output it returns (a torch tensor) is summed over
+    all ranks in place (world = 1: no exchange, whatever process group exists).  The same function drives
+    the GPU ranks (``apply`` calls libfwime on the rank's device) and the CPU tests (``apply`` calls the
+    oracle, gloo all-reduce)."""
+    start, stop = shard(nshot, world, rank)
+    out = apply(start, stop)
+    return allreduce_model(out, group) if world > 1 else out

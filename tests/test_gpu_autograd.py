@@ -1,7 +1,9 @@
 """The differentiable FWIME objective (Eq. 1 at fixed p~, gradient Eqs. 7-9):
-torch.autograd backward = B* r + T* r from the hand-written adjoint kernels,
-checked against the FP64 oracle gradient and against central finite
-differences of the objective along 10 random smooth model perturbations."""
+torch.autograd forward = the forward sweep alone, backward = B* r + T* r from
+the hand-written adjoint kernels, checked against the FP64 oracle gradient,
+against central finite differences of the objective along 10 random smooth
+model perturbations, and by kernel-family launch counts (no adjoint kernel in
+the forward pass)."""
 import numpy as np
 import pytest
 
@@ -88,6 +90,53 @@ def test_gradient_against_central_finite_differences(prob):
                 rels.append(abs(fd - an) / abs(an))
     assert max(errs) <= 1e-4, errs
     assert len(rels) >= 5 and max(rels) <= 2e-3, rels
+
+
+def test_forward_runs_no_adjoint_kernel_and_backward_matches_oracle(prob):
+    """Under requires_grad the forward pass runs the forward sweep only (the same stencil launches as
+    the objective alone, no imaging launch); backward runs the adjoint sweep from the kept state and
+    matches the oracle gradient, scaled by a non-scalar-shaped incoming gradient."""
+    p = prob
+    J_o, g_o = oracle.gradient(p.og, p.v0.astype(np.float64), p.ogeo, p.w.astype(np.float64),
+                               p.pt.astype(np.float64), p.dobs.astype(np.float64), eps=p.eps)
+    with fw.Context(p.grid, p.geom, segment=16, shots_per_batch=3, profile=1) as ctx:
+        w, pt, dobs = cu(p.w), cu(p.pt), cu(p.dobs)
+        ctx.objective(cu(p.v0), w, pt, dobs, eps=p.eps)
+        obj = ctx.profile_read(reset=True)
+        v = cu(p.v0).requires_grad_(True)
+        J = fwime_objective(ctx, v, w, pt, dobs, p.eps)
+        fwd = ctx.profile_read(reset=True)
+        assert fwd["prop"]["launches"] == obj["prop"]["launches"]
+        assert fwd["image"]["launches"] == 0
+        J.reshape(1).backward(torch.tensor([2.0], dtype=torch.float64, device="cuda"))
+        bwd = ctx.profile_read(reset=True)
+        assert ctx.get_option("background_reused") == 1      # started from the kept state
+        assert bwd["image"]["launches"] > 0
+        # the adjoint half recomputes 2 fields and runs 2 adjoint fields: 4 stencil launches per step
+        assert bwd["prop"]["launches"] == 4 * (p.nt - 1) * 2     # 2 batches of 3 and 1 shots
+        g = v.grad.double().cpu().numpy() / 2.0
+    assert abs(J.item() - J_o) <= 1e-5 * J_o
+    assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) <= 1e-4
+
+
+def test_backward_without_kept_state_recomputes(prob):
+    """gradient_backward on pointers the forward half did not see runs the whole gradient."""
+    p = prob
+    J_o, g_o = oracle.gradient(p.og, p.v0.astype(np.float64), p.ogeo, p.w.astype(np.float64),
+                               p.pt.astype(np.float64), p.dobs.astype(np.float64), eps=p.eps)
+    with fw.Context(p.grid, p.geom, segment=16) as ctx:
+        g = torch.zeros((p.nz, p.nx), device="cuda")
+        ctx.gradient_backward(cu(p.v0), cu(p.w), cu(p.pt), cu(p.dobs), g, eps=p.eps)
+        assert ctx.get_option("background_reused") == 0
+        g2 = g.clone()                       # accumulate onto values of the gradient's own size
+        v, w, pt, dobs = cu(p.v0), cu(p.w), cu(p.pt), cu(p.dobs)
+        J = ctx.gradient_forward(v, w, pt, dobs, eps=p.eps)
+        ctx.gradient_backward(v, w, pt, dobs, g2, eps=p.eps, accumulate=True)
+        assert ctx.get_option("background_reused") == 1
+    g, g2 = g.double().cpu().numpy(), g2.double().cpu().numpy()
+    assert abs(J - J_o) <= 1e-5 * J_o
+    assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) <= 1e-4
+    assert np.linalg.norm(g2 - 2.0 * g_o) / np.linalg.norm(2.0 * g_o) <= 1e-4
 
 
 def test_no_grad_path_runs_forward_sweep_only(prob):

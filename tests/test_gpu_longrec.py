@@ -19,7 +19,9 @@ range) until the FP64 oracle finishes in minutes:
   segments of 50 steps (every segment recomputed from its checkpoint), and the
   gradient of one shot.
 
-Bars: rel. L2 <= 1e-4 on traces, images and gradients, objective within 1e-5.
+Bars: rel. L2 <= 1e-4 on traces, images (also per offset plane) and gradients; the
+objective within the change that a 1e-4 relative error on the predicted traces can
+make to it (``objective_bound``).
 The oracle's jobs start on host threads when the module's fixture is first
 used (ctypes releases the GIL, OpenMP runs each job's shots in parallel) and
 run while the GPU computes; jobs are admitted by an estimate of their FP64
@@ -206,6 +208,16 @@ def plane_errors(img, ref):
     return [rel(img[i], ref[i]) for i in range(ref.shape[0])]
 
 
+def objective_bound(c, J_ref, dobs, nshot=None):
+    """Largest |Phi_gpu - Phi_oracle| the trace contract allows: Phi = 1/2 ||r||^2 + (DSO term), r = pred -
+    d_obs, and a relative error of at most TOL on the predicted traces moves ||r|| by at most
+    TOL ||pred|| <= TOL (||r|| + ||d_obs||), hence Phi by at most ||r|| TOL (||r|| + ||d_obs||) to first order."""
+    nz, nx, W, nt, dt, dx, nh = c["grid"]
+    og = oracle.Grid(nz=nz, nx=nx, W=W, nt=nt, dt=dt, dx=dx, nh=nh)
+    r = np.sqrt(2.0 * (J_ref - oracle.dso_penalty(og, f32(c["pt"]), c["eps"])))
+    return TOL * r * (r + np.linalg.norm(dobs))
+
+
 def test_marmousi2_full_record_born_ext_and_adjoint(cases):
     c = cases["marmousi"]
     ctx, g = fw_setup(c, reuse_background=1)
@@ -237,7 +249,7 @@ def test_north_sea_full_record_gradient(cases):
     J_ref, g_ref = c["gradient"].result()
     e_g = rel(grad.double().cpu().numpy(), g_ref)
     print(f"north sea nt 5000: objective {abs(J - J_ref) / abs(J_ref):.3e}, gradient {e_g:.3e}")
-    assert abs(J - J_ref) <= 1e-5 * abs(J_ref)
+    assert abs(J - J_ref) <= objective_bound(c, J_ref, c["d_in"])
     assert e_g <= TOL
 
 
@@ -277,5 +289,5 @@ def test_salt_full_record_gradient(cases):
     J_ref, g_ref = c["gradient1"].result()
     e_g = rel(grad.double().cpu().numpy(), g_ref)
     print(f"salt nt 8000: objective {abs(J - J_ref) / abs(J_ref):.3e}, gradient {e_g:.3e}")
-    assert abs(J - J_ref) <= 1e-5 * abs(J_ref)
+    assert abs(J - J_ref) <= objective_bound(c, J_ref, c["dobs1"])
     assert e_g <= TOL

@@ -81,3 +81,23 @@ def test_autograd_through_the_spline(ctx):
     a = torch.zeros_like(m)
     ctx.spline(zs, xs, wgt, a, adjoint=True)
     assert torch.allclose(m.grad, a, rtol=1e-6, atol=1e-6)
+
+
+def test_spline_refinement_matches_oracle_and_reproduces_the_coarse_model(ctx):
+    """Model-space multiscale step: a 0.2 km x 0.45 km coarse grid refined by halving its spacing twice.
+    The carried-over model equals the oracle's, and S on the fine nodes reproduces S on the coarse nodes
+    on the finite-difference grid (every coarse node is a fine node)."""
+    zc, xc = np.arange(0, 601, 200.0), np.arange(0, 2021, 450.0)
+    zf, xf = np.arange(0, 601, 50.0), np.arange(0, 2021, 112.5)
+    rng = np.random.default_rng(synth.SEED0 + 601)
+    mc = (2000.0 + 300.0 * rng.standard_normal((len(zc), len(xc)))).astype(np.float32)
+    mf = torch.zeros((len(zf), len(xf)), device="cuda")
+    ctx.spline_refine(zc, xc, torch.from_numpy(mc).cuda(), zf, xf, mf)
+    ref = oracle.spline_refine(zc.astype(np.float32), xc.astype(np.float32), mc.astype(np.float64),
+                               zf.astype(np.float32), xf.astype(np.float32))
+    assert np.abs(mf.double().cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+    assert torch.equal(mf[::4, ::4], torch.from_numpy(mc).cuda())     # shared nodes keep their values
+    vf, vc = torch.zeros((NZ, NX), device="cuda"), torch.zeros((NZ, NX), device="cuda")
+    ctx.spline(zf, xf, mf, vf)
+    ctx.spline(zc, xc, torch.from_numpy(mc).cuda(), vc)
+    assert (vf - vc).abs().max().item() <= 1e-6 * vc.abs().max().item()

@@ -50,3 +50,52 @@ def test_adjoint_dot_product():
     lhs = np.sum(oracle.spline(zs, xs, nz, nx, dz, dx, m) * g)
     rhs = np.sum(m * oracle.spline_adj(zs, xs, nz, nx, dz, dx, g))
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def nested_grids():
+    """A coarse node set (0.2 km x 1 km, as the paper's first Marmousi2 spline grid), its refinement by
+    halving the spacing twice, and a finite-difference grid of 10 m."""
+    zc = np.arange(0.0, 1401.0, 200.0)
+    xc = np.arange(0.0, 6001.0, 1000.0)
+    zm, xm = np.arange(0.0, 1401.0, 100.0), np.arange(0.0, 6001.0, 500.0)
+    zf, xf = np.arange(0.0, 1401.0, 50.0), np.arange(0.0, 6001.0, 250.0)
+    return zc, xc, zm, xm, zf, xf
+
+
+def test_refinement_reproduces_the_coarse_model_exactly():
+    """Coarse nodes that are also fine nodes: S on the fine nodes applied to the carried-over model equals S
+    on the coarse nodes (a piecewise-linear function on a partition is piecewise linear on any refinement),
+    also beyond the grid's end nodes (constant extension)."""
+    zc, xc, zm, xm, zf, xf = nested_grids()
+    rng = np.random.default_rng(42)
+    mc = 1500.0 + 3000.0 * rng.random((len(zc), len(xc)))
+    nz, nx, dz, dx = 150, 620, 10.0, 10.0                    # the FD grid reaches past the last nodes
+    for z2, x2 in ((zm, xm), (zf, xf), (zf, xm)):
+        mf = oracle.spline_refine(zc, xc, mc, z2, x2)
+        a = oracle.spline(z2, x2, nz, nx, dz, dx, mf)
+        b = oracle.spline(zc, xc, nz, nx, dz, dx, mc)
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    # the fine nodes that coincide with coarse ones keep their values exactly
+    mf = oracle.spline_refine(zc, xc, mc, zf, xf)
+    assert np.array_equal(mf[::4, ::4], mc)
+
+
+def test_refinement_composes_and_is_the_identity_on_the_same_nodes():
+    zc, xc, zm, xm, zf, xf = nested_grids()
+    rng = np.random.default_rng(7)
+    mc = rng.standard_normal((len(zc), len(xc)))
+    assert np.array_equal(oracle.spline_refine(zc, xc, mc, zc, xc), mc)
+    two = oracle.spline_refine(zm, xm, oracle.spline_refine(zc, xc, mc, zm, xm), zf, xf)
+    one = oracle.spline_refine(zc, xc, mc, zf, xf)
+    assert np.abs(two - one).max() <= 1e-12 * np.abs(one).max()
+
+
+def test_refinement_of_a_linear_model_samples_it():
+    zc, xc, zm, xm, zf, xf = nested_grids()
+    lin = lambda z, x: 1500.0 + 1.5 * z[:, None] + 0.25 * x[None, :]  # noqa: E731
+    mf = oracle.spline_refine(zc, xc, lin(zc, xc), zf, xf)
+    assert np.abs(mf - lin(zf, xf)).max() <= 1e-9
+    # a coarse grid that is not a subset: the transfer still samples the coarse spline exactly
+    zo, xo = zf + 17.0, xf + 33.0
+    mo = oracle.spline_refine(zc, xc, lin(zc, xc), zo[:-1], xo[:-1])
+    assert np.abs(mo - lin(zo[:-1], xo[:-1])).max() <= 1e-9

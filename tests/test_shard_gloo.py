@@ -1,7 +1,7 @@
-"""Multi-rank shot sharding on CPU: world_size 2 over gloo.  Each rank applies the
-(oracle) extended imaging operator to its block of shots; the sum all-reduce of
-the images must equal the single-process result over all shots.  The same host
-logic (shard + all-reduce of model-space outputs) drives the GPU ranks."""
+"""Multi-rank shot sharding on CPU: world_size 2 over gloo.  Each rank runs
+``shard.rank_step`` -- the function bench.py's GPU ranks run -- with the (oracle)
+extended imaging operator on its block of shots; the sum all-reduce of the images
+must equal the single-process result over all shots."""
 import os
 import socket
 
@@ -38,18 +38,21 @@ def _worker(rank, world, port, q):
 
     import oracle
     import synth
-    from paper_2206_02362_gb300.shard import allreduce_model, shard
+    from paper_2206_02362_gb300.shard import rank_step
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         g, v, geo, w, d = _problem()
-        a, b = shard(geo.nshot, world, rank)
-        sub = oracle.Geometry(geo.src_iz[a:b], geo.src_ix[a:b], geo.rec_iz, geo.rec_ix)
-        img = oracle.born_ext_adj(g, v, sub, w[a:b], d[a:b], nthreads=1)
-        t = torch.from_numpy(img)
-        allreduce_model(t)
-        q.put((rank, t.numpy()))
+        blocks = []
+
+        def apply(a, b):                 # the rank's operator call: the oracle on its shot block
+            blocks.append((a, b))
+            sub = oracle.Geometry(geo.src_iz[a:b], geo.src_ix[a:b], geo.rec_iz, geo.rec_ix)
+            return torch.from_numpy(oracle.born_ext_adj(g, v, sub, w[a:b], d[a:b], nthreads=1))
+
+        t = rank_step(apply, geo.nshot, world, rank)
+        q.put((rank, t.numpy(), blocks))
     finally:
         dist.destroy_process_group()
 
@@ -76,11 +79,14 @@ def test_two_rank_gloo_image_sum_matches_single_process():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    res = dict(q.get(timeout=300) for _ in procs)
+    got = [q.get(timeout=300) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
+    res = {r: img for r, img, _ in got}
+    blocks = {r: b for r, _, b in got}
     g, v, geo, w, d = _problem()
     full = oracle.born_ext_adj(g, v, geo, w, d, nthreads=1)
+    assert blocks == {0: [(0, 3)], 1: [(3, 5)]}        # contiguous shot blocks, each shot on one rank
     for r in (0, 1):
         assert np.allclose(res[r], full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
