@@ -53,10 +53,13 @@ def parse():
     ap.add_argument("--no-grad", action="store_true", help="skip the FWIME-gradient batched-vs-plain section")
     ap.add_argument("--no-tune", action="store_true", help="skip the stencil autotuner (automatic chunking)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix section")
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-active", type=int, default=16, help="requests in flight at most")
     ap.add_argument("--grad-shots", type=int, default=120)
     ap.add_argument("--no-tlag", action="store_true", help="skip the time-lag extension section")
+    ap.add_argument("--no-salt", action="store_true", help="skip the Salt-shaped batched-gradient section")
+    ap.add_argument("--salt-shots", type=int, default=4)
     ap.add_argument("--no-reuse", action="store_true",
                     help="B~* runs its own checkpointing sweep instead of starting from the background states "
                          "kept by the B~ of the same step")
@@ -209,41 +212,42 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def serving_section(nreq: int, rate: float):
+def serving_section(nreq: int, rate: float, active: int = 16):
     """Serving mix: Poisson arrivals at `rate`/s of forward and FWIME-gradient shot requests on grids
-    200-600 x 400-2000 at 10 m, nt 2000-6000, nh in {1, 11, 31}, served with memory admission and
-    overlap (continuous batching); p50/p99 latency and shots/s.  The plain comparison serves the
-    same requests one at a time, one shot per launch."""
+    200-600 x 400-2000 at 10 m, nt 2000-6000, nh in {1, 11, 31}, served through libfwime's request
+    server (memory admission, up to `active` requests in flight, one stream each, grouped forward
+    launches); p50/p99 latency and shots/s, timed from the first submission (the requests' host
+    buffers are pinned before).  A steady-state run offers the same mix at 0.7 x the measured
+    throughput.  The plain comparison serves a subset of the same requests one at a time, one shot
+    per launch, host-driven steps."""
     from paper_2206_02362_gb300 import serve
     reqs = [serve.from_synth(r) for r in synth.serving_mix(nreq=nreq, rate=rate)]
-    srv = serve.Server(max_active=16)
+    srv = serve.Server(max_active=active)
     try:
         warm = [serve.from_synth(r) for r in synth.serving_mix(nreq=4, rate=rate, seed=synth.SEED0 + 99)]
         srv.serve(warm, realtime=False)
-        t0 = time.perf_counter()
         res = srv.serve(reqs, realtime=True)
-        wall = time.perf_counter() - t0
+        s1 = serve.summarize(res, srv.last_wall)
         out = {"workload": f"serving mix, {nreq} requests, Poisson {rate}/s (overload: arrivals outpace the GPU)",
-               "max_in_flight": 16, **serve.summarize(res, wall)}
+               "max_in_flight": active, **s1,
+               "enqueue_share": s1["enqueue_s_total"] / (s1["span_s"] * min(8, active))}
         # steady state: the same mix arriving at 0.7x the throughput just measured
         rate2 = 0.7 * out["shots_per_s"]
         reqs2 = [serve.from_synth(r) for r in synth.serving_mix(nreq=max(20, nreq // 2), rate=rate2,
                                                                  seed=synth.SEED0 + 98)]
-        t0 = time.perf_counter()
         res2 = srv.serve(reqs2, realtime=True)
-        s2 = serve.summarize(res2, time.perf_counter() - t0)
+        s2 = serve.summarize(res2, srv.last_wall)
         out["steady_state"] = {"rate_per_s": rate2, "requests": len(reqs2), "p50_s": s2["p50_s"],
                                "p99_s": s2["p99_s"], "shots_per_s": s2["shots_per_s"]}
     finally:
         srv.close()
     out["kinds"] = {k: sum(1 for r in reqs if r.kind == k) for k in ("forward", "gradient")}
-    # plain: the same requests alone, one after the other, one shot per launch (a subset, scaled)
+    # plain: the same requests alone, one after the other, one shot per launch (a subset)
     sub = reqs[: max(4, nreq // 8)]
     plain = serve.Server(max_active=1, plain=True)
     try:
-        t0 = time.perf_counter()
         plain.serve(sub, realtime=False)
-        tp = time.perf_counter() - t0
+        tp = plain.last_wall
     finally:
         plain.close()
     out["plain_shots_per_s"] = len(sub) / tp
@@ -288,8 +292,10 @@ def time_lag_section(fw, torch, dev, wl, nh=21, lag=2):
 
 def gradient_section(fw, torch, dev, nshot):
     """FWIME gradient (objective + B* r + T* r, checkpointed) on the North-Sea-shaped workload,
-    400 x 1600 at 12.5 m, nt 5000, nh 31: all shots batched vs the plain path (one shot per
-    launch, host-driven steps) on 2 shots.  Shots/s of each and their ratio."""
+    400 x 1600 at 12.5 m, nt 5000, nh 31: all shots batched, the call captured once in a CUDA graph
+    and replayed on its own stream (timed), vs the plain path (one shot per launch, host-driven steps)
+    on 2 shots.  Shots/s of each and their ratio; kernel-family shares from one more call in profile
+    mode (an event pair around every launch, no graph)."""
     wl, v0 = synth.north_sea(nshot=nshot)
     grid = fw.Grid(nz=wl.nz, nx=wl.nx, sponge=wl.W, nt=wl.nt, dt=wl.dt, dx=wl.dx, nh=wl.nh)
     rng = np.random.default_rng(synth.SEED0 + 21)
@@ -300,22 +306,29 @@ def gradient_section(fw, torch, dev, nshot):
     g = torch.zeros((wl.nz, wl.nx), device=dev)
     geom = fw.Geometry(wl.src_iz, wl.src_ix, wl.rec_iz, wl.rec_ix)
     out = {"workload": wl.name, "nshot": wl.nshot, "segment": "auto"}
-    with fw.Context(grid, geom, profile=1) as c:
-        c.gradient(v, w, pt, dobs, g, eps=1e-3)              # warm-up (workspace)
-        c.profile_read(reset=True)
+    stream = torch.cuda.Stream(device=dev)
+    with fw.Context(grid, geom, stream=stream, graph=1) as c:
+        c.gradient(v, w, pt, dobs, g, eps=1e-3)              # warm-up: workspace, capture, first replay
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        c.gradient(v, w, pt, dobs, g, eps=1e-3, sync=False)
-        e1.record()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J = c.gradient(v, w, pt, dobs, g, eps=1e-3, sync=False)
+        e1.record(stream)
         c.sync()
         tb = e0.elapsed_time(e1) * 1e-3
         out["batched_shots_per_s"] = wl.nshot / tb
         out["batched_seconds"] = tb
         out["launches"] = c.launches
+        out["shots_per_batch"] = c.get_option("batch_used")
+        out["graph_replay"] = True
+        c.set_option("graph", 0)
+        c.set_option("profile", 1)
+        c.gradient(v, w, pt, dobs, g, eps=1e-3)
         prof = c.profile_read(reset=True)
         kms = sum(p["ms"] for p in prof.values())
         out["time_share"] = {k: round(p["ms"] / kms, 4) for k, p in prof.items()} if kms else None
         out["family_gbs"] = {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items() if p["ms"] > 0}
+        out["profiled_seconds"] = kms * 1e-3
     nps = 2
     geom2 = fw.Geometry(wl.src_iz[:nps], wl.src_ix[:nps], wl.rec_iz, wl.rec_ix)
     with fw.Context(grid, geom2, plain=1) as c:
@@ -329,6 +342,49 @@ def gradient_section(fw, torch, dev, nshot):
     out["batched_vs_plain"] = out["batched_shots_per_s"] / out["plain_shots_per_s"]
     NZ, NX = wl.padded
     out["useful_gupd_s"] = 6.0 * wl.nshot * NZ * NX * (wl.nt - 1) / tb / 1e9   # 6 propagations (Eq. 11)
+    out["objective"] = J
+    return out
+
+
+def salt_section(fw, torch, dev, nshot):
+    """The batched FWIME gradient on the Salt-shaped workload (1200 x 5000 at 6.25 m, nt 8000,
+    dt 0.5 ms, nh 41), where one shot's source-wavefield history (~214 GB padded) exceeds HBM, so the
+    adjoint sweep recomputes every segment from its checkpoints: a subset of `nshot` shots in one
+    batch, timed in profile mode (shares and GB/s of each kernel family) after a warm-up call."""
+    wl = synth.salt(nshot=nshot)
+    grid = fw.Grid(nz=wl.nz, nx=wl.nx, sponge=wl.W, nt=wl.nt, dt=wl.dt, dx=wl.dx, nh=wl.nh)
+    rng = np.random.default_rng(synth.SEED0 + 41)
+    NZ, NX = wl.padded
+    v = torch.from_numpy(wl.v).to(dev)
+    # a smooth initial model: the true one with its salt body and feeder stem removed (sediment trend)
+    v0 = torch.from_numpy(np.where(wl.v == 4500.0, np.float32(3000.0), wl.v)).to(dev)
+    w = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(wl.w.astype(np.float32), (wl.nshot, wl.nt)))).to(dev)
+    pt = torch.from_numpy((1e-3 * rng.standard_normal((wl.nh, wl.nz, wl.nx))).astype(np.float32)).to(dev)
+    geom = fw.Geometry(wl.src_iz, wl.src_ix, wl.rec_iz, wl.rec_ix)
+    dobs = torch.zeros((wl.nshot, wl.nt, wl.nrec), device=dev)
+    g = torch.zeros((wl.nz, wl.nx), device=dev)
+    out = {"workload": wl.name + f" (subset: {wl.nshot} of 400 shots)", "nshot": wl.nshot, "nt": wl.nt,
+           "nh": wl.nh, "history_gb_per_shot": round(4.0 * NZ * NX * wl.nt / 1e9, 1)}
+    with fw.Context(grid, geom, profile=1) as c:
+        c.forward(v, w, dobs)                                   # observed data of the salt model
+        c.gradient(v0, w, pt, dobs, g, eps=1e-3)                # warm-up (workspace)
+        c.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        c.gradient(v0, w, pt, dobs, g, eps=1e-3, sync=False)
+        e1.record()
+        c.sync()
+        t = e0.elapsed_time(e1) * 1e-3
+        prof = c.profile_read(reset=True)
+        out["segment"] = "auto"
+        out["workspace_gb"] = round(c.get_option("workspace") / 1e9, 1)
+    kms = sum(p["ms"] for p in prof.values())
+    out["seconds"] = t
+    out["shots_per_s"] = wl.nshot / t
+    out["useful_gupd_s"] = 6.0 * wl.nshot * NZ * NX * (wl.nt - 1) / t / 1e9
+    out["time_share"] = {k: round(p["ms"] / kms, 4) for k, p in prof.items()} if kms else None
+    out["family_gbs"] = {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items() if p["ms"] > 0}
     return out
 
 
@@ -524,7 +580,7 @@ def main():
         ctx.born_ext(arr(vh), arr(wh), arr(ph), arr(dh))     # warm (staging allocation)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ne = 1
+        ne = 3
         for _ in range(ne):
             ctx.born_ext(arr(vh), arr(wh), arr(ph), arr(dh))
             ctx.born_ext_adj(arr(vh), arr(wh), arr(dh), arr(ih))
@@ -546,9 +602,12 @@ def main():
         line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots)
     if not args.no_tlag and rank == 0 and world == 1:
         line["time_lag"] = time_lag_section(fw, torch, dev, wl)
+    # Salt-shaped batched gradient with checkpoint/recompute (a shot subset)
+    if not args.no_salt and rank == 0 and world == 1:
+        line["salt"] = salt_section(fw, torch, dev, args.salt_shots)
     # serving mix: continuous batching with memory admission, p50/p99 (Poisson arrivals)
     if not args.no_serve and rank == 0:
-        line["serving"] = serving_section(args.serve_requests, args.serve_rate)
+        line["serving"] = serving_section(args.serve_requests, args.serve_rate, args.serve_active)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -112,6 +112,8 @@ enum {
                                        the odd mirror of the 4 rows below after every step (forward and
                                        adjoint); receivers on the surface row record 0.  Not available in
                                        fwime_forward_group. */
+    FWIME_OPT_BATCH_USED = 15       /* read-only: shots per batch the last operator call planned (the
+                                       planner splits the shots into equal batches that fit) */
 };
 
 /* Kernel families, for fwime_profile_read. */
@@ -305,6 +307,7 @@ typedef struct {
     double objective;              /* gradient requests: Phi */
     double queued_s;               /* submission to admission, seconds */
     double latency_s;              /* submission to completion seen by the server, seconds */
+    double enqueue_s;              /* host time spent enqueuing the request's launches (its launch group's) */
 } fwime_result;
 
 /* memory_budget: device bytes the admitted requests may hold together (0 = 80 % of the free memory now);

@@ -31,6 +31,7 @@ OPT_REUSE_BACKGROUND = 10
 OPT_BACKGROUND_REUSED = 11
 OPT_TIME_LAG = 12
 OPT_FREE_SURFACE = 13
+OPT_BATCH_USED = 15
 K_PROP, K_SCATTER, K_IMAGE, K_POINTS, K_OTHER = range(5)
 KERNEL_NAMES = ("prop", "scatter", "image", "points", "other")
 (OP_FORWARD, OP_BORN, OP_BORN_ADJ, OP_BORN_EXT, OP_BORN_EXT_ADJ, OP_TOMO, OP_TOMO_ADJ,
@@ -76,7 +77,7 @@ class RequestC(ctypes.Structure):
 
 class ResultC(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("objective", ctypes.c_double),
-                ("queued_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+                ("queued_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("enqueue_s", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -261,7 +262,7 @@ class Context:
 
     def get_option(self, name) -> int:
         opt = {**self._OPTS, "launches": OPT_LAUNCHES, "workspace": OPT_WORKSPACE,
-               "background_reused": OPT_BACKGROUND_REUSED}[name] \
+               "background_reused": OPT_BACKGROUND_REUSED, "batch_used": OPT_BATCH_USED}[name] \
             if isinstance(name, str) else int(name)
         v = ctypes.c_longlong(0)
         self._check(self._lib.fwime_get_option(self._h, opt, ctypes.byref(v)), "fwime_get_option")

@@ -80,6 +80,7 @@ struct fwime_ctx {
     } gs;
     bool bg_used = false;           // the last call started from the cache
     long long launches = 0;
+    int last_S = 0;                 // shots per batch the last planned operator call used
     // persistent device memory
     int *d_src_off = nullptr, *d_rec_off = nullptr, *d_status = nullptr;
     double *d_J = nullptr, *d_part = nullptr, *h_J = nullptr;
@@ -344,8 +345,14 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
     else {
         if (fixed + per > budget) S = 1;
         else S = (int)std::min<size_t>((size_t)x->nshot, (budget - fixed) / per);
+        // as many batches as memory forces, of equal size: a short last batch runs its launches at a
+        // fraction of the work for the same per-launch overheads
+        S = std::max(S, 1);
+        const int nb = (x->nshot + S - 1) / S;
+        S = (x->nshot + nb - 1) / nb;
     }
     w.S = std::max(S, 1);
+    x->last_S = w.S;
     const size_t need = fixed + per * (size_t)w.S + 4096;
     if (x->max_ws && need > x->max_ws)
         return fail(x, FWIME_ENOMEM, "operator needs %zu bytes for S=%d, K=%d; budget %zu", need, w.S, w.K, x->max_ws);
@@ -482,9 +489,16 @@ static void init_run(fwime_ctx *x, Run &r, int S)
     a.zs_lo = x->o; a.zs_hi = x->o + x->g.nz;
 }
 
+// Receivers of a stencil launch's input field, recorded by the launch itself: row d of the data (=, or +=).
+struct RecTo {
+    float *d = nullptr;
+    int acc = 0;
+};
+
 static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out, float *d2, const float *wsrc,
                 int src_shot0, const float *f0 = nullptr, float a0 = 0.f, const float *f1 = nullptr, float a1 = 0.f,
-                const float *f2 = nullptr, float a2 = 0.f, const float *coef = nullptr, const float *fc = nullptr)
+                const float *f2 = nullptr, float a2 = 0.f, const float *coef = nullptr, const float *fc = nullptr,
+                RecTo rec = RecTo{})
 {
     fwime_ctx *x = r.x;
     PropArgs a = r.base;
@@ -496,12 +510,18 @@ static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out,
         a.src_stride = x->g.nt;
     }
     a.f0 = f0; a.a0 = a0; a.f1 = f1; a.a1 = a1; a.f2 = f2; a.a2 = a2; a.coef = coef; a.fc = fc;
+    if (rec.d) {
+        a.rec_off = x->d_rec_off; a.rec_d = rec.d; a.rec_dstride = (long long)x->g.nt * x->nrec;
+        a.nrec = x->nrec; a.rec_acc = rec.acc;
+    }
     // compulsory bytes: per shot-point read q^n, q^{n-1}, write q^{n+1}, and per point once per launch
     // the shared c, over the padded grid; D2t out and the local source fields (and coef) over the
     // physical rows only (zero elsewhere, not needed there)
     const double pts = (double)x->NZ * x->NX, spts = (double)x->g.nz * x->NX;
     const double srcb = (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) + (fc ? 4 : 0);
-    LAUNCH(FWIME_K_PROP, pts * (Sb * 12.0 + 4.0) + spts * (Sb * srcb + (coef ? 4.0 : 0.0)), launch_prop(a, Sb, x->st));
+    const double recb = rec.d ? (double)Sb * x->nrec * (rec.acc ? 12.0 : 8.0) : 0.0;
+    LAUNCH(FWIME_K_PROP, pts * (Sb * 12.0 + 4.0) + spts * (Sb * srcb + (coef ? 4.0 : 0.0)) + recb,
+           launch_prop(a, Sb, x->st));
     if (x->opt_fs)
         LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * (d2 ? 44.0 : 40.0),
                launch_free_surface(out, d2, Sb, x->P, x->NXP, x->o, x->st));
@@ -703,11 +723,13 @@ static int run_forward(fwime_ctx *x, Run &r, const float *v, const float *w, flo
         for (int i = 0; i < 2; ++i) TRY(zero(x, r.w.f[i], sizeof(float) * Sb * x->P));
         float *db = d + s0 * nd;
         TRY(zero(x, db, sizeof(float) * Sb * nd));
+        // the launch of step n records its input q^n; the last sample q^{nt-1} is recorded after the loop
         for (int n = 0; n + 1 < nt; ++n) {
-            TRY(prop(r, Sb, cur, prv, prv, nullptr, w + (size_t)s0 * nt + n, s0));
-            TRY(record(r, Sb, prv, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+            TRY(prop(r, Sb, cur, prv, prv, nullptr, w + (size_t)s0 * nt + n, s0, nullptr, 0.f, nullptr, 0.f, nullptr,
+                     0.f, nullptr, nullptr, RecTo{db + (size_t)n * x->nrec, 0}));
             std::swap(cur, prv);
         }
+        TRY(record(r, Sb, cur, nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -731,11 +753,12 @@ static int run_born(fwime_ctx *x, Run &r, const float *v, const float *w, const 
                 TRY(copyf(x, bg_slot(x, n / r.w.K, 1, s0), p0, (size_t)Sb * x->P));
             }
             TRY(prop(r, Sb, c0, p0, p0, D, w + (size_t)s0 * nt + n, s0));
-            TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, r.w.coef, D));
-            TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+            TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, r.w.coef, D,
+                     RecTo{db + (size_t)n * x->nrec, 0}));
             std::swap(c0, p0);
             std::swap(c1, p1);
         }
+        TRY(record(r, Sb, c1, nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -770,11 +793,12 @@ static int run_born_ext(fwime_ctx *x, Run &r, const float *v, const float *w, co
             }
             TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Dr, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
             for (int n = n0; n < n1; ++n) {
-                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
-                TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0.f, nullptr, 0.f,
+                         nullptr, nullptr, RecTo{db + (size_t)n * x->nrec, 0}));
                 std::swap(c1, p1);
             }
         }
+        TRY(record(r, Sb, c1, nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -883,11 +907,12 @@ static int run_born_tlag(fwime_ctx *x, Run &r, const float *w, const float *pt, 
             TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Dr, SP, RD, 0), ringref(Er, SP, 0, 0),
                             ringref(nullptr, 0, 0, 0), nullptr));
             for (int n = n0; n < n1; ++n) {
-                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
-                TRY(record(r, Sb, p1, nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                TRY(prop(r, Sb, c1, p1, p1, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0.f, nullptr, 0.f,
+                         nullptr, nullptr, RecTo{db + (size_t)n * x->nrec, 0}));
                 std::swap(c1, p1);
             }
         }
+        TRY(record(r, Sb, c1, nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -1009,11 +1034,11 @@ static int run_tomo_tlag(fwime_ctx *x, Run &r, const float *v, const float *w, c
             TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Dq0r, SP, RD, 0), er, none, nullptr, r.w.W, 1, 1));
             for (int n = n0; n < n1; ++n) {   // tomographic wavefield
                 TRY(prop(r, Sb, f[6], f[7], f[7], nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0, nullptr, 0,
-                         r.w.coef, Dsr + (n - n0) * SP));
-                TRY(record(r, Sb, f[7], nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                         r.w.coef, Dsr + (n - n0) * SP, RecTo{db + (size_t)n * x->nrec, 0}));
                 std::swap(f[6], f[7]);
             }
         }
+        TRY(record(r, Sb, f[6], nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -1203,11 +1228,11 @@ static int run_tomo(fwime_ctx *x, Run &r, const float *v, const float *w, const 
             TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0d, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 1));
             for (int n = n0; n < n1; ++n) {   // tomographic wavefield
                 TRY(prop(r, Sb, f[6], f[7], f[7], nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0, nullptr, 0,
-                         r.w.coef, Dsr + (n - n0) * SP));
-                TRY(record(r, Sb, f[7], nullptr, db + (size_t)(n + 1) * x->nrec, 0));
+                         r.w.coef, Dsr + (n - n0) * SP, RecTo{db + (size_t)n * x->nrec, 0}));
                 std::swap(f[6], f[7]);
             }
         }
+        TRY(record(r, Sb, f[6], nullptr, db + (size_t)(nt - 1) * x->nrec, 0));
     }
     return FWIME_OK;
 }
@@ -1280,19 +1305,22 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
                 }
                 if (!grad && j == nseg - 1) break;
                 const int n0 = j * K, n1 = std::min(n0 + K, nt - 1), kk = n1 - n0;
+                // with the gradient, the launch of step n adds its input (q0^n, then the scattered field's)
+                // to the prediction's row n (zeroed above; a + b is exact in either order of the two)
                 for (int n = n0; n < n1; ++n) {
-                    TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0));
-                    if (grad) TRY(record(r, Sb, q0p, nullptr, pred + (size_t)(n + 1) * x->nrec, 0));
+                    TRY(prop(r, Sb, q0c, q0p, q0p, D0r + (n - n0) * SP, ws + n, s0, nullptr, 0.f, nullptr, 0.f,
+                             nullptr, 0.f, nullptr, nullptr, RecTo{grad ? pred + (size_t)n * x->nrec : nullptr, 1}));
                     std::swap(q0c, q0p);
                 }
                 TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(D0r, SP, 0, 0), ringref(Er, SP, 0, 0), +1, 0));
                 for (int n = n0; n < n1; ++n) {
-                    TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f));
-                    if (grad) TRY(record(r, Sb, qsp, nullptr, pred + (size_t)(n + 1) * x->nrec, 1));
+                    TRY(prop(r, Sb, qsc, qsp, qsp, nullptr, nullptr, 0, Er + (n - n0) * SP, 1.f, nullptr, 0.f, nullptr,
+                             0.f, nullptr, nullptr, RecTo{grad ? pred + (size_t)n * x->nrec : nullptr, 1}));
                     std::swap(qsc, qsp);
                 }
             }
-            if (grad) {
+            if (grad) {   // the last sample of both fields
+                TRY(record(r, Sb, q0c, qsc, pred + (size_t)(nt - 1) * x->nrec, 1));
                 LAUNCH(FWIME_K_OTHER, 12.0 * Sb * nd,
                        launch_residual(pred, d + s0 * nd, pred, (long long)Sb * nd, x->d_part, nred, x->st));
                 LAUNCH(FWIME_K_OTHER, 8.0 * nred, launch_sum_partials(x->d_part, nred, x->d_J, 1, 1.0, x->st));
@@ -1686,6 +1714,7 @@ int fwime_get_option(fwime_ctx *x, int option, long long *value)
     case FWIME_OPT_BACKGROUND_REUSED: *value = x->bg_used; return FWIME_OK;
     case FWIME_OPT_TIME_LAG: *value = x->opt_tlag; return FWIME_OK;
     case FWIME_OPT_FREE_SURFACE: *value = x->opt_fs; return FWIME_OK;
+    case FWIME_OPT_BATCH_USED: *value = x->last_S; return FWIME_OK;
     }
     return fail(x, FWIME_EINVAL, "bad option %d", option);
 }

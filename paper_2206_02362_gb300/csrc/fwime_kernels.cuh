@@ -66,6 +66,13 @@ struct PropArgs {
     // imaging kernels, read physical rows only)
     int zs_lo, zs_hi;
     int naux_max;                  // rows per aux stage (set by launch_prop)
+    // optional receiver recording of the INPUT field: d[s * rec_dstride + r] (=, or += with rec_acc)
+    // = cur[s * P + rec_off[r]] for r < nrec, done by the first CTA of every shot (cur is complete
+    // before the launch, so any CTA may read it)
+    const int *rec_off;
+    float *rec_d;
+    long long rec_dstride;
+    int nrec, rec_acc;
     // each scalar twice, the operands of the packed two-lane (f32x2) arithmetic (set by prop_pairs)
     float2 kx2[5], kz2[5], axc2, inv2, a02, a12, a22;
 };

@@ -41,6 +41,7 @@ struct Job {
     std::vector<int> siz, six, riz, rix;    // geometry, copied at submit
     size_t ws = 0, need = 0;                // workspace cap of its context; bytes admitted
     Clock::time_point t_submit, t_admit, t_done;
+    double enqueue_s = 0.0;                 // host time spent enqueuing its launch group's work
     fwime_ctx *ctx = nullptr;
     float *stage = nullptr;                 // device staging of host buffers
     double J = 0.0;
@@ -99,6 +100,7 @@ namespace {
 // the operators and the event that completes the group.
 void enqueue_group(Server *s, Group *g)
 {
+    const auto t0 = Clock::now();
     cudaSetDevice(s->device);
     cudaStream_t st = s->streams[g->stream];
     auto fail_all = [&](int code) {
@@ -180,6 +182,8 @@ void enqueue_group(Server *s, Group *g)
         cudaStreamSynchronize(st);          // no event: complete the group the blocking way
         fail_all(FWIME_ECUDA);
     }
+    const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
+    for (Job *j : g->jobs) j->enqueue_s = dt;
     std::lock_guard<std::mutex> lk(s->mu);
     g->enqueued = true;
     s->cv_disp.notify_all();
@@ -381,6 +385,7 @@ int fill(const Job *j, fwime_result *res)
     res->done = j->done ? 1 : 0;
     res->status = j->status;
     res->objective = j->J;
+    res->enqueue_s = j->enqueue_s;
     if (j->done) {
         res->queued_s = std::chrono::duration<double>(j->t_admit - j->t_submit).count();
         res->latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
@@ -415,7 +420,7 @@ int fwime_server_create(fwime_ctx **out, size_t memory_budget, int max_active, i
     s->budget = memory_budget;
     s->options = options;
     s->max_active = (options & FWIME_SERVE_PLAIN) ? 1 : max_active;
-    s->nworkers = std::min(4, s->max_active);
+    s->nworkers = std::min(8, s->max_active);
     s->dispatcher = std::thread(dispatch_loop, s);
     for (int i = 0; i < s->nworkers; ++i) s->workers.emplace_back(worker_loop, s);
     *out = ctx_for_server(s);

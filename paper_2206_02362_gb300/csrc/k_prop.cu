@@ -399,6 +399,14 @@ template <int LOC, bool D2, bool SRC>
 __global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN)) k_prop(const PropArgs a)
 {
     extern __shared__ float4 smem4[];
+    if (a.rec_d && blockIdx.x == 0) {         // receivers of the input field (the previous step's output)
+        const long long s = blockIdx.y;
+        for (int r = threadIdx.x; r < a.nrec; r += PROP_WARPS * 32) {
+            const float val = a.cur[s * a.P + a.rec_off[r]];
+            float *dp = a.rec_d + s * a.rec_dstride + r;
+            *dp = a.rec_acc ? *dp + val : val;
+        }
+    }
     const int wic = threadIdx.x >> 5;
     const int wid = blockIdx.x * PROP_WARPS + wic;
     if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform

@@ -53,6 +53,7 @@ class ShotResult:
     data: np.ndarray | None = None      # forward: d [nt][nrec]
     grad: np.ndarray | None = None      # gradient: [nz][nx]
     objective: float | None = None
+    enqueue_s: float = 0.0              # host time the server spent enqueuing its launches
 
     @property
     def latency(self) -> float:
@@ -184,7 +185,7 @@ class Server:
                 if res.status != self.fw.FWIME_OK:
                     raise self.fw.FwimeError(res.status, f"request {req.rid}")
                 m = marsh[req.rid]
-                out = ShotResult(req.rid, req.kind, req.arrival, ts + res.queued_s, done)
+                out = ShotResult(req.rid, req.kind, req.arrival, ts + res.queued_s, done, enqueue_s=res.enqueue_s)
                 if req.kind == "forward":
                     out.data = m.t["d"][0].numpy().copy()
                 else:
@@ -193,6 +194,7 @@ class Server:
                 results[req.rid] = out
             if inflight and not (k < len(pending) and pending[k].arrival <= time.perf_counter() - t0):
                 time.sleep(2e-4)
+        self.last_wall = time.perf_counter() - t0       # serving time, after the buffers were pinned
         return [results[r] for r in sorted(results)]
 
     def close(self):
@@ -211,7 +213,8 @@ def summarize(results: list[ShotResult], wall: float | None = None) -> dict:
     lat = np.array([r.latency for r in results])
     span = wall if wall is not None else (max(r.done for r in results) - min(r.arrival for r in results))
     return {"requests": len(results), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "shots_per_s": len(results) / span, "span_s": span}
+            "mean_s": float(lat.mean()), "shots_per_s": len(results) / span, "span_s": span,
+            "enqueue_s_total": float(sum(r.enqueue_s for r in results))}
 
 
 def from_synth(req) -> ShotRequest:

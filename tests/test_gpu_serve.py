@@ -87,3 +87,60 @@ def test_over_budget_request_is_rejected():
             srv.serve(reqs, realtime=False)
     finally:
         srv.close()
+
+
+def test_device_pointer_requests_through_the_c_abi():
+    """fwime_submit with device buffers (host_io = 0): a forward and a gradient request on different
+    grids, submitted together and waited for; each result equals the same operator on its own context
+    bit for bit."""
+    import ctypes
+
+    import paper_2206_02362_gb300 as fw
+    lib = fw.load()
+    reqs = mix(n=12, seed=11)
+    grd = next(r for r in reqs if r.kind == "gradient")
+    fwd = next(r for r in reqs if r is not grd)
+    fwd.kind = "forward"                       # (a gradient request's p~ and d_obs are then unused)
+    h = ctypes.c_void_p()
+    assert lib.fwime_server_create(ctypes.byref(h), ctypes.c_size_t(4 << 30), 8, 0) == fw.FWIME_OK
+    keep, tickets, outs = [], [], []
+    try:
+        for r in (fwd, grd):
+            grid = fw.Grid(nz=r.nz, nx=r.nx, sponge=r.sponge, nt=r.nt, dt=r.dt, dx=r.dx, nh=r.nh)
+            geom = fw.Geometry(np.array([r.src[0]]), np.array([r.src[1]]), r.rec_iz, r.rec_ix)
+            t = {"v": torch.from_numpy(r.v).cuda(), "w": torch.from_numpy(r.w[None]).cuda()}
+            if r.kind == "forward":
+                t["out"] = torch.zeros((1, r.nt, len(r.rec_iz)), device="cuda")
+            else:
+                t["pt"] = torch.from_numpy(r.pt).cuda()
+                t["dobs"] = torch.from_numpy(r.dobs[None]).cuda()
+                t["out"] = torch.zeros((r.nz, r.nx), device="cuda")
+            gm, kg = geom.c()
+            p = lambda k: t[k].data_ptr() if k in t else None  # noqa: E731
+            c = fw.RequestC(fw.REQ_FORWARD if r.kind == "forward" else fw.REQ_GRADIENT, grid.c(), gm, 0,
+                            p("v"), p("w"), p("pt"), p("dobs"), p("out") if r.kind == "forward" else None,
+                            p("out") if r.kind == "gradient" else None, ctypes.c_float(r.eps))
+            tk = ctypes.c_uint64(0)
+            assert lib.fwime_submit(h, ctypes.byref(c), ctypes.byref(tk)) == fw.FWIME_OK
+            keep.append((c, kg, gm, grid, geom))
+            tickets.append(tk.value)
+            outs.append(t)
+        res = []
+        for tk in tickets:
+            rr = fw.ResultC()
+            assert lib.fwime_wait(h, ctypes.c_uint64(tk), ctypes.byref(rr)) == fw.FWIME_OK
+            assert rr.done == 1 and rr.status == fw.FWIME_OK and rr.latency_s >= rr.queued_s >= 0.0
+            res.append(rr.objective)
+        r = fw.ResultC()
+        assert lib.fwime_poll(h, ctypes.c_uint64(tickets[0]), ctypes.byref(r)) == fw.FWIME_EINVAL   # collected once
+    finally:
+        lib.fwime_destroy(h)
+    (c0, _, _, grid0, geom0), (c1, _, _, grid1, geom1) = keep
+    with fw.Context(grid0, geom0, shots_per_batch=1) as ctx:
+        ref = torch.zeros_like(outs[0]["out"])
+        ctx.forward(outs[0]["v"], outs[0]["w"], ref)
+    assert torch.equal(ref, outs[0]["out"])
+    with fw.Context(grid1, geom1, shots_per_batch=1) as ctx:
+        g = torch.zeros_like(outs[1]["out"])
+        J = ctx.gradient(outs[1]["v"], outs[1]["w"], outs[1]["pt"], outs[1]["dobs"], g, eps=grd.eps)
+    assert torch.equal(g, outs[1]["out"]) and J == res[1]
