@@ -230,7 +230,7 @@ def serving_section(nreq: int, rate: float, active: int = 16):
         s1 = serve.summarize(res, srv.last_wall)
         out = {"workload": f"serving mix, {nreq} requests, Poisson {rate}/s (overload: arrivals outpace the GPU)",
                "max_in_flight": active, **s1,
-               "enqueue_share": s1["enqueue_s_total"] / (s1["span_s"] * min(8, active))}
+               "enqueue_share": s1["enqueue_s_total"] / (s1["span_s"] * min(12, active))}
         # steady state: the same mix arriving at 0.7x the throughput just measured
         rate2 = 0.7 * out["shots_per_s"]
         reqs2 = [serve.from_synth(r) for r in synth.serving_mix(nreq=max(20, nreq // 2), rate=rate2,

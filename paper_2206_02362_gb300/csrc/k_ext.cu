@@ -155,6 +155,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_IMG_F32X2
 #define FWIME_IMG_F32X2 1
 #endif
+#ifndef FWIME_SC_PAIRS
+#define FWIME_SC_PAIRS 1      // (step, shot) pairs per loop iteration of the scatter (sharing its weights)
+#endif
 #ifndef FWIME_SC_PACK_MAX
 #define FWIME_SC_PACK_MAX 96   // largest nh * A whose weights are packed (more spills)
 #endif
@@ -258,93 +261,122 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
         st_in = st_in + 4u * Sh::STG == 4u * NS * Sh::STG ? 0u : st_in + 4u * Sh::STG;
         cpa_commit();
     };
+    // PP pairs per iteration share the weights: PP independent sets of accumulator chains per warp
+    constexpr int PP = FWIME_SC_PAIRS;
+    static_assert(NS >= 2 * PP, "ring too short for the pairs per iteration");
 #pragma unroll 1
-    for (int q = 0; q < NS - 1; ++q) issue(q);
+    for (int q = 0; q < NS - PP; ++q) issue(q);
     const int ys = yw + 2 * A * tp + A * par;      // first of the A consecutive outputs this lane stores
     const float *lsm = wsm + par * Sh::OFF + A * tp;
 #pragma unroll 1
-    for (int p = 0; p < a.npair; ++p) {
-        cpa_wait<NS - 2>();                        // pair p has landed (this lane's copies) ...
-        __syncwarp();                              // ... and every lane's; all finished pair p - 1
-        issue(p + NS - 1);                         // refills the stage of pair p - 1
-        float dv[Sh::NWV];                         // dv[k] = D(yf - 2 HM + 2k)
-        lds_vec<Sh::VW>(dv, lsm + st_c);
-        st_c = st_c + Sh::STG == NS * Sh::STG ? 0 : st_c + Sh::STG;
-        float e[A];
+    for (int p = 0; p < a.npair; p += PP) {
+        cpa_wait<NS - 2 * PP>();                   // pairs p .. p + PP - 1 have landed (this lane's copies) ...
+        __syncwarp();                              // ... and every lane's; all finished the pairs before
+#pragma unroll
+        for (int u = 0; u < PP; ++u) issue(p + NS - PP + u);   // refills the stages of the previous pairs
+        float dv[PP][Sh::NWV];                     // dv[u][k] = D(yf - 2 HM + 2k) of pair p + u
+#pragma unroll
+        for (int u = 0; u < PP; ++u) {
+            lds_vec<Sh::VW>(dv[u], lsm + st_c);
+            st_c = st_c + Sh::STG == NS * Sh::STG ? 0 : st_c + Sh::STG;
+        }
+        float e[PP][A];
         if constexpr (PACK) {
-            f32x2 ae[A / 2], ao = pk(0.f, 0.f);
-            float ao0 = 0.f, ao3 = 0.f;
+            f32x2 ae[PP][A / 2], ao[PP];
+            float ao0[PP], ao3[PP];
 #pragma unroll
-            for (int q = 0; q < A / 2; ++q) ae[q] = pk(0.f, 0.f);
+            for (int u = 0; u < PP; ++u) {
+                ao[u] = pk(0.f, 0.f);
+                ao0[u] = ao3[u] = 0.f;
 #pragma unroll
-            for (int m = 0; m < NH; ++m) {             // offsets in the order of their samples
+                for (int q = 0; q < A / 2; ++q) ae[u][q] = pk(0.f, 0.f);
+            }
+#pragma unroll
+            for (int m = 0; m < NH; ++m) {                 // offsets in the order of their samples
                 const int ih = SIGMA > 0 ? NH - 1 - m : m;
                 const int o = HM - SIGMA * (ih - HM);
-                if (ih % 2 == 0) {
 #pragma unroll
-                    for (int q = 0; q < A / 2; ++q) ae[q] = fma2(WE[ih / 2][q], pk(dv[o + 2 * q], dv[o + 2 * q + 1]), ae[q]);
-                } else {
-                    if (A == 4) ao = fma2(WO[ih / 2], pk(dv[o + 1], dv[o + 2]), ao);
-                    ao0 = fmaf(WO0[ih / 2], dv[o], ao0);
-                    ao3 = fmaf(WO3[ih / 2], dv[o + A - 1], ao3);
+                for (int u = 0; u < PP; ++u) {             // the pairs' chains interleaved
+                    if (ih % 2 == 0) {
+#pragma unroll
+                        for (int q = 0; q < A / 2; ++q)
+                            ae[u][q] = fma2(WE[ih / 2][q], pk(dv[u][o + 2 * q], dv[u][o + 2 * q + 1]), ae[u][q]);
+                    } else {
+                        if (A == 4) ao[u] = fma2(WO[ih / 2], pk(dv[u][o + 1], dv[u][o + 2]), ao[u]);
+                        ao0[u] = fmaf(WO0[ih / 2], dv[u][o], ao0[u]);
+                        ao3[u] = fmaf(WO3[ih / 2], dv[u][o + A - 1], ao3[u]);
+                    }
                 }
             }
-            float el[A], ol[A];
 #pragma unroll
-            for (int q = 0; q < A / 2; ++q) upk(ae[q], el[2 * q], el[2 * q + 1]);
-            ol[0] = ao0;
-            ol[A - 1] = ao3;
-            if (A == 4) upk(ao, ol[1], ol[A - 2]);
+            for (int u = 0; u < PP; ++u) {
+                float el[A], ol[A];
 #pragma unroll
-            for (int j = 0; j < A; ++j) e[j] = el[j] + ol[j];
+                for (int q = 0; q < A / 2; ++q) upk(ae[u][q], el[2 * q], el[2 * q + 1]);
+                ol[0] = ao0[u];
+                ol[A - 1] = ao3[u];
+                if (A == 4) upk(ao[u], ol[1], ol[A - 2]);
+#pragma unroll
+                for (int j = 0; j < A; ++j) e[u][j] = el[j] + ol[j];
+            }
         } else {
-            // two partial sums per output (even / odd offsets): 2 A independent chains.  Offsets are
-            // visited in the order of their samples, so the first products wait only for the first load.
-            float acc[2][A];
+            // two partial sums per output (even / odd offsets): 2 A independent chains per pair.  Offsets
+            // are visited in the order of their samples, so the first products wait only for the first load.
+            float acc[PP][2][A];
 #pragma unroll
-            for (int j = 0; j < A; ++j) acc[0][j] = acc[1][j] = 0.f;
+            for (int u = 0; u < PP; ++u)
+#pragma unroll
+                for (int j = 0; j < A; ++j) acc[u][0][j] = acc[u][1][j] = 0.f;
 #pragma unroll
             for (int m = 0; m < NH; ++m) {
                 const int ih = SIGMA > 0 ? NH - 1 - m : m;
 #pragma unroll
-                for (int j = 0; j < A; ++j)            // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
-                    acc[m & 1][j] = fmaf(Wr[j][ih], dv[j - SIGMA * (ih - HM) + HM], acc[m & 1][j]);
+                for (int u = 0; u < PP; ++u)
+#pragma unroll
+                    for (int j = 0; j < A; ++j)            // D(y_j - 2 SIGMA h) = dv[j - SIGMA (ih - HM) + HM]
+                        acc[u][m & 1][j] = fmaf(Wr[j][ih], dv[u][j - SIGMA * (ih - HM) + HM], acc[u][m & 1][j]);
             }
 #pragma unroll
-            for (int j = 0; j < A; ++j) e[j] = acc[0][j] + acc[1][j];
+            for (int u = 0; u < PP; ++u)
+#pragma unroll
+                for (int j = 0; j < A; ++j) e[u][j] = acc[u][0][j] + acc[u][1][j];
         }
-        float v[A];
-        if constexpr (A == 4) {
-            const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[0] : e[2], 16);
-            const float r1 = __shfl_xor_sync(0xffffffffu, par ? e[1] : e[3], 16);
-            v[0] = par ? r0 : e[0]; v[1] = par ? e[2] : r0;
-            v[2] = par ? r1 : e[1]; v[3] = par ? e[3] : r1;
-        } else {
-            const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[0] : e[1], 16);
-            v[0] = par ? r0 : e[0]; v[1] = par ? e[1] : r0;
-        }
-        float *o = const_cast<float *>(pout.row) + ys;
-        pout.next();
-        if (ys + A <= a.x_hi) {
+#pragma unroll
+        for (int u = 0; u < PP; ++u) {
+            if (PP > 1 && p + u >= a.npair) break;   // warp-uniform
+            float v[A];
             if constexpr (A == 4) {
-                float4 w4 = make_float4(v[0], v[1], v[2], v[3]);
-                if (a.accumulate) {
-                    const float4 old = *reinterpret_cast<const float4 *>(o);
-                    w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
-                }
-                *reinterpret_cast<float4 *>(o) = w4;
+                const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[u][0] : e[u][2], 16);
+                const float r1 = __shfl_xor_sync(0xffffffffu, par ? e[u][1] : e[u][3], 16);
+                v[0] = par ? r0 : e[u][0]; v[1] = par ? e[u][2] : r0;
+                v[2] = par ? r1 : e[u][1]; v[3] = par ? e[u][3] : r1;
             } else {
-                float2 w2 = make_float2(v[0], v[1]);
-                if (a.accumulate) {
-                    const float2 old = *reinterpret_cast<const float2 *>(o);
-                    w2.x += old.x; w2.y += old.y;
-                }
-                *reinterpret_cast<float2 *>(o) = w2;
+                const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[u][0] : e[u][1], 16);
+                v[0] = par ? r0 : e[u][0]; v[1] = par ? e[u][1] : r0;
             }
-        } else {
+            float *o = const_cast<float *>(pout.row) + ys;
+            pout.next();
+            if (ys + A <= a.x_hi) {
+                if constexpr (A == 4) {
+                    float4 w4 = make_float4(v[0], v[1], v[2], v[3]);
+                    if (a.accumulate) {
+                        const float4 old = *reinterpret_cast<const float4 *>(o);
+                        w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+                    }
+                    *reinterpret_cast<float4 *>(o) = w4;
+                } else {
+                    float2 w2 = make_float2(v[0], v[1]);
+                    if (a.accumulate) {
+                        const float2 old = *reinterpret_cast<const float2 *>(o);
+                        w2.x += old.x; w2.y += old.y;
+                    }
+                    *reinterpret_cast<float2 *>(o) = w2;
+                }
+            } else {
 #pragma unroll
-            for (int k = 0; k < A; ++k)
-                if (ys + k < a.x_hi) o[k] = a.accumulate ? o[k] + v[k] : v[k];
+                for (int k = 0; k < A; ++k)
+                    if (ys + k < a.x_hi) o[k] = a.accumulate ? o[k] + v[k] : v[k];
+            }
         }
     }
     cpa_wait<0>();
