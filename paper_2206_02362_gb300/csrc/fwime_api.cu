@@ -87,6 +87,11 @@ struct fwime_ctx {
     int *h_status = nullptr;
     void *small = nullptr;          // one stream-ordered block: J, partials, status, offsets
     std::vector<int> h_off;         // host copy of the offsets (source of the async upload)
+    // receiver injection map for the adjoint steps: rows [inj_lo, inj_hi) x NXP -> first receiver at the
+    // point or -1, then the chain of further receivers at the same point (host copy and device copy)
+    std::vector<int> h_inj;
+    int *d_inj_map = nullptr, *d_inj_next = nullptr;
+    int inj_lo = 0, inj_hi = 0;
     double *user_J = nullptr;
     double *vp_hist_dev = nullptr, *vp_hist_user = nullptr;   // VP objective history (device, caller's host)
     int vp_hist_n = 0;
@@ -495,10 +500,15 @@ struct RecTo {
     int acc = 0;
 };
 
+// Residual injected at the receivers into a (plain) stencil launch's output: row `val` of the data.
+struct InjFrom {
+    const float *val = nullptr;
+};
+
 static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out, float *d2, const float *wsrc,
                 int src_shot0, const float *f0 = nullptr, float a0 = 0.f, const float *f1 = nullptr, float a1 = 0.f,
                 const float *f2 = nullptr, float a2 = 0.f, const float *coef = nullptr, const float *fc = nullptr,
-                RecTo rec = RecTo{})
+                RecTo rec = RecTo{}, InjFrom inj = InjFrom{})
 {
     fwime_ctx *x = r.x;
     PropArgs a = r.base;
@@ -514,12 +524,17 @@ static int prop(Run &r, int Sb, const float *cur, const float *prev, float *out,
         a.rec_off = x->d_rec_off; a.rec_d = rec.d; a.rec_dstride = (long long)x->g.nt * x->nrec;
         a.nrec = x->nrec; a.rec_acc = rec.acc;
     }
+    if (inj.val) {
+        a.inj_map = x->d_inj_map; a.inj_next = x->d_inj_next; a.inj_val = inj.val;
+        a.inj_vstride = (long long)x->g.nt * x->nrec; a.inj_lo = x->inj_lo; a.inj_hi = x->inj_hi;
+    }
     // compulsory bytes: per shot-point read q^n, q^{n-1}, write q^{n+1}, and per point once per launch
     // the shared c, over the padded grid; D2t out and the local source fields (and coef) over the
     // physical rows only (zero elsewhere, not needed there)
     const double pts = (double)x->NZ * x->NX, spts = (double)x->g.nz * x->NX;
     const double srcb = (d2 ? 4 : 0) + 4.0 * ((f0 != nullptr) + (f1 != nullptr) + (f2 != nullptr)) + (fc ? 4 : 0);
-    const double recb = rec.d ? (double)Sb * x->nrec * (rec.acc ? 12.0 : 8.0) : 0.0;
+    const double recb = (rec.d ? (double)Sb * x->nrec * (rec.acc ? 12.0 : 8.0) : 0.0) +
+                        (inj.val ? (double)Sb * x->nrec * 4.0 : 0.0);
     LAUNCH(FWIME_K_PROP, pts * (Sb * 12.0 + 4.0) + spts * (Sb * srcb + (coef ? 4.0 : 0.0)) + recb,
            launch_prop(a, Sb, x->st));
     if (x->opt_fs)
@@ -539,17 +554,12 @@ static int record(Run &r, int Sb, const float *f1, const float *f2, float *d, in
     return FWIME_OK;
 }
 
-static int inject(Run &r, int Sb, float *fld, const float *val)
+// One adjoint time step with the residual's injection at the receivers folded into the stencil launch
+// (the transpose of recording; the same arithmetic as a separate injection after the step)
+static int adj_step(Run &r, int Sb, const float *cur, const float *prev, float *out, const float *val)
 {
-    fwime_ctx *x = r.x;
-    PointsArgs a{};
-    a.nrec = x->nrec; a.P = x->P; a.rec_off = x->d_rec_off;
-    a.fld = fld; a.val = val; a.vstride = (long long)x->g.nt * x->nrec; a.c = r.w.c;
-    LAUNCH(FWIME_K_POINTS, (double)Sb * x->nrec * 12.0, launch_points(a, Sb, x->st));
-    // free surface: receivers within 4 rows of the surface change rows whose mirror the next step reads
-    if (x->opt_fs)
-        LAUNCH(FWIME_K_OTHER, (double)Sb * x->NXP * 40.0, launch_free_surface(fld, nullptr, Sb, x->P, x->NXP, x->o, x->st));
-    return FWIME_OK;
+    return prop(r, Sb, cur, prev, out, nullptr, nullptr, 0, nullptr, 0.f, nullptr, 0.f, nullptr, 0.f, nullptr,
+                nullptr, RecTo{}, InjFrom{val});
 }
 
 static RingRef ringref(const float *base, long long slot_stride, int mod, int shift)
@@ -843,8 +853,7 @@ static int run_born_adj(fwime_ctx *x, Run &r, bool ext, const float *v, const fl
             }
             for (int m = n1; m >= n0 + 1; --m) {
                 float *mo = Mu + (m % R) * SP;
-                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
-                TRY(inject(r, Sb, mo, d + s0 * nd + (size_t)m * x->nrec));
+                TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, d + s0 * nd + (size_t)m * x->nrec));
             }
             if (ext)
                 TRY(image(r, Sb, n0, kk, IMG_EXT, ringref(Dr, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(nullptr, 0, 0, 0),
@@ -968,8 +977,7 @@ static int run_born_tlag_adj(fwime_ctx *x, Run &r, const float *v, const float *
             for (; next_block >= j; --next_block) TRY(block(next_block));
             for (int m = n1; m >= n0 + 1; --m) {
                 float *mo = Mu + (m % R) * SP;
-                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
-                TRY(inject(r, Sb, mo, d + s0 * nd + (size_t)m * x->nrec));
+                TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, d + s0 * nd + (size_t)m * x->nrec));
             }
             TRY(tlag_launch(r, Sb, n0, n1, true, ringref(Dr, SP, RD, 0), ringref(nullptr, 0, 0, 0),
                             ringref(Mu, SP, R, 1), r.w.acc1));
@@ -1147,9 +1155,8 @@ static int run_tomo_adj_tlag(fwime_ctx *x, Run &r, int mode, const float *v, con
             for (const int lo = std::max(n0 - Hs + 1, 1); mu_lo - 1 >= lo; --mu_lo) {
                 const int k = mu_lo - 1;
                 float *mo = Mu + (long long)(k % RM) * SP;
-                TRY(prop(r, Sb, Mu + (long long)((k + 1) % RM) * SP, Mu + (long long)((k + 2) % RM) * SP, mo, nullptr,
-                         nullptr, 0));
-                TRY(inject(r, Sb, mo, rr + (size_t)k * x->nrec));
+                TRY(adj_step(r, Sb, Mu + (long long)((k + 1) % RM) * SP, Mu + (long long)((k + 2) % RM) * SP, mo,
+                             rr + (size_t)k * x->nrec));
             }
             // z^m = sum_i W_i lambda^(m + 2 s_i) for m in [n0, n1) (lambda^n = mu^(n+1))
             TRY(tlag_launch(r, Sb, n0, n1, false, ringref(Mu, SP, RM, 1), ringref(Zr, SP, R, n0), none, nullptr, r.w.W,
@@ -1347,8 +1354,7 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
             // adjoint of the residual: mu^m, m = n1 .. n0+1 (lambda^ at step n is mu^{n+1})
             for (int m = n1; m >= n0 + 1; --m) {
                 float *mo = Mu + (m % R) * SP;
-                TRY(prop(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, nullptr, nullptr, 0));
-                TRY(inject(r, Sb, mo, rr + (size_t)m * x->nrec));
+                TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, rr + (size_t)m * x->nrec));
             }
             // z^n = E_D^T(W, lambda^n) for n in [n0, n1)
             TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Mu, SP, R, 1), ringref(Zr, SP, R, 0), -1, 0));
@@ -1614,7 +1620,27 @@ int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo, si
     for (int s = 0; s < x->nshot; ++s) x->h_off[s] = (x->src_iz[s] + x->o) * x->NXP + x->src_ix[s] + x->o;
     for (int r = 0; r < x->nrec; ++r)
         x->h_off[x->nshot + r] = (x->rec_iz[r] + x->o) * x->NXP + x->rec_ix[r] + x->o;
-    const size_t small_bytes = (1 + 1024) * sizeof(double) + sizeof(int) * (1 + x->h_off.size());
+    // injection map: rows of the receivers x NXP (first receiver at a point, -1 elsewhere), then the chain
+    int rlo = x->NZ, rhi = 0;
+    for (int r = 0; r < x->nrec; ++r) {
+        rlo = std::min(rlo, x->rec_iz[r] + x->o);
+        rhi = std::max(rhi, x->rec_iz[r] + x->o + 1);
+    }
+    x->inj_lo = rlo;
+    x->inj_hi = rhi;
+    const size_t nmap = (size_t)(rhi - rlo) * x->NXP;
+    x->h_inj.assign(nmap + x->nrec, -1);
+    {
+        std::vector<int> last(nmap, -1);
+        for (int r = 0; r < x->nrec; ++r) {
+            const size_t pos = (size_t)(x->rec_iz[r] + x->o - rlo) * x->NXP + x->rec_ix[r] + x->o;
+            if (x->h_inj[pos] < 0) x->h_inj[pos] = r;
+            else x->h_inj[nmap + last[pos]] = r;
+            last[pos] = r;
+        }
+    }
+    const size_t off_inj = ((1 + 1024) * sizeof(double) + sizeof(int) * (1 + x->h_off.size()) + 15) / 16 * 16;
+    const size_t small_bytes = off_inj + sizeof(int) * x->h_inj.size();
     double *slot = pinned_slot();
     bool ok = slot != nullptr &&
               cudaMallocAsync(&x->small, small_bytes, x->st) == cudaSuccess;
@@ -1626,8 +1652,12 @@ int fwime_create(fwime_ctx **out, const fwime_grid *g, const fwime_geom *geo, si
         x->d_status = reinterpret_cast<int *>(x->d_part + 1024);
         x->d_src_off = x->d_status + 1;
         x->d_rec_off = x->d_src_off + x->nshot;
+        x->d_inj_map = reinterpret_cast<int *>(reinterpret_cast<char *>(x->small) + off_inj);
+        x->d_inj_next = x->d_inj_map + nmap;
         ok = cudaMemsetAsync(x->small, 0, small_bytes, x->st) == cudaSuccess &&
              cudaMemcpyAsync(x->d_src_off, x->h_off.data(), x->h_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             x->st) == cudaSuccess &&
+             cudaMemcpyAsync(x->d_inj_map, x->h_inj.data(), x->h_inj.size() * sizeof(int), cudaMemcpyHostToDevice,
                              x->st) == cudaSuccess;
     }
     if (!ok) {

@@ -73,6 +73,14 @@ struct PropArgs {
     float *rec_d;
     long long rec_dstride;
     int nrec, rec_acc;
+    // optional receiver injection into the OUTPUT field: out(rec_r) += c(rec_r) inj_val[s * inj_vstride + r]
+    // (the transpose of recording, as k_points injects it).  inj_map[(z - inj_lo) * NXP + x] is the first
+    // receiver at padded point (z, x) of the rows [inj_lo, inj_hi) or -1, inj_next[r] the next receiver at
+    // the same point or -1.
+    const int *inj_map, *inj_next;
+    const float *inj_val;
+    long long inj_vstride;
+    int inj_lo, inj_hi;
     // each scalar twice, the operands of the packed two-lane (f32x2) arithmetic (set by prop_pairs)
     float2 kx2[5], kz2[5], axc2, inv2, a02, a12, a22;
 };

@@ -249,9 +249,17 @@ __device__ __forceinline__ void row_math(const PropArgs &a, const PropK &K, cons
                                     gxv, sj, amp, o, d2);
 }
 
+// Adds the injections of the receivers chained from r at one output point: o + c v per receiver, each
+// product and sum rounded separately (the arithmetic of a separate injection launch after the step).
+__device__ __forceinline__ void inject_point(const PropArgs &a, int shot, int r, float c, float &o)
+{
+    for (; r >= 0; r = __ldg(a.inj_next + r))
+        o = __fadd_rn(o, __fmul_rn(c, __ldg(a.inj_val + (long long)shot * a.inj_vstride + r)));
+}
+
 // The time step of one warp's work item (strip, chunk) of shot `shot`; wsm is the warp's shared
 // memory (CUR_SLOTS x CUR_ROW + AUX_SLOTS x naux_max x STRIP floats).
-template <int LOC, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC, bool INJ = false>
 __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, const int shot, float *wsm)
 {
     constexpr bool LOCAL = LOC > 0;
@@ -371,6 +379,13 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         row_math<LOC, D2, SRC>(a, prop_k(a), L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
                                  q[(4 + (R)) % 9], q[(5 + (R)) % 9], q[(6 + (R)) % 9], q[(7 + (R)) % 9],      \
                                  q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
+        if (INJ && zz >= a.inj_lo && zz < a.inj_hi && xin) { /* receivers on this row (warp-uniform) */      \
+            const int4 m4 = *reinterpret_cast<const int4 *>(a.inj_map + (long long)(zz - a.inj_lo) * NXP + x); \
+            inject_point(a, shot, m4.x, cv.x, o.x);                                                          \
+            inject_point(a, shot, m4.y, cv.y, o.y);                                                          \
+            inject_point(a, shot, m4.z, cv.z, o.z);                                                          \
+            inject_point(a, shot, m4.w, cv.w, o.w);                                                          \
+        }                                                                                                    \
         if (xin) {                                                                                           \
             st4(out + idx, o);                                                                               \
             if (D2 && zz >= a.zs_lo && zz < a.zs_hi) st4(a.d2 + so + idx, d2);                               \
@@ -395,8 +410,9 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
     cp_wait<0>();
 }
 
-template <int LOC, bool D2, bool SRC>
-__global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN)) k_prop(const PropArgs a)
+// INJ: the receivers' injection into the output (the adjoint step; LOC = 0, no D2t, no point source)
+template <int LOC, bool D2, bool SRC, bool INJ = false>
+__global__ void __launch_bounds__(PROP_WARPS * 32, INJ ? 4 : (LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN))) k_prop(const PropArgs a)
 {
     extern __shared__ float4 smem4[];
     if (a.rec_d && blockIdx.x == 0) {         // receivers of the input field (the previous step's output)
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLO
     const int wid = blockIdx.x * PROP_WARPS + wic;
     if (wid >= a.nstrip * a.nchunk) return;   // warp-uniform
     float *wsm = reinterpret_cast<float *>(smem4) + wic * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP);
-    prop_body<LOC, D2, SRC>(a, wid, blockIdx.y, wsm);
+    prop_body<LOC, D2, SRC, INJ>(a, wid, blockIdx.y, wsm);
 }
 
 // ------------------------------------------------------------- grouped forward
@@ -472,15 +488,15 @@ cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const
     return cudaGetLastError();
 }
 
-template <int LOC, bool D2, bool SRC>
+template <int LOC, bool D2, bool SRC, bool INJ = false>
 static void launch_prop_t(const PropArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_prop<LOC, D2, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_prop<LOC, D2, SRC, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr = true;
     }
-    k_prop<LOC, D2, SRC><<<grid, block, smem, st>>>(a);
+    k_prop<LOC, D2, SRC, INJ><<<grid, block, smem, st>>>(a);
 }
 
 // Resident CTAs per SM of the plain (no local source) variant with the smem it launches with.
@@ -505,6 +521,11 @@ cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
     const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP) * sizeof(float);
     const int loc = !local ? 0 : (a.f1 || a.f2 || a.fc || !a.f0) ? 2 : 1;
     const int key = loc * 4 + (d2 ? 2 : 0) + (src ? 1 : 0);
+    if (a.inj_val) {                           // the caller injects only into plain steps
+        if (key != 0) return cudaErrorInvalidValue;
+        launch_prop_t<0, false, false, true>(a, grid, block, smem, st);
+        return cudaGetLastError();
+    }
     switch (key) {
     case 0: launch_prop_t<0, false, false>(a, grid, block, smem, st); break;
     case 1: launch_prop_t<0, false, true>(a, grid, block, smem, st); break;
