@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--segment", type=int, default=0, help="checkpoint/ring segment length (0 = auto)")
     ap.add_argument("--no-grad", action="store_true", help="skip the FWIME-gradient batched-vs-plain section")
-    ap.add_argument("--no-tune", action="store_true", help="skip the stencil autotuner (automatic chunking)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (automatic schedule)")
+    ap.add_argument("--tune", default="schedule", choices=["schedule", "chunk"],
+                    help="schedule: segment x shots per launch x chunking; chunk: the stencil's chunking only")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix section")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -290,7 +292,7 @@ def time_lag_section(fw, torch, dev, wl, nh=21, lag=2):
             "family_gbs": {k: round(p["bytes"] / (p["ms"] * 1e-3) / 1e9, 1) for k, p in prof.items() if p["ms"] > 0}}
 
 
-def gradient_section(fw, torch, dev, nshot):
+def gradient_section(fw, torch, dev, nshot, tune=True):
     """FWIME gradient (objective + B* r + T* r, checkpointed) on the North-Sea-shaped workload,
     400 x 1600 at 12.5 m, nt 5000, nh 31: all shots batched, the call captured once in a CUDA graph
     and replayed on its own stream (timed), vs the plain path (one shot per launch, host-driven steps)
@@ -308,6 +310,8 @@ def gradient_section(fw, torch, dev, nshot):
     out = {"workload": wl.name, "nshot": wl.nshot, "segment": "auto"}
     stream = torch.cuda.Stream(device=dev)
     with fw.Context(grid, geom, stream=stream, graph=1) as c:
+        if tune:                                              # segment x shots per launch x chunking (untimed)
+            out["autotune"] = c.autotune_schedule(fw.OP_GRADIENT)
         c.gradient(v, w, pt, dobs, g, eps=1e-3)              # warm-up: workspace, capture, first replay
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -450,7 +454,11 @@ def main():
     ctx = fw.Context(grid, geom, profile=1, segment=args.segment, reuse_background=reuse)
     tuned = None
     if not args.no_tune:
-        tuned = ctx.autotune(fw.OP_BORN_EXT_ADJ)    # stencil chunking measured on this batch (untimed)
+        if args.tune == "schedule":   # segment x shots per launch x chunking, timed on this GPU (untimed here)
+            tuned = ctx.autotune_schedule(fw.OP_BORN_EXT_ADJ)
+        else:                         # stencil chunking only
+            zc, us = ctx.autotune(fw.OP_BORN_EXT_ADJ)
+            tuned = {"zchunk": zc, "us_stencil": us}
     launches = [0]
 
     reused = [0]
@@ -528,7 +536,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Marmousi2-shaped stand-in)",
             "config": config(wl, args, world), "roofline": roofline, "gpu_launches": launches[0],
             "clocks": clocks, "shots_per_s": shots_per_s,
-            "autotune": {"stencil_rows_per_warp": tuned[0], "us_per_launch": tuned[1]} if tuned else None,
+            "autotune": tuned,
             "executed_gupd_s": value * (4.0 if reused[0] else 5.0) / 4.0,
             "background_reuse": {"used": bool(reused[0]),
                                  "note": "B~* starts from the background states kept by the B~ of the same step "
@@ -599,7 +607,7 @@ def main():
     torch.cuda.empty_cache()
     # FWIME gradient (Eqs. 7-9) on the North-Sea-shaped workload: batched vs plain shots/s
     if not args.no_grad and rank == 0:
-        line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots)
+        line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots, tune=not args.no_tune)
     if not args.no_tlag and rank == 0 and world == 1:
         line["time_lag"] = time_lag_section(fw, torch, dev, wl)
     # Salt-shaped batched gradient with checkpoint/recompute (a shot subset)

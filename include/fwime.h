@@ -323,6 +323,22 @@ int fwime_poll(fwime_ctx *server, uint64_t ticket, fwime_result *res);
 int fwime_wait(fwime_ctx *server, uint64_t ticket, fwime_result *res);
 int fwime_server_last_error(char *buf, size_t n);
 
+/* Schedule autotuner for operator `op`: segment length K (the automatic one, half and double, unless
+ * FWIME_OPT_SEGMENT fixes it) x shots per launch S (the largest equal batch that fits at that K, and half
+ * of it) x the stencil's rows per warp.  At every (K, S) it plans the operator's workspace, times the stencil
+ * for its chunking candidates and the operator's extension kernels once over a full segment of K x S
+ * (step, shot) pairs with CUDA events, and models the time per shot as
+ *   ((nt - 1) props t_stencil + nseg (scatters t_scatter + images t_image)) / S
+ * with the operator's launches per step and per segment.  The fastest schedule is set as the context's
+ * FWIME_OPT_SEGMENT, FWIME_OPT_SHOTS_PER_BATCH and FWIME_OPT_ZCHUNK and returned.  Synchronous; the
+ * workspace contents are overwritten (no operator state survives it).  Not with the plain path. */
+typedef struct {
+    int segment, shots_per_batch, zchunk;
+    float us_stencil, us_scatter, us_image;   /* per launch at the chosen schedule */
+    double us_per_shot;                       /* modelled operator time per shot */
+} fwime_schedule;
+int fwime_autotune_schedule(fwime_ctx *ctx, int op, fwime_schedule *res);
+
 /* Waits for the context's stream and returns the latched device status
  * (FWIME_OK, FWIME_ECFL, FWIME_ETIMEOUT) or FWIME_ECUDA; clears the latch. */
 int fwime_sync(fwime_ctx *ctx);

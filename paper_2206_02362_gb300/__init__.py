@@ -41,7 +41,7 @@ ABI_FUNCTIONS = ("fwime_create", "fwime_workspace_bytes", "fwime_set_option", "f
                  "fwime_forward", "fwime_born", "fwime_born_adj", "fwime_born_ext", "fwime_born_ext_adj",
                  "fwime_tomo", "fwime_tomo_adj", "fwime_gradient", "fwime_gradient_forward", "fwime_gradient_backward",
                  "fwime_objective", "fwime_vp_solve", "fwime_spline", "fwime_spline_refine",
-                 "fwime_autotune", "fwime_forward_group", "fwime_sync", "fwime_profile_read",
+                 "fwime_autotune", "fwime_autotune_schedule", "fwime_forward_group", "fwime_sync", "fwime_profile_read",
                  "fwime_last_error_detail", "fwime_strerror", "fwime_destroy",
                  "fwime_server_create", "fwime_request_bytes", "fwime_submit", "fwime_poll", "fwime_wait",
                  "fwime_server_last_error")
@@ -67,6 +67,12 @@ class GeomC(ctypes.Structure):
     _fields_ = [("nshot", ctypes.c_int), ("src_iz", ctypes.POINTER(ctypes.c_int)),
                 ("src_ix", ctypes.POINTER(ctypes.c_int)), ("nrec", ctypes.c_int),
                 ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int))]
+
+
+class ScheduleC(ctypes.Structure):
+    _fields_ = [("segment", ctypes.c_int), ("shots_per_batch", ctypes.c_int), ("zchunk", ctypes.c_int),
+                ("us_stencil", ctypes.c_float), ("us_scatter", ctypes.c_float), ("us_image", ctypes.c_float),
+                ("us_per_shot", ctypes.c_double)]
 
 
 class RequestC(ctypes.Structure):
@@ -118,6 +124,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     fl = ctypes.POINTER(ctypes.c_float)
     lib.fwime_spline_refine.argtypes = [vp, ip, fl, ip, fl, fp, ip, fl, ip, fl, fp]
     lib.fwime_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    lib.fwime_autotune_schedule.argtypes = [vp, ip, ctypes.POINTER(ScheduleC)]
     lib.fwime_forward_group.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
     lib.fwime_sync.argtypes = [vp]
@@ -395,6 +402,13 @@ class Context:
         zc, us = ctypes.c_int(0), ctypes.c_float(0)
         self._check(self._lib.fwime_autotune(self._h, int(op), ctypes.byref(zc), ctypes.byref(us)), "fwime_autotune")
         return int(zc.value), float(us.value)
+
+    def autotune_schedule(self, op: int) -> dict:
+        """Times segment length x shots per launch x stencil chunking for operator `op` and keeps the fastest
+        (fwime_autotune_schedule); returns the schedule and its timings."""
+        r = ScheduleC()
+        self._check(self._lib.fwime_autotune_schedule(self._h, int(op), ctypes.byref(r)), "fwime_autotune_schedule")
+        return {k: getattr(r, k) for k, _ in ScheduleC._fields_}
 
     def objective(self, v, w, pt, dobs, eps=0.0, sync=True):
         """Phi = 1/2||f + B~p~ - dobs||^2 + eps^2/2||D p~||^2 alone (no adjoint sweep); valid once synced."""

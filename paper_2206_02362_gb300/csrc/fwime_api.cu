@@ -2166,6 +2166,154 @@ int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_o
     return FWIME_OK;
 }
 
+// Schedule autotuner: segment length K x shots per launch S x stencil chunking, timed on this device.
+// For each K (the automatic one, half, double) the planner gives the largest equal batch S_K that fits;
+// S_K and half of it are tried.  At each (K, S) the stencil is timed for its chunking candidates and the
+// operator's extension kernels once over a full segment of K x S pairs; the modelled time per shot,
+//   (nt - 1) * props * t_stencil / S + nseg * (scatters * t_scatter + images * t_image) / S,
+// picks the schedule (props, scatters, images: the operator's launches per step and per segment).
+int fwime_autotune_schedule(fwime_ctx *x, int op, fwime_schedule *res)
+{
+    if (!x || !res || op < 0 || op > FWIME_OP_OBJECTIVE) return FWIME_EINVAL;
+    NOT_SERVER(x);
+    if (x->capturing) return FWIME_EBUSY;
+    if (x->opt_plain) return fail(x, FWIME_EINVAL, "the plain path has a fixed schedule");
+    static const int PROPS[] = {1, 2, 3, 2, 3, 4, 6, 6, 2};
+    static const int SCAT[] = {0, 0, 0, 1, 0, 3, 2, 2, 1};
+    static const int IMGS[] = {0, 0, 0, 0, 1, 0, 1, 1, 0};
+    const bool lag = x->opt_tlag > 0;   // the time-lag schedules: extension kernels not timed here
+    const int saved_K = x->opt_K, saved_S = x->opt_S, saved_zc = x->opt_zchunk, saved_prof = x->opt_profile;
+    x->opt_profile = 0;
+    std::vector<int> Ks;
+    if (saved_K > 0) Ks = {saved_K};
+    else {
+        const int K0 = seg_K(x);
+        Ks = {K0, std::max(K0 / 2, 8), std::min(2 * K0, x->g.nt - 1)};
+        std::sort(Ks.begin(), Ks.end());
+        Ks.erase(std::unique(Ks.begin(), Ks.end()), Ks.end());
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        x->opt_profile = saved_prof;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(x, FWIME_ECUDA, "autotune events");
+    }
+    auto timed = [&](auto &&body, int reps, float &us) -> int {
+        for (int it = 0; it < 1; ++it) TRY(body());
+        CK(cudaEventRecord(e0, x->st));
+        for (int it = 0; it < reps; ++it) TRY(body());
+        CK(cudaEventRecord(e1, x->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        us = 1e3f * ms / reps;
+        return FWIME_OK;
+    };
+    double best = 1e300;
+    fwime_schedule out{};
+    int rc = FWIME_OK;
+    for (int K : Ks) {
+        x->opt_K = K;
+        x->opt_S = 0;
+        Run r;
+        rc = plan(x, op, r.w);
+        if (rc != FWIME_OK) { rc = FWIME_OK; continue; }   // this K does not fit: skip it
+        const int SK = r.w.S;
+        std::vector<int> Ss = {SK};
+        if (SK > 1) {
+            const int nb = (x->nshot + SK - 1) / SK;
+            Ss.push_back((x->nshot + 2 * nb - 1) / (2 * nb));
+        }
+        for (int S : Ss) {
+            x->opt_S = S;
+            rc = plan(x, op, r.w);
+            if (rc != FWIME_OK) break;
+            const long long SP = (long long)S * x->P;
+            // timing needs no model: zeros everywhere the kernels read
+            rc = zero(x, x->ws, x->ws_bytes);
+            if (rc != FWIME_OK) break;
+            // stencil: the chunking candidates (a ladder and whole waves of resident warps)
+            const int rows = x->NZ - 8;
+            std::vector<int> cand = {16, 32, 48, 64, 96, 128};
+            int bps = 0, nsm = 0, dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess && prop_occupancy(&bps) == cudaSuccess &&
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && bps > 0) {
+                const long long resident = (long long)bps * nsm * PROP_WARPS;
+                const long long per_chunk = (long long)((x->NXP + STRIP - 1) / STRIP) * S;
+                for (int waves = 1; waves <= 12; ++waves) {
+                    const long long nchunk = (waves * resident) / per_chunk;
+                    if (nchunk < 1) continue;
+                    const int zc = (int)((rows + nchunk - 1) / nchunk);
+                    if (zc >= 4 && zc <= 512) cand.push_back(zc);
+                }
+            }
+            cudaGetLastError();
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            float tp = 1e30f;
+            int zbest = 0;
+            for (int zc : cand) {
+                if (zc > rows && zc != cand.front()) break;
+                x->opt_zchunk = zc;
+                init_run(x, r, S);
+                float us = 0.f;
+                rc = timed([&]() { return prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0); }, 4, us);
+                if (rc != FWIME_OK) break;
+                if (us < tp) { tp = us; zbest = zc; }
+            }
+            if (rc != FWIME_OK) break;
+            x->opt_zchunk = zbest;
+            init_run(x, r, S);
+            const int kk = std::min(K, x->g.nt - 1);
+            float tsc = 0.f, tim = 0.f;
+            if (!lag && SCAT[op] > 0 && r.w.W && r.w.ring[0] && r.w.ring[1]) {
+                rc = timed([&]() {
+                    return scatter(r, S, 0, kk, r.w.W, ringref(r.w.ring[0], SP, 0, 0), ringref(r.w.ring[1], SP, 0, 0),
+                                   +1, 0);
+                }, 2, tsc);
+                if (rc != FWIME_OK) break;
+            }
+            float *img_acc = op == FWIME_OP_BORN_EXT_ADJ ? r.w.acc1 : r.w.acc2;
+            float *lring = op == FWIME_OP_BORN_EXT_ADJ ? r.w.ring[1] : r.w.ring[3];
+            if (!lag && IMGS[op] > 0 && img_acc && r.w.ring[0] && lring) {
+                rc = timed([&]() {
+                    return image(r, S, 0, kk, IMG_EXT, ringref(r.w.ring[0], SP, 0, 0), ringref(lring, SP, r.w.R, 1),
+                                 ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 1.f, nullptr, img_acc);
+                }, 2, tim);
+                if (rc != FWIME_OK) break;
+            }
+            const double nseg = (double)r.w.nseg;
+            const double per_shot = ((double)(x->g.nt - 1) * PROPS[op] * tp + nseg * (SCAT[op] * tsc + IMGS[op] * tim)) / S;
+            if (per_shot < best) {
+                best = per_shot;
+                out.shots_per_batch = S;
+                out.segment = K;
+                out.zchunk = zbest;
+                out.us_stencil = tp;
+                out.us_scatter = tsc;
+                out.us_image = tim;
+                out.us_per_shot = per_shot;
+            }
+        }
+        if (rc != FWIME_OK) break;
+    }
+    cleanup();
+    if (rc != FWIME_OK || best >= 1e299) {
+        x->opt_K = saved_K; x->opt_S = saved_S; x->opt_zchunk = saved_zc;
+        return rc != FWIME_OK ? rc : fail(x, FWIME_ENOMEM, "no schedule fits");
+    }
+    x->opt_K = out.segment;
+    x->opt_S = out.shots_per_batch;
+    x->opt_zchunk = out.zchunk;
+    *res = out;
+    return FWIME_OK;
+}
+
 int fwime_objective(fwime_ctx *x, const float *v, const float *w, const float *pt, const float *dobs, float eps,
                     double *objective)
 {

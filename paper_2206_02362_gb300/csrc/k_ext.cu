@@ -246,11 +246,16 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     auto issue = [&](int p) {
         if (p < a.npair) {
             const unsigned d = sm0 + st_in;
+            // samples n = lane + 32 c of the window [0, SPAN): the last round copies only its first REM
+            // lanes' samples (nothing past the window is read, from memory or from shared memory)
+            constexpr int REM = Sh::SPAN - 32 * (Sh::NCP - 1);
             if (interior) {
-                cpa4_run<64, 128>(d, pin.row + col0, std::make_integer_sequence<int, Sh::NCP>{});
+                cpa4_run<64, 128>(d, pin.row + col0, std::make_integer_sequence<int, Sh::NCP - 1>{});
+                if (REM == 32 || lane < REM) cpa4_imm<64 * (Sh::NCP - 1), 128 * (Sh::NCP - 1)>(d, pin.row + col0);
             } else {
 #pragma unroll
                 for (int c = 0; c < Sh::NCP; ++c) {
+                    if (c == Sh::NCP - 1 && REM < 32 && lane >= REM) break;
                     const int col = col0 + 32 * c;
                     const bool ok = col >= 0 && col < a.NXP;
                     cpa4(d + 64u * c, pin.row + (ok ? col : 0), ok);

@@ -379,13 +379,6 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
         row_math<LOC, D2, SRC>(a, prop_k(a), L, q[(0 + (R)) % 9], q[(1 + (R)) % 9], q[(2 + (R)) % 9], q[(3 + (R)) % 9], \
                                  q[(4 + (R)) % 9], q[(5 + (R)) % 9], q[(6 + (R)) % 9], q[(7 + (R)) % 9],      \
                                  q[(8 + (R)) % 9], Rr, pv, cv, lf0, lf1, lf2, lcf, lfc, gzz, gxv, sj, amp, o, d2); \
-        if (INJ && zz >= a.inj_lo && zz < a.inj_hi && xin) { /* receivers on this row (warp-uniform) */      \
-            const int4 m4 = *reinterpret_cast<const int4 *>(a.inj_map + (long long)(zz - a.inj_lo) * NXP + x); \
-            inject_point(a, shot, m4.x, cv.x, o.x);                                                          \
-            inject_point(a, shot, m4.y, cv.y, o.y);                                                          \
-            inject_point(a, shot, m4.z, cv.z, o.z);                                                          \
-            inject_point(a, shot, m4.w, cv.w, o.w);                                                          \
-        }                                                                                                    \
         if (xin) {                                                                                           \
             st4(out + idx, o);                                                                               \
             if (D2 && zz >= a.zs_lo && zz < a.zs_hi) st4(a.d2 + so + idx, d2);                               \
@@ -408,11 +401,28 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
     }
 #undef FWIME_PROP_ROW
     cp_wait<0>();
+    if (INJ && xin) {
+        // receivers in this warp's rows: each lane adds the injection to the outputs it wrote itself (read
+        // back by the writing thread), after the march so the loop above keeps its registers
+        const int zlo = max(z0, a.inj_lo), zhi = min(z1, a.inj_hi);
+        for (int zz = zlo; zz < zhi; ++zz) {
+            const int4 m4 = *reinterpret_cast<const int4 *>(a.inj_map + (long long)(zz - a.inj_lo) * NXP + x);
+            if ((m4.x & m4.y & m4.z & m4.w) < 0) continue;   // none of the lane's four points
+            const long long idx = (long long)zz * NXP + x;
+            float4 o = *reinterpret_cast<const float4 *>(out + idx);
+            const float4 cv = ldg4(a.c + idx);
+            inject_point(a, shot, m4.x, cv.x, o.x);
+            inject_point(a, shot, m4.y, cv.y, o.y);
+            inject_point(a, shot, m4.z, cv.z, o.z);
+            inject_point(a, shot, m4.w, cv.w, o.w);
+            st4(out + idx, o);
+        }
+    }
 }
 
 // INJ: the receivers' injection into the output (the adjoint step; LOC = 0, no D2t, no point source)
 template <int LOC, bool D2, bool SRC, bool INJ = false>
-__global__ void __launch_bounds__(PROP_WARPS * 32, INJ ? 4 : (LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN))) k_prop(const PropArgs a)
+__global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN)) k_prop(const PropArgs a)
 {
     extern __shared__ float4 smem4[];
     if (a.rec_d && blockIdx.x == 0) {         // receivers of the input field (the previous step's output)
