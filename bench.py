@@ -607,7 +607,8 @@ def main():
     torch.cuda.empty_cache()
     # FWIME gradient (Eqs. 7-9) on the North-Sea-shaped workload: batched vs plain shots/s
     if not args.no_grad and rank == 0:
-        line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots, tune=not args.no_tune)
+        line["gradient"] = gradient_section(fw, torch, dev, args.grad_shots,
+                                            tune=not args.no_tune and args.tune == "schedule")
     if not args.no_tlag and rank == 0 and world == 1:
         line["time_lag"] = time_lag_section(fw, torch, dev, wl)
     # Salt-shaped batched gradient with checkpoint/recompute (a shot subset)
