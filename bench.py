@@ -417,7 +417,7 @@ def ncu_traffic():
         return None
     return {"dram_bytes_per_launch": float(t.group(1)),
             "algorithmic_bytes_per_launch": float(a.group(1)) if a else None,
-            "captured": "every k_prop launch of one timed bench step (full size, 100 shots, nt 200), 1-pass ncu",
+            "captured": "every k_prop launch of one timed bench step (full-size launches: 100 shots, nt 40), 1-pass ncu",
             "source": "profiles/k_prop_marmousi2_ncu.md"}
 
 
