@@ -577,7 +577,10 @@ static void ext_cols(fwime_ctx *x, int &lo, int &hi)
     hi = std::min(x->NX - 4, x->o + x->g.nx + hm);
 }
 
-static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, RingRef out, int sigma, int accumulate)
+// with y (transposed scatter into a ring only): also y^m = (z^{m-1} - 2 z^m + z^{m+1}) idt2 for
+// m in (n0, n0 + kk] at y + (m - n0 - 1) slots, the source of the second adjoint field (Eq. 9)
+static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, RingRef out, int sigma, int accumulate,
+                   float *y = nullptr, float idt2 = 0.f)
 {
     fwime_ctx *x = r.x;
     ExtArgs a{};
@@ -585,8 +588,16 @@ static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, R
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz;
     ext_cols(x, a.x_lo, a.x_hi);   // the launcher may start a few columns earlier (zero weights there)
     a.sigma = sigma; a.W = W; a.in = in; a.outr = out; a.accumulate = accumulate;
+    if (y) {
+        a.yout = ringref(y, (long long)Sb * x->P, 0, 0);
+        a.yout.slot_stride = out.slot_stride;
+        a.idt2 = idt2;
+    }
     const double pts = (double)x->g.nz * (a.x_hi - a.x_lo);
-    LAUNCH(FWIME_K_SCATTER, pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0)) + 4.0 * x->g.nh),
+    // y: one more write per pair and point, two reads per shot and point (z past the segment)
+    LAUNCH(FWIME_K_SCATTER,
+           pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0) + (y ? 4 : 0)) + (y ? 8.0 * Sb : 0.0) +
+                 4.0 * x->g.nh),
            launch_scatter(a, x->st));
     return FWIME_OK;
 }
@@ -1356,13 +1367,13 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
                 float *mo = Mu + (m % R) * SP;
                 TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, rr + (size_t)m * x->nrec));
             }
-            // z^n = E_D^T(W, lambda^n) for n in [n0, n1)
-            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Mu, SP, R, 1), ringref(Zr, SP, R, 0), -1, 0));
-            // second adjoint field driven by d2t^T z
+            // z^n = E_D^T(W, lambda^n) for n in [n0, n1), and with it y^m = d2t^T z at m in (n0, n1] into
+            // the scattered-field ring (free again once the recomputed q_s is past this segment)
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Mu, SP, R, 1), ringref(Zr, SP, R, 0), -1, 0, Er, idt2));
+            // second adjoint field driven by y
             for (int m = n1; m >= n0 + 1; --m) {
                 TRY(prop(r, Sb, Mu2 + ((m + 1) % R) * SP, Mu2 + ((m + 2) % R) * SP, Mu2 + (m % R) * SP, nullptr,
-                         nullptr, 0, Zr + ((m - 1) % R) * SP, idt2, Zr + (m % R) * SP, -2.f * idt2,
-                         Zr + ((m + 1) % R) * SP, idt2));
+                         nullptr, 0, Er + (m - n0 - 1) * SP, 1.f));
             }
             TRY(image(r, Sb, n0, kk, IMG_LOCAL, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(Mu2, SP, R, 1),
                       ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc1));

@@ -272,6 +272,21 @@ def test_offsets_past_the_sponge_and_generic_nh(nh, W):
     with c.ctx(segment=13) as ctx:
         assert rel_l2(c.g_ext(ctx), oracle.born_ext(c.og, v, c.ogeo, w, c.pt.astype(np.float64))) <= TOL
         assert rel_l2(c.g_ext_adj(ctx), oracle.born_ext_adj(c.og, v, c.ogeo, w, c.d.astype(np.float64))) <= TOL
+        # T*: the transposed scatter also emits the second adjoint field's source (generic kernel + a
+        # separate second difference at nh 7, two outputs per lane at nh 41)
+        assert rel_l2(c.g_tomo_adj(ctx), oracle.tomo_adj(c.og, v, c.ogeo, w, c.pt.astype(np.float64),
+                                                         c.d.astype(np.float64))) <= TOL
+
+
+@pytest.mark.parametrize("segment", [1, 2, 3])
+def test_tomo_adj_short_segments(segment):
+    """Segments of one to three steps: the source of the second adjoint field at a segment's last
+    steps takes one or two samples of the transposed scatter from the segment after it."""
+    c = Case(nz=16, nx=120, W=6, nt=40, nh=5, nshot=3, seed=6)
+    v, w = c.v.astype(np.float64), c.w.astype(np.float64)
+    ref = oracle.tomo_adj(c.og, v, c.ogeo, w, c.pt.astype(np.float64), c.d.astype(np.float64))
+    with c.ctx(segment=segment, shots_per_batch=2) as ctx:
+        assert rel_l2(c.g_tomo_adj(ctx), ref) <= TOL
 
 
 def test_two_time_samples():
