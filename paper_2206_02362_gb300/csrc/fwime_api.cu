@@ -555,10 +555,12 @@ static int record(Run &r, int Sb, const float *f1, const float *f2, float *d, in
 }
 
 // One adjoint time step with the residual's injection at the receivers folded into the stencil launch
-// (the transpose of recording; the same arithmetic as a separate injection after the step)
-static int adj_step(Run &r, int Sb, const float *cur, const float *prev, float *out, const float *val)
+// (the transpose of recording; the same arithmetic as a separate injection after the step), and
+// optionally the D2t of its output, injection included
+static int adj_step(Run &r, int Sb, const float *cur, const float *prev, float *out, const float *val,
+                    float *d2 = nullptr)
 {
-    return prop(r, Sb, cur, prev, out, nullptr, nullptr, 0, nullptr, 0.f, nullptr, 0.f, nullptr, 0.f, nullptr,
+    return prop(r, Sb, cur, prev, out, d2, nullptr, 0, nullptr, 0.f, nullptr, 0.f, nullptr, 0.f, nullptr,
                 nullptr, RecTo{}, InjFrom{val});
 }
 
@@ -577,10 +579,7 @@ static void ext_cols(fwime_ctx *x, int &lo, int &hi)
     hi = std::min(x->NX - 4, x->o + x->g.nx + hm);
 }
 
-// with y (transposed scatter into a ring only): also y^m = (z^{m-1} - 2 z^m + z^{m+1}) idt2 for
-// m in (n0, n0 + kk] at y + (m - n0 - 1) slots, the source of the second adjoint field (Eq. 9)
-static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, RingRef out, int sigma, int accumulate,
-                   float *y = nullptr, float idt2 = 0.f)
+static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, RingRef out, int sigma, int accumulate)
 {
     fwime_ctx *x = r.x;
     ExtArgs a{};
@@ -588,16 +587,8 @@ static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, R
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz;
     ext_cols(x, a.x_lo, a.x_hi);   // the launcher may start a few columns earlier (zero weights there)
     a.sigma = sigma; a.W = W; a.in = in; a.outr = out; a.accumulate = accumulate;
-    if (y) {
-        a.yout = ringref(y, (long long)Sb * x->P, 0, 0);
-        a.yout.slot_stride = out.slot_stride;
-        a.idt2 = idt2;
-    }
     const double pts = (double)x->g.nz * (a.x_hi - a.x_lo);
-    // y: one more write per pair and point, two reads per shot and point (z past the segment)
-    LAUNCH(FWIME_K_SCATTER,
-           pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0) + (y ? 4 : 0)) + (y ? 8.0 * Sb : 0.0) +
-                 4.0 * x->g.nh),
+    LAUNCH(FWIME_K_SCATTER, pts * ((double)a.npair * (8.0 + (accumulate ? 4 : 0)) + 4.0 * x->g.nh),
            launch_scatter(a, x->st));
     return FWIME_OK;
 }
@@ -1290,7 +1281,6 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
     const bool report_J = grad && fwd;
     if (report_J) TRY(zero(x, x->d_J, sizeof(double)));
     const int nred = 1024;
-    const float idt2 = (float)(1.0 / ((double)x->g.dt * x->g.dt));
     float *res_state = state ? x->gs.buf + 4LL * nseg * x->nshot * x->P : nullptr;
     for (int s0 = 0; s0 < x->nshot; s0 += S) {
         const int Sb = std::min(S, x->nshot - s0);
@@ -1362,15 +1352,19 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
                 TRY(prop(r, Sb, qsc, qsp, qsp, Dsr + (n - n0) * SP, nullptr, 0, Er + (n - n0) * SP, 1.f));
                 std::swap(qsc, qsp);
             }
-            // adjoint of the residual: mu^m, m = n1 .. n0+1 (lambda^ at step n is mu^{n+1})
+            // adjoint of the residual: mu^m, m = n1 .. n0+1 (lambda^ at step n is mu^{n+1}), each step also
+            // writing its D2t, (mu^m - 2 mu^{m+1} + mu^{m+2}) / dt^2, at slot m - n0 - 1 of Zr
             for (int m = n1; m >= n0 + 1; --m) {
                 float *mo = Mu + (m % R) * SP;
-                TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, rr + (size_t)m * x->nrec));
+                TRY(adj_step(r, Sb, Mu + ((m + 1) % R) * SP, Mu + ((m + 2) % R) * SP, mo, rr + (size_t)m * x->nrec,
+                             Zr + (m - n0 - 1) * SP));
             }
-            // z^n = E_D^T(W, lambda^n) for n in [n0, n1), and with it y^m = d2t^T z at m in (n0, n1] into
-            // the scattered-field ring (free again once the recomputed q_s is past this segment)
-            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Mu, SP, R, 1), ringref(Zr, SP, R, 0), -1, 0, Er, idt2));
-            // second adjoint field driven by y
+            // The second adjoint field's source d2t^T z, z^n = E_D^T(W, lambda^n): E_D^T acts on space only,
+            // so y^m = (z^{m-1} - 2 z^m + z^{m+1}) / dt^2 = E_D^T(W, D2t of the step producing mu^m): one
+            // transposed scatter of those D2t into slots m - n0 - 1 of the scattered-field ring (free again
+            // once the recomputed q_s is past this segment; zero outside the scatter's columns, which only
+            // scatters write)
+            TRY(scatter(r, Sb, n0, kk, r.w.W, ringref(Zr, SP, 0, 0), ringref(Er, SP, 0, 0), -1, 0));
             for (int m = n1; m >= n0 + 1; --m) {
                 TRY(prop(r, Sb, Mu2 + ((m + 1) % R) * SP, Mu2 + ((m + 2) % R) * SP, Mu2 + (m % R) * SP, nullptr,
                          nullptr, 0, Er + (m - n0 - 1) * SP, 1.f));

@@ -148,11 +148,6 @@ struct ExtArgs {
     RingRef in;                    // D
     RingRef outr;                  // output ring (written through a non-const cast)
     int accumulate;
-    // sigma = -1 only, optional: also y^m = (z^{m-1} - 2 z^m + z^{m+1}) idt2 for m in [n0 + 1, n0 + K]
-    // (K = npair / S steps) into ring yout at slot m - n0 - 1 (direct ring), z^{n0+K} and z^{n0+K+1}
-    // read from outr (the previous segment's); the pairs are then walked step-fastest within each shot
-    RingRef yout;
-    float idt2;
 };
 
 enum { IMG_EXT = 0, IMG_CONTRACT = 1, IMG_LOCAL = 2 };

@@ -18,6 +18,7 @@
 // rows de-interleaved into their even and odd samples: the products of offset h
 // pair samples of one parity (y and y - 2h; x - h and x + h), so a lane that
 // owns samples of one parity reuses every loaded sample for several offsets.
+#include <algorithm>
 #include <utility>
 
 #include "fwime_kernels.cuh"
@@ -76,31 +77,23 @@ __device__ __forceinline__ void cpa4_run(unsigned dst, const float *src, std::in
 }
 
 // Row pointer of the (step, shot) pairs of a segment in order (shot fastest), advanced by one
-// addition per pair and a multiply only when the time slot changes.  With K > 0 the pairs are walked
-// step fastest instead: the K steps of shot 0, then those of shot 1, ...
+// addition per pair and a multiply only when the time slot changes.
 struct PairRow {
     const float *base, *row;
-    long long slot_stride, P, shot_off;
-    int S, mod, s, slot, slot0, K, j;
-    __device__ __forceinline__ void init(const RingRef &r, int n0, int S_, long long P_, long long rowoff, int K_ = 0)
+    long long slot_stride, P;
+    int S, mod, s, slot;
+    // starting at pair p0
+    __device__ __forceinline__ void init(const RingRef &r, int n0, int S_, long long P_, long long rowoff, int p0 = 0)
     {
-        base = r.base + rowoff; slot_stride = r.slot_stride; P = P_; S = S_; mod = r.mod; s = 0;
-        slot = slot0 = r.mod > 0 ? (n0 + r.shift) % r.mod : r.shift;
-        K = K_; j = 0; shot_off = 0;
-        row = base + (long long)slot * slot_stride;
+        base = r.base + rowoff; slot_stride = r.slot_stride; P = P_; S = S_; mod = r.mod;
+        const int step = p0 / S_;
+        s = p0 % S_;
+        slot = r.mod > 0 ? (n0 + r.shift + step) % r.mod : r.shift + step;
+        row = base + (long long)slot * slot_stride + (long long)s * P_;
     }
     __device__ __forceinline__ void next()
     {
-        if (K > 0) {                       // step fastest
-            if (++j == K) {
-                j = 0;
-                shot_off += P;
-                slot = slot0;
-            } else if (++slot == mod) {
-                slot = 0;
-            }
-            row = base + (long long)slot * slot_stride + shot_off;
-        } else if (++s == S) {
+        if (++s == S) {
             s = 0;
             if (++slot == mod) slot = 0;   // mod == 0 (direct rings) never wraps
             row = base + (long long)slot * slot_stride;
@@ -109,36 +102,6 @@ struct PairRow {
         }
     }
 };
-
-// A consecutive outputs at o (float4 / float2 when they all lie below x_hi)
-template <int A>
-__device__ __forceinline__ void load_out(float (&v)[A], const float *o, int ys, int x_hi)
-{
-    if (ys + A <= x_hi) {
-        if constexpr (A == 4) {
-            const float4 t = *reinterpret_cast<const float4 *>(o);
-            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-        } else {
-            const float2 t = *reinterpret_cast<const float2 *>(o);
-            v[0] = t.x; v[1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < A; ++k) v[k] = ys + k < x_hi ? o[k] : 0.f;
-    }
-}
-template <int A>
-__device__ __forceinline__ void store_out(float *o, const float (&v)[A], int ys, int x_hi)
-{
-    if (ys + A <= x_hi) {
-        if constexpr (A == 4) *reinterpret_cast<float4 *>(o) = make_float4(v[0], v[1], v[2], v[3]);
-        else *reinterpret_cast<float2 *>(o) = make_float2(v[0], v[1]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < A; ++k)
-            if (ys + k < x_hi) o[k] = v[k];
-    }
-}
 
 // ------------------------------------------------------------------ scatter
 
@@ -200,6 +163,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #define FWIME_SC_PAIRS 0      // (step, shot) pairs per loop iteration of the scatter (sharing its weights);
                               // 0: two at nh 21 and 31 (measured -4.3 % at nh 31, -0.6 % at nh 21), else one
 #endif
+#ifndef FWIME_SC_BALANCE
+#define FWIME_SC_BALANCE 1    // split the scatter's pairs over several warps per task to fill the last wave
+#endif
 #ifndef FWIME_SC_PACK_MAX
 #define FWIME_SC_PACK_MAX 96   // largest nh * A whose weights are packed (more spills)
 #endif
@@ -223,21 +189,26 @@ struct ScatterShape {
     static_assert(OFF >= HALF + 16 && 15 * A + NWV <= OFF, "parity array overflow");
 };
 
-// YM (SIGMA = -1): also the time second difference y of the outputs, pairs walked step fastest
-template <int NH, int A, int SIGMA, bool YM = false>
-__global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(const ExtArgs a, int nwx)
+template <int NH, int A, int SIGMA>
+__global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(const ExtArgs a, int nwx, int nsplit)
 {
-    static_assert(!YM || SIGMA < 0, "the time second difference is a transposed-scatter output");
     using Sh = ScatterShape<NH, A>;
     constexpr int HM = Sh::HM, NS = SC_STAGES;
     extern __shared__ float4 sm4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wsm = reinterpret_cast<float *>(sm4) + warp * NS * Sh::STG;
-    // warps are numbered over (row, column block) so that no warp of a CTA idles at a row's end
-    const int gw = blockIdx.x * SC_WARPS + warp;
-    if (gw >= nwx * (a.z_hi - a.z_lo)) return;     // whole warp; no block-wide barrier follows
-    const int Z = a.z_lo + gw / nwx;
-    const int yw = a.x_lo + (gw % nwx) * Sh::WOUT;  // multiple of 4
+    // Warps are numbered over (row, column block, part) so that no warp of a CTA idles at a row's end;
+    // each of a task's nsplit parts takes an equal share of its (step, shot) pairs,
+    // the split chosen on the host so that the segment-long CTAs fill their last wave.  Warps share
+    // nothing: no block-wide barrier follows.
+    const long long gw = (long long)blockIdx.x * SC_WARPS + warp;
+    if (gw >= (long long)nwx * (a.z_hi - a.z_lo) * nsplit) return;
+    const long long task = gw / nsplit;
+    const int part = (int)(gw % nsplit);
+    const int pb = (int)((long long)part * a.npair / nsplit), pe = (int)((long long)(part + 1) * a.npair / nsplit);
+    if (pb == pe) return;
+    const int Z = a.z_lo + (int)(task / nwx);
+    const int yw = a.x_lo + (int)(task % nwx) * Sh::WOUT;  // multiple of 4
     const int par = lane >> 4, tp = lane & 15;
     const int yf = yw + par + 2 * A * tp;          // this lane's outputs yf + 2j, j < A
     const long long rowoff = (long long)Z * a.NXP;
@@ -283,16 +254,12 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     const int col0 = wal + lane;
     const bool interior = wal >= 0 && wal + 32 * Sh::NCP <= a.NXP;
     PairRow pin, pout;
-    const int KY = YM ? a.npair / a.S : 0;         // steps per shot (step-fastest walk)
-    pin.init(a.in, a.n0, a.S, a.P, rowoff, KY);
-    pout.init(a.outr, a.n0, a.S, a.P, rowoff, KY);
-    float h1[A] = {}, h2[A] = {};                  // YM: z of the two previous steps of this shot
-    int jy = 0;                                    // YM: step index within the shot
-    long long yshot = 0;                           // YM: the shot's offset in the rings
+    pin.init(a.in, a.n0, a.S, a.P, rowoff, pb);
+    pout.init(a.outr, a.n0, a.S, a.P, rowoff, pb);
     unsigned st_in = 0;
     int st_c = 0;
     auto issue = [&](int p) {
-        if (p < a.npair) {
+        if (p < pe) {
             const unsigned d = sm0 + st_in;
             // samples n = lane + 32 c of the window [0, SPAN): the last round copies only its first REM
             // lanes' samples (nothing past the window is read, from memory or from shared memory)
@@ -318,11 +285,11 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     constexpr int PP = FWIME_SC_PAIRS > 0 ? FWIME_SC_PAIRS : (NH == 21 || NH == 31 ? 2 : 1);
     static_assert(NS >= 2 * PP, "ring too short for the pairs per iteration");
 #pragma unroll 1
-    for (int q = 0; q < NS - PP; ++q) issue(q);
+    for (int q = 0; q < NS - PP; ++q) issue(pb + q);
     const int ys = yw + 2 * A * tp + A * par;      // first of the A consecutive outputs this lane stores
     const float *lsm = wsm + par * Sh::OFF + A * tp;
 #pragma unroll 1
-    for (int p = 0; p < a.npair; p += PP) {
+    for (int p = pb; p < pe; p += PP) {
         cpa_wait<NS - 2 * PP>();                   // pairs p .. p + PP - 1 have landed (this lane's copies) ...
         __syncwarp();                              // ... and every lane's; all finished the pairs before
 #pragma unroll
@@ -396,7 +363,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
         }
 #pragma unroll
         for (int u = 0; u < PP; ++u) {
-            if (PP > 1 && p + u >= a.npair) break;   // warp-uniform
+            if (PP > 1 && p + u >= pe) break;   // warp-uniform
             float v[A];
             if constexpr (A == 4) {
                 const float r0 = __shfl_xor_sync(0xffffffffu, par ? e[u][0] : e[u][2], 16);
@@ -409,36 +376,6 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
             }
             float *o = const_cast<float *>(pout.row) + ys;
             pout.next();
-            if constexpr (YM) {
-                // y^{n-1} = (z^{n-2} - 2 z^{n-1} + z^n) idt2 once two steps are behind; at the shot's last
-                // step also y^{n1-1} and y^{n1} from z^{n1}, z^{n1+1} of the previous segment (n1 = n0 + K)
-                float *yrow = const_cast<float *>(a.yout.base) + yshot + rowoff + ys;
-                if (jy >= 2) {
-                    float y[A];
-#pragma unroll
-                    for (int k = 0; k < A; ++k) y[k] = (fmaf(-2.f, h1[k], h2[k]) + v[k]) * a.idt2;
-                    store_out<A>(yrow + (long long)(jy - 2) * a.yout.slot_stride, y, ys, a.x_hi);
-                }
-#pragma unroll
-                for (int k = 0; k < A; ++k) { h2[k] = h1[k]; h1[k] = v[k]; }
-                if (++jy == KY) {
-                    const int n1 = a.n0 + KY;
-                    const float *zb = a.outr.base + yshot + rowoff + ys;
-                    float z1[A], z2[A], y[A];
-                    load_out<A>(z1, zb + (long long)(n1 % a.outr.mod) * a.outr.slot_stride, ys, a.x_hi);
-                    load_out<A>(z2, zb + (long long)((n1 + 1) % a.outr.mod) * a.outr.slot_stride, ys, a.x_hi);
-                    if (KY >= 2) {
-#pragma unroll
-                        for (int k = 0; k < A; ++k) y[k] = (fmaf(-2.f, h1[k], h2[k]) + z1[k]) * a.idt2;
-                        store_out<A>(yrow + (long long)(KY - 2) * a.yout.slot_stride, y, ys, a.x_hi);
-                    }
-#pragma unroll
-                    for (int k = 0; k < A; ++k) y[k] = (fmaf(-2.f, z1[k], h1[k]) + z2[k]) * a.idt2;
-                    store_out<A>(yrow + (long long)(KY - 1) * a.yout.slot_stride, y, ys, a.x_hi);
-                    jy = 0;
-                    yshot += a.P;
-                }
-            }
             if (ys + A <= a.x_hi) {
                 if constexpr (A == 4) {
                     float4 w4 = make_float4(v[0], v[1], v[2], v[3]);
@@ -509,44 +446,41 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
     a.x_lo -= a.x_lo % 4;          // outputs start on a 16-byte boundary (leading columns get zero weights)
     const int nwx = (a.x_hi - a.x_lo + Sh::WOUT - 1) / Sh::WOUT;        // warps per row
     const long long nw = (long long)nwx * (a.z_hi - a.z_lo);
-    dim3 grid((unsigned)((nw + SC_WARPS - 1) / SC_WARPS));
     static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    static int resident = 0;       // CTAs per SM of the less resident of the two variants
     if (!attr) {
         cudaFuncSetAttribute(k_scatter_ps<NH, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         cudaFuncSetAttribute(k_scatter_ps<NH, A, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        cudaFuncSetAttribute(k_scatter_ps<NH, A, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Sh::SMEM);
+        int r1 = 0, r2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r1, k_scatter_ps<NH, A, 1>, SC_WARPS * 32, Sh::SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r2, k_scatter_ps<NH, A, -1>, SC_WARPS * 32, Sh::SMEM);
+        resident = std::max(1, std::min(r1, r2));
         attr = true;
     }
-    if (a.sigma > 0) k_scatter_ps<NH, A, 1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
-    else if (a.yout.base) k_scatter_ps<NH, A, -1, true><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
-    else k_scatter_ps<NH, A, -1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx);
-}
-
-// y^m = (z^{m-1} - 2 z^m + z^{m+1}) idt2, m = n0 + 1 + j, j < K, over the scatter's region (the
-// time second difference after the generic-nh transposed scatter)
-__global__ void k_second_diff(const ExtArgs a, int K)  // grid (columns / 128, K, rows)
-{
-    const int x = a.x_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.x_hi) return;
-    const int j = blockIdx.y, m = a.n0 + 1 + j, R = a.outr.mod;
-    for (int s = 0; s < a.S; ++s) {
-        const long long off = (long long)s * a.P + (long long)(a.z_lo + blockIdx.z) * a.NXP + x;
-        const float *z = a.outr.base + off;
-        const float zm = z[(long long)((m - 1) % R) * a.outr.slot_stride],
-                    z0 = z[(long long)(m % R) * a.outr.slot_stride], zp = z[(long long)((m + 1) % R) * a.outr.slot_stride];
-        const_cast<float *>(a.yout.base)[off + (long long)j * a.yout.slot_stride] = (fmaf(-2.f, z0, zm) + zp) * a.idt2;
+    // Split every task's pairs into nsplit parts, nsplit <= 8 and parts of at least 4 ring depths of
+    // pairs, picked to fill the last wave of resident CTAs best (the smallest within 1 %).
+    int nsplit = 1;
+    if (FWIME_SC_BALANCE) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const double wave = (double)resident * std::max(nsm, 1);
+        auto fill = [&](int k) {   // used fraction of the launch's waves of CTAs
+            const double w = std::ceil((double)nw * k / SC_WARPS) / wave;
+            return w / std::ceil(w);
+        };
+        double best = fill(1);
+        for (int k = 2; k <= 8 && a.npair / k >= 4 * SC_STAGES; ++k)
+            if (fill(k) > best + 0.01) { best = fill(k); nsplit = k; }
     }
+    dim3 grid((unsigned)((nw * nsplit + SC_WARPS - 1) / SC_WARPS));
+    if (a.sigma > 0) k_scatter_ps<NH, A, 1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx, nsplit);
+    else k_scatter_ps<NH, A, -1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx, nsplit);
 }
 
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
 {
     if (a.npair <= 0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
-    // the second-difference output: transposed, written (not added), whole shots of K steps in a ring
-    // that keeps the two samples past the segment (z^{n0+K}, z^{n0+K+1} not overwritten)
-    if (a.yout.base && (a.sigma > 0 || a.accumulate || a.S <= 0 || a.npair % a.S != 0 ||
-                        a.outr.mod < a.npair / a.S + 2 || a.outr.shift != 0))
-        return cudaErrorInvalidValue;
     switch (a.nh) {
     case 1: launch_scatter_ps<1, 4>(a, st); break;
     case 3: launch_scatter_ps<3, 4>(a, st); break;
@@ -559,10 +493,6 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
         dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
         const int hm = (a.nh - 1) / 2;
         k_scatter_gen<<<grid, EXT_TX, (EXT_TX + 4 * hm) * sizeof(float), st>>>(a);
-        if (a.yout.base) {
-            const int K = a.npair / a.S;
-            k_second_diff<<<dim3((a.x_hi - a.x_lo + 127) / 128, K, a.z_hi - a.z_lo), 128, 0, st>>>(a, K);
-        }
     }
     }
     return cudaGetLastError();

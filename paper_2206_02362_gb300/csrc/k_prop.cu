@@ -409,18 +409,30 @@ __device__ __forceinline__ void prop_body(const PropArgs &a, const int wid, cons
             const int4 m4 = *reinterpret_cast<const int4 *>(a.inj_map + (long long)(zz - a.inj_lo) * NXP + x);
             if ((m4.x & m4.y & m4.z & m4.w) < 0) continue;   // none of the lane's four points
             const long long idx = (long long)zz * NXP + x;
-            float4 o = *reinterpret_cast<const float4 *>(out + idx);
+            const float4 o0 = *reinterpret_cast<const float4 *>(out + idx);
+            float4 o = o0;
             const float4 cv = ldg4(a.c + idx);
             inject_point(a, shot, m4.x, cv.x, o.x);
             inject_point(a, shot, m4.y, cv.y, o.y);
             inject_point(a, shot, m4.z, cv.z, o.z);
             inject_point(a, shot, m4.w, cv.w, o.w);
             st4(out + idx, o);
+            if (D2 && zz >= a.zs_lo && zz < a.zs_hi) {
+                // the D2t output gains the injection too: d2 + (o - o0) / dt^2
+                float *dp = a.d2 + so + idx;
+                float4 d = *reinterpret_cast<const float4 *>(dp);
+                d.x = fmaf(o.x - o0.x, a.inv_dt2, d.x);
+                d.y = fmaf(o.y - o0.y, a.inv_dt2, d.y);
+                d.z = fmaf(o.z - o0.z, a.inv_dt2, d.z);
+                d.w = fmaf(o.w - o0.w, a.inv_dt2, d.w);
+                st4(dp, d);
+            }
         }
     }
 }
 
-// INJ: the receivers' injection into the output (the adjoint step; LOC = 0, no D2t, no point source)
+// INJ: the receivers' injection into the output (the adjoint step; LOC = 0, no point source; with D2 the
+// injection reaches the D2t output as well)
 template <int LOC, bool D2, bool SRC, bool INJ = false>
 __global__ void __launch_bounds__(PROP_WARPS * 32, LOC == 2 ? FWIME_PROP_MIN_BLOCKS : (LOC == 1 ? FWIME_PROP_MINB_LOC1 : FWIME_PROP_MINB_PLAIN)) k_prop(const PropArgs a)
 {
@@ -531,9 +543,10 @@ cudaError_t launch_prop(const PropArgs &a0, int nshot, cudaStream_t st)
     const size_t smem = (size_t)PROP_WARPS * (CUR_SLOTS * CUR_ROW + AUX_SLOTS * a.naux_max * STRIP) * sizeof(float);
     const int loc = !local ? 0 : (a.f1 || a.f2 || a.fc || !a.f0) ? 2 : 1;
     const int key = loc * 4 + (d2 ? 2 : 0) + (src ? 1 : 0);
-    if (a.inj_val) {                           // the caller injects only into plain steps
-        if (key != 0) return cudaErrorInvalidValue;
-        launch_prop_t<0, false, false, true>(a, grid, block, smem, st);
+    if (a.inj_val) {                           // the caller injects only into plain steps, with or without D2t
+        if (key != 0 && key != 2) return cudaErrorInvalidValue;
+        if (d2) launch_prop_t<0, true, false, true>(a, grid, block, smem, st);
+        else launch_prop_t<0, false, false, true>(a, grid, block, smem, st);
         return cudaGetLastError();
     }
     switch (key) {

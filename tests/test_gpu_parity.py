@@ -278,6 +278,18 @@ def test_offsets_past_the_sponge_and_generic_nh(nh, W):
                                                          c.d.astype(np.float64))) <= TOL
 
 
+def test_scatter_pairs_split_over_warps():
+    """Few (row, column block) tasks and long segments: the scatter splits every task's pairs (shots,
+    for the transposed one of T*) over several warps to fill the last wave of resident CTAs."""
+    c = Case(nz=64, nx=600, W=10, nt=121, nh=5, nshot=4, seed=8)
+    v, w = c.v.astype(np.float64), c.w.astype(np.float64)
+    with c.ctx(segment=60) as ctx:
+        assert rel_l2(c.g_ext(ctx), oracle.born_ext(c.og, v, c.ogeo, w, c.pt.astype(np.float64))) <= TOL
+        assert rel_l2(c.g_ext_adj(ctx), oracle.born_ext_adj(c.og, v, c.ogeo, w, c.d.astype(np.float64))) <= TOL
+        assert rel_l2(c.g_tomo_adj(ctx), oracle.tomo_adj(c.og, v, c.ogeo, w, c.pt.astype(np.float64),
+                                                         c.d.astype(np.float64))) <= TOL
+
+
 @pytest.mark.parametrize("segment", [1, 2, 3])
 def test_tomo_adj_short_segments(segment):
     """Segments of one to three steps: the source of the second adjoint field at a segment's last
