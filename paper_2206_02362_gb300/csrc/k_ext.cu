@@ -189,7 +189,8 @@ struct ScatterShape {
     static_assert(OFF >= HALF + 16 && 15 * A + NWV <= OFF, "parity array overflow");
 };
 
-template <int NH, int A, int SIGMA>
+// SPLIT: each (row, column block) task's pairs are divided among nsplit warps
+template <int NH, int A, int SIGMA, bool SPLIT>
 __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(const ExtArgs a, int nwx, int nsplit)
 {
     using Sh = ScatterShape<NH, A>;
@@ -197,18 +198,22 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     extern __shared__ float4 sm4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wsm = reinterpret_cast<float *>(sm4) + warp * NS * Sh::STG;
-    // Warps are numbered over (row, column block, part) so that no warp of a CTA idles at a row's end;
-    // each of a task's nsplit parts takes an equal share of its (step, shot) pairs,
-    // the split chosen on the host so that the segment-long CTAs fill their last wave.  Warps share
-    // nothing: no block-wide barrier follows.
-    const long long gw = (long long)blockIdx.x * SC_WARPS + warp;
-    if (gw >= (long long)nwx * (a.z_hi - a.z_lo) * nsplit) return;
-    const long long task = gw / nsplit;
-    const int part = (int)(gw % nsplit);
-    const int pb = (int)((long long)part * a.npair / nsplit), pe = (int)((long long)(part + 1) * a.npair / nsplit);
-    if (pb == pe) return;
-    const int Z = a.z_lo + (int)(task / nwx);
-    const int yw = a.x_lo + (int)(task % nwx) * Sh::WOUT;  // multiple of 4
+    // Warps are numbered over (row, column block[, part]) so that no warp of a CTA idles at a row's end;
+    // with SPLIT each of a task's nsplit parts takes an equal share of its (step, shot) pairs, the split
+    // chosen on the host so that the segment-long CTAs fill their last wave (the bounds cost registers,
+    // so the unsplit variant keeps the whole range).  Warps share nothing: no block-wide barrier follows.
+    const int gw = blockIdx.x * SC_WARPS + warp;   // 32-bit indexing (64-bit spills at nh 31)
+    if (gw >= nwx * (a.z_hi - a.z_lo) * (SPLIT ? nsplit : 1)) return;
+    const int task = SPLIT ? gw / nsplit : gw;
+    int pb = 0, pe = a.npair;
+    if constexpr (SPLIT) {
+        const int part = (int)(gw % nsplit);
+        pb = (int)((long long)part * a.npair / nsplit);
+        pe = (int)((long long)(part + 1) * a.npair / nsplit);
+        if (pb == pe) return;
+    }
+    const int Z = a.z_lo + task / nwx;
+    const int yw = a.x_lo + (task % nwx) * Sh::WOUT;  // multiple of 4
     const int par = lane >> 4, tp = lane & 15;
     const int yf = yw + par + 2 * A * tp;          // this lane's outputs yf + 2j, j < A
     const long long rowoff = (long long)Z * a.NXP;
@@ -446,21 +451,30 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
     a.x_lo -= a.x_lo % 4;          // outputs start on a 16-byte boundary (leading columns get zero weights)
     const int nwx = (a.x_hi - a.x_lo + Sh::WOUT - 1) / Sh::WOUT;        // warps per row
     const long long nw = (long long)nwx * (a.z_hi - a.z_lo);
+    // split variants where their two bounds fit the register budget without spills
+    constexpr bool CAN_SPLIT = FWIME_SC_BALANCE && NH <= 21;
     static bool attr = false;      // once per instantiation, before any launch (and any capture)
-    static int resident = 0;       // CTAs per SM of the less resident of the two variants
+    static int resident = 0;       // CTAs per SM of the least resident variant
     if (!attr) {
-        cudaFuncSetAttribute(k_scatter_ps<NH, A, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        cudaFuncSetAttribute(k_scatter_ps<NH, A, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        int r1 = 0, r2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r1, k_scatter_ps<NH, A, 1>, SC_WARPS * 32, Sh::SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r2, k_scatter_ps<NH, A, -1>, SC_WARPS * 32, Sh::SMEM);
-        resident = std::max(1, std::min(r1, r2));
+        int r[4] = {0, 0, 0, 0};
+        const auto setup = [&](auto kern, int &res) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, kern, SC_WARPS * 32, Sh::SMEM);
+        };
+        setup(k_scatter_ps<NH, A, 1, false>, r[0]);
+        setup(k_scatter_ps<NH, A, -1, false>, r[1]);
+        r[2] = r[3] = r[0];
+        if constexpr (CAN_SPLIT) {
+            setup(k_scatter_ps<NH, A, 1, true>, r[2]);
+            setup(k_scatter_ps<NH, A, -1, true>, r[3]);
+        }
+        resident = std::max(1, std::min(std::min(r[0], r[1]), std::min(r[2], r[3])));
         attr = true;
     }
     // Split every task's pairs into nsplit parts, nsplit <= 8 and parts of at least 4 ring depths of
     // pairs, picked to fill the last wave of resident CTAs best (the smallest within 1 %).
     int nsplit = 1;
-    if (FWIME_SC_BALANCE) {
+    if (CAN_SPLIT) {
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -474,8 +488,17 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
             if (fill(k) > best + 0.01) { best = fill(k); nsplit = k; }
     }
     dim3 grid((unsigned)((nw * nsplit + SC_WARPS - 1) / SC_WARPS));
-    if (a.sigma > 0) k_scatter_ps<NH, A, 1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx, nsplit);
-    else k_scatter_ps<NH, A, -1><<<grid, SC_WARPS * 32, Sh::SMEM, st>>>(a, nwx, nsplit);
+    const int nt = SC_WARPS * 32;
+    if (nsplit > 1) {
+        if constexpr (CAN_SPLIT) {
+            if (a.sigma > 0) k_scatter_ps<NH, A, 1, true><<<grid, nt, Sh::SMEM, st>>>(a, nwx, nsplit);
+            else k_scatter_ps<NH, A, -1, true><<<grid, nt, Sh::SMEM, st>>>(a, nwx, nsplit);
+        }
+    } else if (a.sigma > 0) {
+        k_scatter_ps<NH, A, 1, false><<<grid, nt, Sh::SMEM, st>>>(a, nwx, 1);
+    } else {
+        k_scatter_ps<NH, A, -1, false><<<grid, nt, Sh::SMEM, st>>>(a, nwx, 1);
+    }
 }
 
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
