@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(SC_WARPS * 32, FWIME_SC_MINB) k_scatter_ps(con
     float *wsm = reinterpret_cast<float *>(sm4) + warp * NS * Sh::STG;
     // Warps are numbered over (row, column block[, part]) so that no warp of a CTA idles at a row's end;
     // with SPLIT each of a task's nsplit parts takes an equal share of its (step, shot) pairs, the split
-    // chosen on the host so that the segment-long CTAs fill their last wave (the bounds cost registers,
-    // so the unsplit variant keeps the whole range).  Warps share nothing: no block-wide barrier follows.
-    const int gw = blockIdx.x * SC_WARPS + warp;   // 32-bit indexing (64-bit spills at nh 31)
+    // chosen on the host so that the segment-long CTAs fill their last wave (the unsplit variant keeps
+    // the whole range, a kernel parameter, out of its registers).  Warps share nothing: no block-wide
+    // barrier follows.
+    const int gw = blockIdx.x * SC_WARPS + warp;   // 32-bit indexing (64-bit indexing spilled at nh 31)
     if (gw >= nwx * (a.z_hi - a.z_lo) * (SPLIT ? nsplit : 1)) return;
     const int task = SPLIT ? gw / nsplit : gw;
     int pb = 0, pe = a.npair;
@@ -451,8 +452,7 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
     a.x_lo -= a.x_lo % 4;          // outputs start on a 16-byte boundary (leading columns get zero weights)
     const int nwx = (a.x_hi - a.x_lo + Sh::WOUT - 1) / Sh::WOUT;        // warps per row
     const long long nw = (long long)nwx * (a.z_hi - a.z_lo);
-    // split variants where their two bounds fit the register budget without spills
-    constexpr bool CAN_SPLIT = FWIME_SC_BALANCE && NH <= 21;
+    constexpr bool CAN_SPLIT = FWIME_SC_BALANCE;
     static bool attr = false;      // once per instantiation, before any launch (and any capture)
     static int resident = 0;       // CTAs per SM of the least resident variant
     if (!attr) {
