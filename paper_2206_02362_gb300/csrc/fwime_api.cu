@@ -240,12 +240,6 @@ static size_t al(size_t n) { return (n + 63) & ~(size_t)63; }   // 256-byte gran
 static int tlag_Hs(const fwime_grid &g, int lag) { return (g.nh - 1) * lag; }
 static int tlag_blocks(const fwime_grid &g, int K, int lag) { return (g.nt - 2 + tlag_Hs(g, lag)) / K + 1; }
 
-// scratch images of a split subsurface-offset imaging launch (its parts beyond the first)
-static size_t img_scratch_floats(const fwime_grid &g, long long P)
-{
-    return (size_t)(image_split_parts(g.nh, g.nx, g.nz) - 1) * al((size_t)g.nh * P);
-}
-
 static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int NZ, int NXP, int op, int K,
                       bool host_io, bool no_ckpt = false, int tlag = 0)
 {
@@ -278,16 +272,10 @@ static Sizes op_sizes(const fwime_grid &g, int nshot, int nrec, long long P, int
     case FWIME_OP_BORN: s.model += al(P); f = 5; break;
     case FWIME_OP_BORN_EXT: s.model += al(nh * P); f = 4 + 2 * K; break;
     case FWIME_OP_BORN_ADJ: s.model += al(P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
-    case FWIME_OP_BORN_EXT_ADJ:
-        s.model += al(nh * P) + img_scratch_floats(g, P);
-        f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg);
-        break;
+    case FWIME_OP_BORN_EXT_ADJ: s.model += al(nh * P); f = 2 + K + R + (no_ckpt ? 0 : 2 * nseg); break;
     case FWIME_OP_TOMO: s.model += 2 * al(nh * P) + al(P); f = 8 + 4 * K; break;
     case FWIME_OP_TOMO_ADJ:
-    case FWIME_OP_GRADIENT:
-        s.model += 2 * al(nh * P) + 2 * al(P) + img_scratch_floats(g, P);
-        f = 4 + 3 * K + 3 * R + (no_ckpt ? 0 : 4 * nseg);
-        break;
+    case FWIME_OP_GRADIENT: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 3 * K + 3 * R + (no_ckpt ? 0 : 4 * nseg); break;
     case FWIME_OP_OBJECTIVE: s.model += 2 * al(nh * P) + 2 * al(P); f = 4 + 2 * K; break;
     default: break;
     }
@@ -330,8 +318,6 @@ struct WS {
     float *f[8];
     float *ring[6];    // rings of K slots (ring[0..3]) and of R slots (ring[3..5] in adjoint ops)
     float *ckpt, *pred;
-    float *img_scratch;   // nimg_scratch images [nh][P] for split subsurface-offset imaging launches
-    int nimg_scratch;
     // host-io staging
     float *sv, *sw, *sd1, *sd2, *sm1, *sdv, *smo;
 };
@@ -418,16 +404,6 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
     case FWIME_OP_GRADIENT:
     case FWIME_OP_OBJECTIVE: w.W = take(nh * P); w.acc1 = take(P); w.acc2 = take(nh * P); break;
     default: break;
-    }
-    w.img_scratch = nullptr;
-    w.nimg_scratch = 0;
-    if (x->opt_tlag == 0 &&
-        (op == FWIME_OP_BORN_EXT_ADJ || op == FWIME_OP_TOMO_ADJ || op == FWIME_OP_GRADIENT)) {
-        const size_t n = img_scratch_floats(x->g, P);   // as counted in op_sizes
-        if (n > 0) {
-            w.nimg_scratch = image_split_parts(x->g.nh, x->g.nx, x->g.nz) - 1;
-            w.img_scratch = take(n);
-        }
     }
     const size_t SP = (size_t)w.S * P;
     for (auto &q : w.f) q = nullptr;
@@ -625,7 +601,6 @@ static int image(Run &r, int Sb, int n0, int kk, int mode, RingRef D, RingRef L,
     a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;   // the physical columns
     a.D = D; a.L = L; a.M2 = M2; a.Ds = Ds; a.alpha = alpha; a.pt = pt; a.img = img;
-    a.scratch = r.w.img_scratch; a.nscratch = r.w.nimg_scratch;
     const double pts = (double)x->g.nz * x->g.nx;
     const double per = 8.0 + (M2.base ? 4 : 0) + (Ds.base ? 4 : 0);
     const double once = mode == IMG_EXT ? 8.0 * x->g.nh : (mode == IMG_CONTRACT ? 8.0 + 4.0 * x->g.nh : 8.0);

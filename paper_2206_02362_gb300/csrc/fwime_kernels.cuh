@@ -163,8 +163,6 @@ struct ImgArgs {
     float alpha;                   // IMG_LOCAL: weight of D * L
     const float *pt;               // IMG_CONTRACT: p~ padded [nh][P]
     float *img;                    // IMG_EXT: [nh][P]; others: [P]
-    float *scratch;                // IMG_EXT, optional: nscratch images [nh][P] for the parts of a split launch
-    int nscratch;
 };
 
 // time-lag extension: one segment [n0, n1) of output steps, S shots
@@ -190,9 +188,6 @@ cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const
 cudaError_t launch_points(const PointsArgs &a, int nshot, cudaStream_t st);
 cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st);
 cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
-// parts the subsurface-offset imaging splits each (row, column block)'s pairs into on this device for
-// a physical width nx and nrows rows (1: no split; each extra part needs a scratch image [nh][P])
-int image_split_parts(int nh, int nx, int nrows);
 cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st);
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st);
 int tlag_jc(int K, int lag, int nh);          // chunk length (outputs of one residue class) for segments of K steps

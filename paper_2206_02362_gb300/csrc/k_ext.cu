@@ -19,7 +19,6 @@
 // pair samples of one parity (y and y - 2h; x - h and x + h), so a lane that
 // owns samples of one parity reuses every loaded sample for several offsets.
 #include <algorithm>
-#include <type_traits>
 #include <utility>
 
 #include "fwime_kernels.cuh"
@@ -147,9 +146,6 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #endif
 #ifndef FWIME_IMG_MINB
 #define FWIME_IMG_MINB 1
-#endif
-#ifndef FWIME_IMG_SPLIT_MAX
-#define FWIME_IMG_SPLIT_MAX 4   // parts of an imaging launch's pairs at most (a scratch image per extra part)
 #endif
 #ifndef FWIME_SC_A21
 #define FWIME_SC_A21 4
@@ -728,9 +724,9 @@ struct ImgTaskBody {
         }
         return acc2[i][j];
     }
-    // adds (add) or writes the accumulators into dst ([nh][P]) at x = x1 + i + o, h = o - i (o = lo + j),
-    // x1 = the lane's first u + its first ut offset; only physical columns [x_lo, x_hi)
-    __device__ __forceinline__ void store(const ImgArgs &a, long long rowoff, int x1, float *dst, bool add)
+    // adds the accumulators into img at x = x1 + i + o, h = o - i (o = lo + j), x1 = the lane's
+    // first u + its first ut offset; only physical columns [x_lo, x_hi)
+    __device__ __forceinline__ void store(const ImgArgs &a, long long rowoff, int x1)
     {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -738,16 +734,14 @@ struct ImgTaskBody {
             for (int j = 0; j < W1; ++j) {
                 if (in1(i, j)) {
                     const int x = x1 + i + T.lo1 + j;
-                    float *o = dst + (T.lo1 + j - i + HM) * a.P + rowoff + x;
-                    if (x >= a.x_lo && x < a.x_hi) *o = add ? *o + val1(i, j) : val1(i, j);
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo1 + j - i + HM) * a.P + rowoff + x] += val1(i, j);
                 }
             }
 #pragma unroll
             for (int j = 0; j < W2; ++j) {
                 if (in2(i, j)) {
                     const int x = x1 + i + T.lo2 + j;
-                    float *o = dst + (T.lo2 + j - i + HM) * a.P + rowoff + x;
-                    if (x >= a.x_lo && x < a.x_hi) *o = add ? *o + val2(i, j) : val2(i, j);
+                    if (x >= a.x_lo && x < a.x_hi) a.img[(T.lo2 + j - i + HM) * a.P + rowoff + x] += val2(i, j);
                 }
             }
         }
@@ -759,8 +753,7 @@ struct ImgTaskBody {
 __device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;\n" ::: "memory"); }
 
 template <int NH, int K>
-__device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *sm, int lane, int pb, int pe, float *dst,
-                                             bool add)
+__device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *sm, int lane)
 {
     using Sh = ImgShape<NH>;
     constexpr int NS = EXT_STAGES;
@@ -780,13 +773,13 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
     // all copied columns, [ub + 2 LO, ub + 2 LO + 2 LL) (which contains the D window), inside the row
     const bool interior = ub + 2 * Sh::LO >= 0 && ub + 2 * Sh::LO + 2 * Sh::LL <= a.NXP;
     PairRow pd, pl;
-    pd.init(a.D, a.n0, a.S, a.P, rowoff, pb);
-    pl.init(a.L, a.n0, a.S, a.P, rowoff, pb);
+    pd.init(a.D, a.n0, a.S, a.P, rowoff);
+    pl.init(a.L, a.n0, a.S, a.P, rowoff);
     int st_in = 0, st_c = 0;
     constexpr int FD = 2 * Sh::LD / Sh::TX, RD = 2 * Sh::LD - FD * Sh::TX;   // full copy rounds, remainder
     constexpr int FL = 2 * Sh::LL / Sh::TX, RL = 2 * Sh::LL - FL * Sh::TX;
     auto issue = [&](int p) {
-        if (p < pe) {
+        if (p < a.npair) {
             const unsigned so = 4u * st_in * Sh::STG;
             if (interior) {
                 const float *sd = pd.row + colD, *sl = pl.row + colL;
@@ -823,8 +816,8 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
     // two pairs per barrier: the prologue fills NS - 2 stages; iteration p waits for pairs p and p + 1,
     // then refills the stages of pairs p - 2 and p - 1, which every warp finished before the barrier
 #pragma unroll 1
-    for (int q = 0; q < NS - 2; ++q) issue(pb + q);
-    for (int p = pb; p < pe; p += 2) {
+    for (int q = 0; q < NS - 2; ++q) issue(q);
+    for (int p = 0; p < a.npair; p += 2) {
         cpa_wait<NS - 4>();
         cta_barrier();
         issue(p + NS - 2);
@@ -834,49 +827,25 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
         const float *s1 = sm + st_c * Sh::STG;
         st_c = st_c + 1 == NS ? 0 : st_c + 1;
         body.pair(s0 + par * Sh::OFFD, s0 + Sh::REGD + par * Sh::OFFL, b);
-        if (p + 1 < pe) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
+        if (p + 1 < a.npair) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
     }
     cpa_wait<0>();
     // u of the lane's first sample: ub + par + 16 b; x = (u + w) / 2 = ub + par + 16 b + i + o
-    body.store(a, rowoff, ub + par + 16 * b, dst, add);
+    body.store(a, rowoff, ub + par + 16 * b);
 }
 
-// SPLIT: part blockIdx.z of gridDim.z takes its share of the pairs; part 0 adds into the image, part
-// k > 0 writes its sums to scratch plane set k - 1, which k_img_combine adds afterwards in part order
-template <int NH, bool SPLIT>
+template <int NH>
 __global__ void __launch_bounds__(ImgShape<NH>::TX, FWIME_IMG_MINB) k_image_ps(const ImgArgs a, int u_lo)
 {
     extern __shared__ float4 sm4[];
     float *sm = reinterpret_cast<float *>(sm4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int pb = 0, pe = a.npair;
-    float *dst = a.img;
-    if constexpr (SPLIT) {
-        const int part = blockIdx.z, np = gridDim.z;
-        pb = (int)((long long)part * a.npair / np);
-        pe = (int)((long long)(part + 1) * a.npair / np);
-        if (part > 0) dst = a.scratch + (long long)(part - 1) * a.nh * a.P;
-    }
-    const bool add = !SPLIT || blockIdx.z == 0;
     // warp-uniform dispatch: every warp runs the same pipeline (barriers included) with its own task
-    constexpr int NT = ImgShape<NH>::NT;
-    if (warp == 0) img_task_run<NH, 0>(a, u_lo, sm, lane, pb, pe, dst, add);
-    if constexpr (NT > 1) if (warp == 1) img_task_run<NH, 1 % NT>(a, u_lo, sm, lane, pb, pe, dst, add);
-    if constexpr (NT > 2) if (warp == 2) img_task_run<NH, 2 % NT>(a, u_lo, sm, lane, pb, pe, dst, add);
-    if constexpr (NT > 3) if (warp == 3) img_task_run<NH, 3 % NT>(a, u_lo, sm, lane, pb, pe, dst, add);
-    if constexpr (NT > 4) if (warp == 4) img_task_run<NH, 4 % NT>(a, u_lo, sm, lane, pb, pe, dst, add);
-}
-
-// img += scratch part 1 + part 2 + ... over the physical rows and columns, every offset plane
-__global__ void k_img_combine(const ImgArgs a, int nparts)   // grid (columns / 128, rows, nh)
-{
-    const int x = a.x_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.x_hi) return;
-    const long long i = (long long)blockIdx.z * a.P + (long long)(a.z_lo + blockIdx.y) * a.NXP + x;
-    const long long plane = (long long)a.nh * a.P;
-    float v = a.img[i];
-    for (int k = 0; k < nparts - 1; ++k) v += a.scratch[k * plane + i];
-    a.img[i] = v;
+    if (warp == 0) img_task_run<NH, 0>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 1) if (warp == 1) img_task_run<NH, 1 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 2) if (warp == 2) img_task_run<NH, 2 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 3) if (warp == 3) img_task_run<NH, 3 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if constexpr (ImgShape<NH>::NT > 4) if (warp == 4) img_task_run<NH, 4 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
 }
 
 
@@ -986,91 +955,19 @@ static cudaError_t launch_image_gen(const ImgArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// CTAs resident per GPU (both variants; 0 when the device cannot be queried)
-template <int NH>
-static int img_wave()
-{
-    using Sh = ImgShape<NH>;
-    static int wave = -1;          // once per instantiation, before any launch (and any capture)
-    if (wave < 0) {
-        int r0 = 0, r1 = 0, dev = 0, nsm = 0;
-        cudaFuncSetAttribute(k_image_ps<NH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        cudaFuncSetAttribute(k_image_ps<NH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r0, k_image_ps<NH, false>, Sh::TX, Sh::SMEM) ==
-                            cudaSuccess &&
-                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r1, k_image_ps<NH, true>, Sh::TX, Sh::SMEM) ==
-                            cudaSuccess &&
-                        cudaGetDevice(&dev) == cudaSuccess &&
-                        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
-        if (!ok) {
-            cudaGetLastError();
-            return 0;
-        }
-        wave = std::min(r0, r1) * nsm;
-    }
-    return wave;
-}
-
-// Parts of the pair range (1 .. kmax) whose CTAs fill their last wave best (the fewest within 1 %);
-// nblk CTAs per part.  The segment-long CTAs otherwise leave the SMs of a partial last wave idle.
-static int fill_parts(long long nblk, int wave, int kmax)
-{
-    if (wave <= 0) return 1;
-    auto fill = [&](int k) {
-        const double w = (double)nblk * k / wave;
-        return w / std::ceil(w);
-    };
-    int best_k = 1;
-    double best = fill(1);
-    for (int k = 2; k <= kmax; ++k)
-        if (fill(k) > best + 0.01) { best = fill(k); best_k = k; }
-    return best_k;
-}
-
-template <int NH>
-static int img_ncb(int x_lo, int x_hi, int &u_lo)
-{
-    u_lo = x_lo - ImgShape<NH>::HM;    // first u = x - h of the physical columns, made even
-    u_lo -= ((u_lo % 2) + 2) % 2;
-    return (x_hi + ImgShape<NH>::HM - u_lo + 255) / 256;
-}
-
 template <int NH>
 static void launch_image_ps(const ImgArgs &a, cudaStream_t st)
 {
     using Sh = ImgShape<NH>;
-    int u_lo = 0;
-    const int ncb = img_ncb<NH>(a.x_lo, a.x_hi, u_lo), nrow = a.z_hi - a.z_lo;
-    // parts: the scratch planes the caller provides, and at least four ring depths of pairs each
-    const int kmax = std::min(std::min(FWIME_IMG_SPLIT_MAX, a.scratch ? a.nscratch + 1 : 1),
-                              std::max(1, a.npair / (4 * EXT_STAGES)));
-    const int np = fill_parts((long long)ncb * nrow, img_wave<NH>(), kmax);
-    if (np == 1) {
-        k_image_ps<NH, false><<<dim3(ncb, nrow), Sh::TX, Sh::SMEM, st>>>(a, u_lo);
-        return;
+    int u_lo = a.x_lo - Sh::HM;    // first u = x - h of the physical columns, made even
+    u_lo -= ((u_lo % 2) + 2) % 2;
+    dim3 grid((a.x_hi + Sh::HM - u_lo + 255) / 256, a.z_hi - a.z_lo);
+    static bool attr = false;      // once per instantiation, before any launch (and any capture)
+    if (!attr) {
+        cudaFuncSetAttribute(k_image_ps<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        attr = true;
     }
-    k_image_ps<NH, true><<<dim3(ncb, nrow, np), Sh::TX, Sh::SMEM, st>>>(a, u_lo);
-    k_img_combine<<<dim3((a.x_hi - a.x_lo + 127) / 128, nrow, a.nh), 128, 0, st>>>(a, np);
-}
-
-int image_split_parts(int nh, int nx, int nrows)
-{
-    auto parts = [&](auto tag) {
-        constexpr int NH = decltype(tag)::value;
-        int u_lo = 0;
-        const int ncb = img_ncb<NH>(ImgShape<NH>::HM, ImgShape<NH>::HM + nx, u_lo);
-        return fill_parts((long long)ncb * nrows, img_wave<NH>(), FWIME_IMG_SPLIT_MAX);
-    };
-    switch (nh) {
-    case 1: return parts(std::integral_constant<int, 1>{});
-    case 3: return parts(std::integral_constant<int, 3>{});
-    case 5: return parts(std::integral_constant<int, 5>{});
-    case 11: return parts(std::integral_constant<int, 11>{});
-    case 21: return parts(std::integral_constant<int, 21>{});
-    case 31: return parts(std::integral_constant<int, 31>{});
-    case 41: return parts(std::integral_constant<int, 41>{});
-    default: return 1;   // the generic kernel
-    }
+    k_image_ps<NH><<<grid, Sh::TX, Sh::SMEM, st>>>(a, u_lo);
 }
 
 template <int MODE>
