@@ -150,6 +150,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_SC_A21
 #define FWIME_SC_A21 4
 #endif
+#ifndef FWIME_SC_A31
+#define FWIME_SC_A31 4
+#endif
 // packed two-lane FP32 (f32x2) forms of the multiply-adds, per kernel where they measured faster
 // (B~ + B~* on the Marmousi2-shaped grid: scatter -1 % at nh 21; imaging -5.5 % at nh 21, +2.7 %
 // at nh 31, so the imaging kernel packs only up to nh 21)
@@ -510,7 +513,7 @@ cudaError_t launch_scatter(const ExtArgs &a, cudaStream_t st)
     case 5: launch_scatter_ps<5, 4>(a, st); break;
     case 11: launch_scatter_ps<11, 4>(a, st); break;
     case 21: launch_scatter_ps<21, FWIME_SC_A21>(a, st); break;
-    case 31: launch_scatter_ps<31, 4>(a, st); break;
+    case 31: launch_scatter_ps<31, FWIME_SC_A31>(a, st); break;
     case 41: launch_scatter_ps<41, 2>(a, st); break;
     default: {
         dim3 grid((a.x_hi - a.x_lo + EXT_TX - 1) / EXT_TX, a.z_hi - a.z_lo);
