@@ -325,9 +325,9 @@ struct WS {
 static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
 {
     w.K = x->opt_K > 0 ? x->opt_K : auto_K(x->g.nt);
-    // time lags: segments of at least 2 Hs steps keep the lag halo (2 Hs samples per segment) below the
-    // segment's own K samples
-    if (x->opt_tlag > 0 && x->opt_K == 0) w.K = std::max(w.K, 2 * tlag_Hs(x->g, x->opt_tlag));
+    // time lags: segments of at least 4 Hs steps keep the lag halo (2 Hs samples per segment, read once per
+    // residue class) at half the segment's own K samples or less
+    if (x->opt_tlag > 0 && x->opt_K == 0) w.K = std::max(w.K, 4 * tlag_Hs(x->g, x->opt_tlag));
     w.K = std::min(w.K, x->g.nt - 1);
     w.K = std::max(w.K, 1);
     w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;
@@ -879,7 +879,7 @@ static int tlag_launch(Run &r, int Sb, int n0, int n1, bool image, RingRef D, Ri
     fwime_ctx *x = r.x;
     TlagArgs a{};
     a.NXP = x->NXP; a.nh = x->g.nh; a.S = Sb; a.lag = x->opt_tlag; a.nt = x->g.nt; a.n0 = n0; a.n1 = n1;
-    a.jc = tlag_jc(r.w.K, x->opt_tlag, x->g.nh); a.nchunk = tlag_chunks(r.w.K, x->opt_tlag, a.jc);
+    a.jc = tlag_jc(r.w.K, x->opt_tlag, x->g.nh);
     a.P = x->P; a.sigma = sigma;
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;
     a.W = W ? W : r.w.W; a.D = D; a.E = E; a.L = L; a.img = img; a.accumulate = accumulate;

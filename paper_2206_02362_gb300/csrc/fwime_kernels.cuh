@@ -167,7 +167,7 @@ struct ImgArgs {
 
 // time-lag extension: one segment [n0, n1) of output steps, S shots
 struct TlagArgs {
-    int NXP, nh, S, lag, nt, n0, n1, nchunk;
+    int NXP, nh, S, lag, nt, n0, n1;
     int jc;                        // outputs of one residue class per thread and chunk (16, 24, 32: tlag_jc)
     int sigma;                     // scatter: +1 reads D at n - 2 s_i, -1 (transpose) at n + 2 s_i
     long long P;
@@ -191,7 +191,6 @@ cudaError_t launch_image(const ImgArgs &a, int mode, cudaStream_t st);
 cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st);
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st);
 int tlag_jc(int K, int lag, int nh);          // chunk length (outputs of one residue class) for segments of K steps
-int tlag_chunks(int K, int lag, int jc);      // output chunks per residue class for a segment of K steps
 
 // model preparation
 struct PrepArgs {

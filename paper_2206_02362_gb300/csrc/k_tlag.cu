@@ -16,19 +16,13 @@
 
 namespace fwk {
 
-// packed two-lane FP32 forms (f32x2): measured faster for the imaging kernel (-3.7 % at nh 21) and
-// slower for the scatter (+8.7 %), whose scalar form keeps JC independent chains per thread
-#ifndef FWIME_TL_SC_F32X2
-#define FWIME_TL_SC_F32X2 0
-#endif
+// packed two-lane FP32 form (f32x2) of the imaging kernel: measured faster (-3.7 % at nh 21); the scatter's
+// packed form measured 8.7 % slower (its scalar form keeps JC independent chains per thread) and is not built
 #ifndef FWIME_TL_IMG_F32X2
 #define FWIME_TL_IMG_F32X2 1
 #endif
 #ifndef FWIME_TL_IMG_MINB
 #define FWIME_TL_IMG_MINB 4   // resident CTAs the imaging kernel is compiled for (up to 21 lags, JC <= 24; spills beyond)
-#endif
-#ifndef FWIME_TL_SC_IOUTER
-#define FWIME_TL_SC_IOUTER 0
 #endif
 constexpr int TL_TX = 128;      // threads per CTA (consecutive columns)
 // JC, the outputs of one residue class a thread handles (one chunk), is 16, 24 or 32, chosen per
@@ -41,116 +35,75 @@ __device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
 }
 
 
-// blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue, chunk)
+// blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue).  A thread walks the chunks of its
+// residue class in time order: chunk c's window starts JC samples after chunk c - 1's, so the last 2 hm
+// samples of one window are the first of the next and stay in registers.  Every sample of the class is
+// loaded once per segment (c + 2 hm loads for c outputs, instead of JC + 2 hm per chunk of JC).
 template <int NH, int SIGMA, int JC>
 __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
 {
     constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
-    // ring offsets of the window samples and of the outputs (-1: outside the record / the segment): the
-    // same for every thread of the CTA, computed once into shared memory
+    // ring offsets of the chunk's window samples and outputs (-1: outside the record / the segment): the
+    // same for every thread of the CTA, computed once per chunk into shared memory
     __shared__ long long s_doff[NW], s_eoff[JC];
     const int Z = a.z_lo + blockIdx.y;
-    int q = blockIdx.z;
-    const int chunk = q % a.nchunk; q /= a.nchunk;
-    const int r = q % (2 * a.lag), s = q / (2 * a.lag);
-    const int base = a.n0 + r + 2 * a.lag * JC * chunk;   // output j of this thread: base + 2 L j
-    if (base >= a.n1) return;                             // the whole CTA
     const int step = 2 * a.lag;
-    const int m0 = base - step * HM;                      // window sample k is step m0 + k (2 L)
-    for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
-        if (k < NW) {
-            const int m = m0 + step * k;
-            s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
-        } else {
-            const int n = base + step * (k - NW);
-            s_eoff[k - NW] = n < a.n1 ? tl_slot(a.E, n - a.n0) : -1;
-        }
-    }
-    __syncthreads();
+    const int r = blockIdx.z % step, s = blockIdx.z / step;
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
-    if (X >= a.x_hi) return;
-    const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
+    const bool act = X < a.x_hi;                          // no early exit: the CTA shares barriers
+    const long long pp = (long long)Z * a.NXP + (act ? X : a.x_lo), off = (long long)s * a.P + pp;
     float Wr[NH];   // sigma = -1 reads lag i at m + 2 s_i = m - 2 s_(nh-1-i): the weights reversed
 #pragma unroll
     for (int i = 0; i < NH; ++i) Wr[i] = __ldg(a.W + (SIGMA > 0 ? i : NH - 1 - i) * a.P + pp);
-    float win[NW];
     const float *db = a.D.base + off;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const long long o = s_doff[k];
-        win[k] = o >= 0 ? __ldg(db + o) : 0.f;
-    }
     float *ob = const_cast<float *>(a.E.base) + off;
-#if FWIME_TL_SC_F32X2
-    // Packed form: output j reads win[j - i + 2 HM] at lag i.  For even i the output pairs (2p, 2p + 1)
-    // read the aligned sample pairs (k, k + 1), k even; for odd i the pairs (2p + 1, 2p + 2) do, and
-    // outputs 0 and JC - 1 stay scalar.  Each output sums its even-i and odd-i products separately.
-    static_assert(JC % 2 == 0, "pairs of outputs");
-    f32x2 pe[JC / 2], po[JC / 2 - 1];
-    float o0 = 0.f, o1 = 0.f;
+    float win[NW];
+#pragma unroll 1
+    for (int base = a.n0 + r, k0 = 0; base < a.n1; base += step * JC, k0 = 2 * HM) {
+        const int m0 = base - step * HM;                  // window sample k is step m0 + k (2 L)
+        __syncthreads();                                  // every thread is done with the previous tables
+        for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
+            if (k < NW) {
+                const int m = m0 + step * k;
+                s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
+            } else {
+                const int n = base + step * (k - NW);
+                s_eoff[k - NW] = n < a.n1 ? tl_slot(a.E, n - a.n0) : -1;
+            }
+        }
+        __syncthreads();
+        if (!act) continue;
+        if (k0 > 0) {                                     // carried over from the previous chunk
 #pragma unroll
-    for (int p = 0; p < JC / 2; ++p) pe[p] = pk(0.f, 0.f);
+            for (int k = 0; k < 2 * HM; ++k) win[k] = win[k + JC];
 #pragma unroll
-    for (int p = 0; p < JC / 2 - 1; ++p) po[p] = pk(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-        const f32x2 wb = pk(Wr[i], Wr[i]);
-        if (i % 2 == 0) {
-#pragma unroll
-            for (int p = 0; p < JC / 2; ++p) {
-                const int k = 2 * p - i + 2 * HM;
-                pe[p] = fma2(wb, pk(win[k], win[k + 1]), pe[p]);
+            for (int k = 2 * HM; k < NW; ++k) {
+                const long long o = s_doff[k];
+                win[k] = o >= 0 ? __ldg(db + o) : 0.f;
             }
         } else {
 #pragma unroll
-            for (int p = 0; p < JC / 2 - 1; ++p) {
-                const int k = 2 * p + 1 - i + 2 * HM;
-                po[p] = fma2(wb, pk(win[k], win[k + 1]), po[p]);
+            for (int k = 0; k < NW; ++k) {
+                const long long o = s_doff[k];
+                win[k] = o >= 0 ? __ldg(db + o) : 0.f;
             }
-            o0 = fmaf(Wr[i], win[-i + 2 * HM], o0);
-            o1 = fmaf(Wr[i], win[JC - 1 - i + 2 * HM], o1);
+        }
+        float acc[JC];
+#pragma unroll
+        for (int j = 0; j < JC; ++j) acc[j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < JC; ++j)
+#pragma unroll
+            for (int i = 0; i < NH; ++i) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
+#pragma unroll
+        for (int j = 0; j < JC; ++j) {
+            const long long eo = s_eoff[j];
+            if (eo >= 0) {
+                float *o = ob + eo;
+                *o = a.accumulate ? *o + acc[j] : acc[j];
+            }
         }
     }
-    float ev[JC], od[JC];
-#pragma unroll
-    for (int p = 0; p < JC / 2; ++p) upk(pe[p], ev[2 * p], ev[2 * p + 1]);
-#pragma unroll
-    for (int p = 0; p < JC / 2 - 1; ++p) upk(po[p], od[2 * p + 1], od[2 * p + 2]);
-    od[0] = o0;
-    od[JC - 1] = o1;
-#pragma unroll
-    for (int j = 0; j < JC; ++j) {
-        const long long eo = s_eoff[j];
-        if (eo >= 0) {
-            const float acc = ev[j] + od[j];
-            float *o = ob + eo;
-            *o = a.accumulate ? *o + acc : acc;
-        }
-    }
-#else
-    float acc[JC];
-#pragma unroll
-    for (int j = 0; j < JC; ++j) acc[j] = 0.f;
-#if FWIME_TL_SC_IOUTER
-#pragma unroll
-    for (int i = 0; i < NH; ++i)                  // every output sums over i in the same order
-#pragma unroll
-        for (int j = 0; j < JC; ++j) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
-#else
-#pragma unroll
-    for (int j = 0; j < JC; ++j)
-#pragma unroll
-        for (int i = 0; i < NH; ++i) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
-#endif
-#pragma unroll
-    for (int j = 0; j < JC; ++j) {
-        const long long eo = s_eoff[j];
-        if (eo >= 0) {
-            float *o = ob + eo;
-            *o = a.accumulate ? *o + acc[j] : acc[j];
-        }
-    }
-#endif
 }
 
 // generic nh: weights and samples re-read per output (any odd nh)
@@ -159,15 +112,10 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const int Z = a.z_lo + blockIdx.y;
-    int q = blockIdx.z;
-    const int chunk = q % a.nchunk; q /= a.nchunk;
-    const int r = q % (2 * a.lag), s = q / (2 * a.lag);
+    const int r = blockIdx.z % (2 * a.lag), s = blockIdx.z / (2 * a.lag);   // (shot, residue), as above
     const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
-    const int base = a.n0 + r + 2 * a.lag * a.jc * chunk;
     const int hm = (a.nh - 1) / 2;
-    for (int j = 0; j < a.jc; ++j) {
-        const int n = base + 2 * a.lag * j;
-        if (n >= a.n1) break;
+    for (int n = a.n0 + r; n < a.n1; n += 2 * a.lag) {   // the residue class's outputs
         float acc = 0.f;
         for (int i = 0; i < a.nh; ++i) {
             const int m = n - a.sigma * 2 * a.lag * (i - hm);
@@ -181,7 +129,8 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
 
 // blockIdx.x: column block, blockIdx.y: row; the thread walks shots, residues and chunks.  The ring
 // offsets of a (residue, chunk)'s window and receiver-side samples are the same for every thread of the
-// CTA: computed once per iteration into shared memory.
+// CTA: computed once per iteration into shared memory.  Within a residue class the chunks' windows
+// overlap by 2 hm samples, carried over in registers (each D sample loaded once per class and segment).
 template <int NH, int JC>
 __global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_MINB : 1) k_tlag_image(const TlagArgs a)
 {
@@ -205,13 +154,14 @@ __global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_M
 #pragma unroll
     for (int q = 0; q < HM; ++q) pe[q] = po[q] = pk(0.f, 0.f);
 #endif
+    float win[NW];                                        // the chunk's window of one residue class
 #pragma unroll 1
     for (int s = 0; s < a.S; ++s) {
         const long long off = (long long)s * a.P + pp;
 #pragma unroll 1
         for (int r = 0; r < step; ++r) {
 #pragma unroll 1
-            for (int base = a.n0 + r; base < a.n1; base += step * JC) {
+            for (int base = a.n0 + r, k0 = 0; base < a.n1; base += step * JC, k0 = 2 * HM) {
                 const int m0 = base - step * HM;
                 __syncthreads();                          // every thread is done with the previous tables
                 for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
@@ -225,12 +175,22 @@ __global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_M
                 }
                 __syncthreads();
                 if (!act) continue;
-                float win[NW], lv[JC];
+                float lv[JC];
                 const float *db = a.D.base + off, *lb0 = a.L.base + off;
+                if (k0 > 0) {                             // carried over from the previous chunk
 #pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    const long long o = s_doff[k];
-                    win[k] = o >= 0 ? __ldg(db + o) : 0.f;
+                    for (int k = 0; k < 2 * HM; ++k) win[k] = win[k + JC];
+#pragma unroll
+                    for (int k = 2 * HM; k < NW; ++k) {
+                        const long long o = s_doff[k];
+                        win[k] = o >= 0 ? __ldg(db + o) : 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        const long long o = s_doff[k];
+                        win[k] = o >= 0 ? __ldg(db + o) : 0.f;
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < JC; ++j) {
@@ -324,7 +284,7 @@ cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     if (a.jc != 16 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
-    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag * a.nchunk);
+    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag);
     switch (a.nh) {
     case 1: launch_tlag_scatter_nh<1>(a, grid, st); break;
     case 3: launch_tlag_scatter_nh<3>(a, grid, st); break;
@@ -364,20 +324,21 @@ cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// A segment of K steps holds at most c = ceil(K / 2L) outputs of one residue class.  With chunks of JC
-// outputs a class costs about ceil(c / JC) (2 JC + 2 hm) loads and stores (window JC + 2 hm, outputs JC):
-// the JC of least cost, ties to the smaller.
+// A segment of K steps holds at most c = ceil(K / 2L) outputs of one residue class.  The kernels load
+// each window sample of a class once (c + 2 hm loads, whatever JC), so JC only sets the outputs computed
+// past c in the last chunk: the JC with the fewest, ties to the shorter chunk (fewer registers: the
+// imaging kernel at nh 21 spills with JC = 24 under its 128-register bound).
 int tlag_jc(int K, int lag, int nh)
 {
-    const int c = (K + 2 * lag - 1) / (2 * lag), hm = (nh - 1) / 2;
+    (void)nh;
+    const int c = (K + 2 * lag - 1) / (2 * lag);
     int best = 16;
     long long bc = -1;
     for (const int jc : {16, 24, 32}) {
-        const long long cost = (long long)((c + jc - 1) / jc) * (2 * jc + 2 * hm);
-        if (bc < 0 || cost < bc) { bc = cost; best = jc; }
+        const long long padded = (long long)((c + jc - 1) / jc) * jc;
+        if (bc < 0 || padded < bc) { bc = padded; best = jc; }
     }
     return best;
 }
-int tlag_chunks(int K, int lag, int jc) { return (K + 2 * lag * jc - 1) / (2 * lag * jc); }
 
 }  // namespace fwk

@@ -55,6 +55,8 @@ def rel(a, b):
     (5, 1, dict(segment=60)),
     (3, 1, dict(segment=90)),
     (7, 1, dict(segment=56)),
+    # 75 outputs per class in chunks of 16: the window carried over four times
+    (5, 1, dict(segment=150)),
 ])
 def test_time_lag_born_and_adjoint_match_oracle(nh, lag, opts):
     assert torch.cuda.is_available()
@@ -100,7 +102,8 @@ def test_time_lag_vp_solve_matches_oracle():
     assert max(abs(a - b) for a, b in zip(hist, h_ref)) <= 1e-5 * h_ref[0]
 
 
-@pytest.mark.parametrize("nh,lag,opts", [(5, 3, {}), (5, 3, dict(shots_per_batch=2, segment=7)), (11, 2, dict(segment=20))])
+@pytest.mark.parametrize("nh,lag,opts", [(5, 3, {}), (5, 3, dict(shots_per_batch=2, segment=7)), (11, 2, dict(segment=20)),
+                                         (5, 1, dict(segment=100))])
 def test_time_lag_tomo_and_gradient_match_oracle(nh, lag, opts):
     c = TL(nh, lag, nt=220)
     rng = np.random.default_rng(21)
