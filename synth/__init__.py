@@ -251,7 +251,7 @@ def marmousi2(nshot: int = 100, nt: int = 4000) -> Workload:
     v = marmousi_like(nz, nx, dx)
     w = lowcut(ricker(nt, dt, 8.0), dt, 2.0, 4.0)
     src_ix = (8 + 17 * np.arange(100))[:nshot]
-    return Workload("marmousi2-like-350x1700-nt4000-nh21", nz, nx, dx, dt, nt, 50, 21, 8.0,
+    return Workload(f"marmousi2-like-350x1700-nt{nt}-nh21", nz, nx, dx, dt, nt, 50, 21, 8.0,
                     np.full(len(src_ix), 2), src_ix, np.full(850, 2), 2 * np.arange(850), v, w,
                     SEED0 + 1)
 
@@ -262,7 +262,7 @@ def north_sea(nshot: int = 120, nt: int = 5000):
     nz, nx, dx, dt = 400, 1600, 12.5, 1e-3
     v, v0 = north_sea_like(nz, nx, dx)
     src_ix = np.round(np.linspace(6, nx - 7, 120)).astype(int)[:nshot]
-    wl = Workload("north-sea-like-400x1600-nt5000-nh31", nz, nx, dx, dt, nt, 50, 31, 8.0,
+    wl = Workload(f"north-sea-like-400x1600-nt{nt}-nh31", nz, nx, dx, dt, nt, 50, 31, 8.0,
                   np.full(len(src_ix), 2), src_ix, np.full(800, 2), 2 * np.arange(800), v,
                   ricker(nt, dt, 8.0), SEED0 + 2)
     return wl, v0
@@ -273,7 +273,7 @@ def salt(nshot: int = 400, nt: int = 8000) -> Workload:
     nz, nx, dx, dt = 1200, 5000, 6.25, 5e-4
     v = salt_like(nz, nx, dx)
     src_ix = np.round(np.linspace(6, nx - 7, 400)).astype(int)[:nshot]
-    return Workload("salt-like-1200x5000-nt8000-nh41", nz, nx, dx, dt, nt, 50, 41, 10.0,
+    return Workload(f"salt-like-1200x5000-nt{nt}-nh41", nz, nx, dx, dt, nt, 50, 41, 10.0,
                     np.full(len(src_ix), 4), src_ix, np.full(2500, 4), 2 * np.arange(2500), v,
                     ricker(nt, dt, 10.0), SEED0 + 4)
 

@@ -50,8 +50,8 @@ def rel(a, b):
     (11, 4, dict(segment=13)),
     (7, 2, {}),                                     # generic lag count
     (1, 1, {}),
-    # chunk lengths (outputs of one residue class per thread): 32 (30 per class), 24 in two chunks
-    # (45 per class), and the generic kernel with 32 (28 per class)
+    # chunks of 16 outputs of one residue class, the window carried from chunk to chunk: two chunks (30
+    # per class), three (45 per class), and the generic kernel (28 per class)
     (5, 1, dict(segment=60)),
     (3, 1, dict(segment=90)),
     (7, 1, dict(segment=56)),
