@@ -168,7 +168,7 @@ struct ImgArgs {
 // time-lag extension: one segment [n0, n1) of output steps, S shots
 struct TlagArgs {
     int NXP, nh, S, lag, nt, n0, n1;
-    int jc;                        // outputs of one residue class per thread and chunk (16, 24, 32: tlag_jc)
+    int jc;                        // outputs of one residue class per thread and chunk (16, 20, 24, 32: tlag_jc)
     int sigma;                     // scatter: +1 reads D at n - 2 s_i, -1 (transpose) at n + 2 s_i
     long long P;
     int z_lo, z_hi, x_lo, x_hi;    // physical rows / columns

@@ -275,7 +275,8 @@ static void launch_tlag_scatter_jc(const TlagArgs &a, dim3 grid, cudaStream_t st
 template <int NH>
 static void launch_tlag_scatter_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
 {
-    if (a.jc == 24) launch_tlag_scatter_jc<NH, 24>(a, grid, st);
+    if (a.jc == 20) launch_tlag_scatter_jc<NH, 20>(a, grid, st);
+    else if (a.jc == 24) launch_tlag_scatter_jc<NH, 24>(a, grid, st);
     else if (a.jc == 32) launch_tlag_scatter_jc<NH, 32>(a, grid, st);
     else launch_tlag_scatter_jc<NH, 16>(a, grid, st);
 }
@@ -283,7 +284,7 @@ static void launch_tlag_scatter_nh(const TlagArgs &a, dim3 grid, cudaStream_t st
 cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
-    if (a.jc != 16 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
+    if (a.jc != 16 && a.jc != 20 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
     dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag);
     switch (a.nh) {
     case 1: launch_tlag_scatter_nh<1>(a, grid, st); break;
@@ -301,7 +302,8 @@ cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 template <int NH>
 static void launch_tlag_image_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
 {
-    if (a.jc == 24) k_tlag_image<NH, 24><<<grid, TL_TX, 0, st>>>(a);
+    if (a.jc == 20) k_tlag_image<NH, 20><<<grid, TL_TX, 0, st>>>(a);
+    else if (a.jc == 24) k_tlag_image<NH, 24><<<grid, TL_TX, 0, st>>>(a);
     else if (a.jc == 32) k_tlag_image<NH, 32><<<grid, TL_TX, 0, st>>>(a);
     else k_tlag_image<NH, 16><<<grid, TL_TX, 0, st>>>(a);
 }
@@ -309,7 +311,7 @@ static void launch_tlag_image_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
-    if (a.jc != 16 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
+    if (a.jc != 16 && a.jc != 20 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
     dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo);
     switch (a.nh) {
     case 1: launch_tlag_image_nh<1>(a, grid, st); break;
@@ -334,7 +336,7 @@ int tlag_jc(int K, int lag, int nh)
     const int c = (K + 2 * lag - 1) / (2 * lag);
     int best = 16;
     long long bc = -1;
-    for (const int jc : {16, 24, 32}) {
+    for (const int jc : {16, 20, 24, 32}) {
         const long long padded = (long long)((c + jc - 1) / jc) * jc;
         if (bc < 0 || padded < bc) { bc = padded; best = jc; }
     }
