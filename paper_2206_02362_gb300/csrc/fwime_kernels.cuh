@@ -24,7 +24,7 @@ constexpr int MAX_NH = 201;     // largest supported number of subsurface offset
 #ifndef FWIME_EXT_STAGES
 #define FWIME_EXT_STAGES 6
 #endif
-constexpr int EXT_STAGES = FWIME_EXT_STAGES;   // cp.async pipeline depth of the imaging kernels (>= 2 x pairs per barrier)
+constexpr int EXT_STAGES = FWIME_EXT_STAGES;   // cp.async pipeline depth of the imaging kernels (even, >= 4)
 
 // status bits latched by kernels
 constexpr int ST_CFL = 1;

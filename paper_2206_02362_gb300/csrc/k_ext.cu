@@ -147,9 +147,6 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_IMG_MINB
 #define FWIME_IMG_MINB 1
 #endif
-#ifndef FWIME_IMG_PB
-#define FWIME_IMG_PB 2        // (step, shot) pairs per block-wide barrier of the imaging ring
-#endif
 #ifndef FWIME_SC_A21
 #define FWIME_SC_A21 4
 #endif
@@ -819,38 +816,21 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
     };
     ImgTaskBody<NH, K> body;
     body.zero();
-    // PB pairs per barrier: the prologue fills NS - PB stages; iteration p waits for pairs p .. p + PB - 1,
-    // then refills the stages of pairs p - PB .. p - 1, which every warp finished before the barrier
-    constexpr int PB = FWIME_IMG_PB;
-    static_assert(NS >= 2 * PB, "ring too short for the pairs per barrier");
+    // two pairs per barrier: the prologue fills NS - 2 stages; iteration p waits for pairs p and p + 1,
+    // then refills the stages of pairs p - 2 and p - 1, which every warp finished before the barrier
 #pragma unroll 1
-    for (int q = 0; q < NS - PB; ++q) issue(q);
-    for (int p = 0; p < a.npair; p += PB) {
-        cpa_wait<NS - 2 * PB>();
+    for (int q = 0; q < NS - 2; ++q) issue(q);
+    for (int p = 0; p < a.npair; p += 2) {
+        cpa_wait<NS - 4>();
         cta_barrier();
-        if constexpr (PB == 2) {
-            issue(p + NS - 2);
-            issue(p + NS - 1);
-            const float *s0 = sm + st_c * Sh::STG;
-            st_c = st_c + 1 == NS ? 0 : st_c + 1;
-            const float *s1 = sm + st_c * Sh::STG;
-            st_c = st_c + 1 == NS ? 0 : st_c + 1;
-            body.pair(s0 + par * Sh::OFFD, s0 + Sh::REGD + par * Sh::OFFL, b);
-            if (p + 1 < a.npair) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
-        } else {
-#pragma unroll
-            for (int u = 0; u < PB; ++u) issue(p + NS - PB + u);
-            const float *sp[PB];
-#pragma unroll
-            for (int u = 0; u < PB; ++u) {
-                sp[u] = sm + st_c * Sh::STG;
-                st_c = st_c + 1 == NS ? 0 : st_c + 1;
-            }
-            body.pair(sp[0] + par * Sh::OFFD, sp[0] + Sh::REGD + par * Sh::OFFL, b);
-#pragma unroll
-            for (int u = 1; u < PB; ++u)
-                if (p + u < a.npair) body.pair(sp[u] + par * Sh::OFFD, sp[u] + Sh::REGD + par * Sh::OFFL, b);
-        }
+        issue(p + NS - 2);
+        issue(p + NS - 1);
+        const float *s0 = sm + st_c * Sh::STG;
+        st_c = st_c + 1 == NS ? 0 : st_c + 1;
+        const float *s1 = sm + st_c * Sh::STG;
+        st_c = st_c + 1 == NS ? 0 : st_c + 1;
+        body.pair(s0 + par * Sh::OFFD, s0 + Sh::REGD + par * Sh::OFFL, b);
+        if (p + 1 < a.npair) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
     }
     cpa_wait<0>();
     // u of the lane's first sample: ub + par + 16 b; x = (u + w) / 2 = ub + par + 16 b + i + o
