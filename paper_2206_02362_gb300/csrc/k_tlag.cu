@@ -35,10 +35,11 @@ __device__ __forceinline__ long long tl_slot(const RingRef &r, int m)
 }
 
 
-// blockIdx.x: column block, blockIdx.y: row, blockIdx.z: (shot, residue).  A thread walks the chunks of its
-// residue class in time order: chunk c's window starts JC samples after chunk c - 1's, so the last 2 hm
-// samples of one window are the first of the next and stay in registers.  Every sample of the class is
-// loaded once per segment (c + 2 hm loads for c outputs, instead of JC + 2 hm per chunk of JC).
+// blockIdx.x: column block, blockIdx.y: row, blockIdx.z: shot.  A thread walks the residue classes of its
+// point, and the chunks of each class in time order: chunk c's window starts JC samples after chunk
+// c - 1's, so the last 2 hm samples of one window are the first of the next and stay in registers.  Every
+// sample of a class is loaded once per segment (c + 2 hm loads for c outputs, instead of JC + 2 hm per
+// chunk of JC), and the nh weights once per point and shot.
 template <int NH, int SIGMA, int JC>
 __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
 {
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
     __shared__ long long s_doff[NW], s_eoff[JC];
     const int Z = a.z_lo + blockIdx.y;
     const int step = 2 * a.lag;
-    const int r = blockIdx.z % step, s = blockIdx.z / step;
+    const int s = blockIdx.z;
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
     const bool act = X < a.x_hi;                          // no early exit: the CTA shares barriers
     const long long pp = (long long)Z * a.NXP + (act ? X : a.x_lo), off = (long long)s * a.P + pp;
@@ -59,48 +60,51 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter(const TlagArgs a)
     float *ob = const_cast<float *>(a.E.base) + off;
     float win[NW];
 #pragma unroll 1
-    for (int base = a.n0 + r, k0 = 0; base < a.n1; base += step * JC, k0 = 2 * HM) {
-        const int m0 = base - step * HM;                  // window sample k is step m0 + k (2 L)
-        __syncthreads();                                  // every thread is done with the previous tables
-        for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
-            if (k < NW) {
-                const int m = m0 + step * k;
-                s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
+    for (int r = 0; r < step; ++r) {
+#pragma unroll 1
+        for (int base = a.n0 + r, k0 = 0; base < a.n1; base += step * JC, k0 = 2 * HM) {
+            const int m0 = base - step * HM;                  // window sample k is step m0 + k (2 L)
+            __syncthreads();                                  // every thread is done with the previous tables
+            for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
+                if (k < NW) {
+                    const int m = m0 + step * k;
+                    s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
+                } else {
+                    const int n = base + step * (k - NW);
+                    s_eoff[k - NW] = n < a.n1 ? tl_slot(a.E, n - a.n0) : -1;
+                }
+            }
+            __syncthreads();
+            if (!act) continue;
+            if (k0 > 0) {                                     // carried over from the previous chunk
+#pragma unroll
+                for (int k = 0; k < 2 * HM; ++k) win[k] = win[k + JC];
+#pragma unroll
+                for (int k = 2 * HM; k < NW; ++k) {
+                    const long long o = s_doff[k];
+                    win[k] = o >= 0 ? __ldg(db + o) : 0.f;
+                }
             } else {
-                const int n = base + step * (k - NW);
-                s_eoff[k - NW] = n < a.n1 ? tl_slot(a.E, n - a.n0) : -1;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    const long long o = s_doff[k];
+                    win[k] = o >= 0 ? __ldg(db + o) : 0.f;
+                }
             }
-        }
-        __syncthreads();
-        if (!act) continue;
-        if (k0 > 0) {                                     // carried over from the previous chunk
+            float acc[JC];
 #pragma unroll
-            for (int k = 0; k < 2 * HM; ++k) win[k] = win[k + JC];
+            for (int j = 0; j < JC; ++j) acc[j] = 0.f;
 #pragma unroll
-            for (int k = 2 * HM; k < NW; ++k) {
-                const long long o = s_doff[k];
-                win[k] = o >= 0 ? __ldg(db + o) : 0.f;
-            }
-        } else {
+            for (int j = 0; j < JC; ++j)
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const long long o = s_doff[k];
-                win[k] = o >= 0 ? __ldg(db + o) : 0.f;
-            }
-        }
-        float acc[JC];
+                for (int i = 0; i < NH; ++i) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
 #pragma unroll
-        for (int j = 0; j < JC; ++j) acc[j] = 0.f;
-#pragma unroll
-        for (int j = 0; j < JC; ++j)
-#pragma unroll
-            for (int i = 0; i < NH; ++i) acc[j] = fmaf(Wr[i], win[j - i + 2 * HM], acc[j]);
-#pragma unroll
-        for (int j = 0; j < JC; ++j) {
-            const long long eo = s_eoff[j];
-            if (eo >= 0) {
-                float *o = ob + eo;
-                *o = a.accumulate ? *o + acc[j] : acc[j];
+            for (int j = 0; j < JC; ++j) {
+                const long long eo = s_eoff[j];
+                if (eo >= 0) {
+                    float *o = ob + eo;
+                    *o = a.accumulate ? *o + acc[j] : acc[j];
+                }
             }
         }
     }
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
     const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
     if (X >= a.x_hi) return;
     const int Z = a.z_lo + blockIdx.y;
-    const int r = blockIdx.z % (2 * a.lag), s = blockIdx.z / (2 * a.lag);   // (shot, residue), as above
+    const int r = blockIdx.z % (2 * a.lag), s = blockIdx.z / (2 * a.lag);   // (shot, residue)
     const long long pp = (long long)Z * a.NXP + X, off = (long long)s * a.P + pp;
     const int hm = (a.nh - 1) / 2;
     for (int n = a.n0 + r; n < a.n1; n += 2 * a.lag) {   // the residue class's outputs
@@ -285,7 +289,9 @@ cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     if (a.jc != 16 && a.jc != 20 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
-    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * 2 * a.lag);
+    // generic nh: one thread per (point, shot, residue); templated: per (point, shot)
+    const bool gen = a.nh != 1 && a.nh != 3 && a.nh != 5 && a.nh != 11 && a.nh != 21 && a.nh != 31 && a.nh != 41;
+    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo, a.S * (gen ? 2 * a.lag : 1));
     switch (a.nh) {
     case 1: launch_tlag_scatter_nh<1>(a, grid, st); break;
     case 3: launch_tlag_scatter_nh<3>(a, grid, st); break;
