@@ -456,11 +456,12 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
     const int nwx = (a.x_hi - a.x_lo + Sh::WOUT - 1) / Sh::WOUT;        // warps per row
     const long long nw = (long long)nwx * (a.z_hi - a.z_lo);
     constexpr bool CAN_SPLIT = FWIME_SC_BALANCE;
-    static bool attr = false;      // once per instantiation, before any launch (and any capture)
-    static int resident = 0;       // CTAs per SM of the least resident variant
-    if (!attr) {
+    // once per instantiation, before any launch (and any capture); a function-local static is
+    // initialised once even when several host threads launch: the attributes, then the CTAs per SM of
+    // the least resident variant
+    static const int resident = [] {
         int r[4] = {0, 0, 0, 0};
-        const auto setup = [&](auto kern, int &res) {
+        const auto setup = [](auto kern, int &res) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, kern, SC_WARPS * 32, Sh::SMEM);
         };
@@ -471,9 +472,8 @@ static void launch_scatter_ps(ExtArgs a, cudaStream_t st)
             setup(k_scatter_ps<NH, A, 1, true>, r[2]);
             setup(k_scatter_ps<NH, A, -1, true>, r[3]);
         }
-        resident = std::max(1, std::min(std::min(r[0], r[1]), std::min(r[2], r[3])));
-        attr = true;
-    }
+        return std::max(1, std::min(std::min(r[0], r[1]), std::min(r[2], r[3])));
+    }();
     // Split every task's pairs into nsplit parts, nsplit <= 8 and parts of at least 4 ring depths of
     // pairs, picked to fill the last wave of resident CTAs best (the smallest within 1 %).
     int nsplit = 1;
@@ -965,11 +965,10 @@ static void launch_image_ps(const ImgArgs &a, cudaStream_t st)
     int u_lo = a.x_lo - Sh::HM;    // first u = x - h of the physical columns, made even
     u_lo -= ((u_lo % 2) + 2) % 2;
     dim3 grid((a.x_hi + Sh::HM - u_lo + 255) / 256, a.z_hi - a.z_lo);
-    static bool attr = false;      // once per instantiation, before any launch (and any capture)
-    if (!attr) {
+    // once per instantiation, before any launch (and any capture), thread-safe (function-local static)
+    static const cudaError_t attr =
         cudaFuncSetAttribute(k_image_ps<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-        attr = true;
-    }
+    (void)attr;
     k_image_ps<NH><<<grid, Sh::TX, Sh::SMEM, st>>>(a, u_lo);
 }
 

@@ -513,11 +513,10 @@ cudaError_t launch_prop_group(const GroupMember *m, int nactive, int ctas, const
 template <int LOC, bool D2, bool SRC, bool INJ = false>
 static void launch_prop_t(const PropArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
+    // once per instantiation, thread-safe (function-local static)
+    static const cudaError_t attr =
         cudaFuncSetAttribute(k_prop<LOC, D2, SRC, INJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr = true;
-    }
+    (void)attr;
     k_prop<LOC, D2, SRC, INJ><<<grid, block, smem, st>>>(a);
 }
 
