@@ -2107,6 +2107,78 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
     return FWIME_OK;
 }
 
+// Stencil chunking (rows per warp) for launches of S shots: every candidate of a ladder and the chunkings
+// that come closest to whole waves of resident warps, timed on the plain variant (reps launches after one
+// warm-up, two passes, the faster kept).  Times within 1 % are noise at this length, so among them the
+// chunking whose last wave is fullest wins (a partly filled last wave idles SMs in every launch, which a
+// long run of launches shows more than the timing does).
+static int pick_zchunk(fwime_ctx *x, Run &r, int S, std::vector<int> cand, int reps, float *us_out)
+{
+    const int rows = x->NZ - 8;
+    const long long per_chunk = (long long)((x->NXP + STRIP - 1) / STRIP) * S;   // warps per chunk row
+    long long resident = 0;
+    int bps = 0, nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && prop_occupancy(&bps) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && bps > 0) {
+        resident = (long long)bps * nsm * PROP_WARPS;
+        for (int waves = 1; waves <= 12; ++waves) {
+            const long long nchunk = (waves * resident) / per_chunk;
+            if (nchunk < 1) continue;
+            const int zc = (int)((rows + nchunk - 1) / nchunk);
+            if (zc >= 4 && zc <= 512) cand.push_back(zc);
+        }
+    }
+    cudaGetLastError();
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    while (cand.size() > 1 && cand.back() > rows) cand.pop_back();
+    auto fill = [&](int zc) {   // used fraction of the launch's waves of resident warps
+        if (resident <= 0) return 1.0;
+        const double w = (double)per_chunk * ((rows + zc - 1) / zc) / (double)resident;
+        return w / std::ceil(w);
+    };
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    std::vector<float> us(cand.size(), 1e30f);
+    int rc = FWIME_OK;
+    for (int pass = 0; pass < 2 && rc == FWIME_OK; ++pass) {
+        for (size_t i = 0; i < cand.size() && rc == FWIME_OK; ++i) {
+            x->opt_zchunk = cand[i];
+            init_run(x, r, S);
+            rc = prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0);
+            if (rc != FWIME_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e0, x->st) != cudaSuccess) { rc = FWIME_ECUDA; break; }
+            for (int it = 0; it < reps && rc == FWIME_OK; ++it)
+                rc = prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0);
+            if (rc != FWIME_OK) break;
+            if (cudaEventRecord(e1, x->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = FWIME_ECUDA;
+                break;
+            }
+            us[i] = std::min(us[i], 1e3f * ms / reps);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FWIME_OK) return 0;
+    float best = 1e30f;
+    for (float u : us) best = std::min(best, u);
+    size_t pi = cand.size();
+    for (size_t i = 0; i < cand.size(); ++i) {
+        if (us[i] > 1.01f * best) continue;
+        const double df = pi == cand.size() ? 1.0 : fill(cand[i]) - fill(cand[pi]);
+        if (df > 1e-9 || (df > -1e-9 && us[i] < us[pi])) pi = i;
+    }
+    if (us_out) *us_out = us[pi];
+    return cand[pi];
+}
+
 int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_out)
 {
     if (!x || op < 0 || op > FWIME_OP_OBJECTIVE) return FWIME_EINVAL;
@@ -2121,51 +2193,13 @@ int fwime_autotune(fwime_ctx *x, int op, int *zchunk_out, float *us_per_launch_o
     TRY(zero(x, r.w.gx, sizeof(float) * x->NXP));
     TRY(zero(x, r.w.f[0], sizeof(float) * S * x->P));
     TRY(zero(x, r.w.f[1], sizeof(float) * S * x->P));
-    const int rows = x->NZ - 8;
-    // candidates: a fixed ladder plus the chunkings that make the work a whole number of waves of
-    // resident warps (a partly filled last wave idles most of the GPU for its duration)
-    std::vector<int> cand = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
-    int bps = 0, nsm = 0, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && prop_occupancy(&bps) == cudaSuccess &&
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && bps > 0) {
-        const long long resident = (long long)bps * nsm * PROP_WARPS;
-        const long long per_chunk = (long long)((x->NXP + STRIP - 1) / STRIP) * S;   // warps per chunk row
-        for (int waves = 1; waves <= 12; ++waves) {
-            const long long nchunk = (waves * resident) / per_chunk;
-            if (nchunk < 1) continue;
-            const int zc = (int)((rows + nchunk - 1) / nchunk);
-            if (zc >= 4 && zc <= 512) cand.push_back(zc);
-        }
-    }
-    cudaGetLastError();
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
     const int saved = x->opt_zchunk, saved_prof = x->opt_profile;
     x->opt_profile = 0;
-    int best = 0;
-    float best_us = 1e30f;
-    for (int zc : cand) {
-        if (zc > rows && zc != cand.front()) break;
-        x->opt_zchunk = zc;
-        init_run(x, r, S);
-        for (int it = 0; it < 2; ++it) TRY(prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0));
-        const int reps = 6;
-        CK(cudaEventRecord(e0, x->st));
-        for (int it = 0; it < reps; ++it) TRY(prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0));
-        CK(cudaEventRecord(e1, x->st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        const float us = 1e3f * ms / reps;
-        if (us < best_us) { best_us = us; best = zc; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    float best_us = 0.f;
+    const int best = pick_zchunk(x, r, S, {8, 16, 24, 32, 48, 64, 96, 128, 192, 256}, 6, &best_us);
     x->opt_profile = saved_prof;
     x->opt_zchunk = best > 0 ? best : saved;
+    if (best == 0) return fail(x, FWIME_ECUDA, "stencil chunking timing failed");
     if (zchunk_out) *zchunk_out = x->opt_zchunk;
     if (us_per_launch_out) *us_per_launch_out = best_us;
     return FWIME_OK;
@@ -2243,35 +2277,9 @@ int fwime_autotune_schedule(fwime_ctx *x, int op, fwime_schedule *res)
             rc = zero(x, x->ws, x->ws_bytes);
             if (rc != FWIME_OK) break;
             // stencil: the chunking candidates (a ladder and whole waves of resident warps)
-            const int rows = x->NZ - 8;
-            std::vector<int> cand = {16, 32, 48, 64, 96, 128};
-            int bps = 0, nsm = 0, dev = 0;
-            if (cudaGetDevice(&dev) == cudaSuccess && prop_occupancy(&bps) == cudaSuccess &&
-                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && bps > 0) {
-                const long long resident = (long long)bps * nsm * PROP_WARPS;
-                const long long per_chunk = (long long)((x->NXP + STRIP - 1) / STRIP) * S;
-                for (int waves = 1; waves <= 12; ++waves) {
-                    const long long nchunk = (waves * resident) / per_chunk;
-                    if (nchunk < 1) continue;
-                    const int zc = (int)((rows + nchunk - 1) / nchunk);
-                    if (zc >= 4 && zc <= 512) cand.push_back(zc);
-                }
-            }
-            cudaGetLastError();
-            std::sort(cand.begin(), cand.end());
-            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-            float tp = 1e30f;
-            int zbest = 0;
-            for (int zc : cand) {
-                if (zc > rows && zc != cand.front()) break;
-                x->opt_zchunk = zc;
-                init_run(x, r, S);
-                float us = 0.f;
-                rc = timed([&]() { return prop(r, S, r.w.f[0], r.w.f[1], r.w.f[1], nullptr, nullptr, 0); }, 4, us);
-                if (rc != FWIME_OK) break;
-                if (us < tp) { tp = us; zbest = zc; }
-            }
-            if (rc != FWIME_OK) break;
+            float tp = 0.f;
+            const int zbest = pick_zchunk(x, r, S, {16, 32, 48, 64, 96, 128}, 4, &tp);
+            if (zbest == 0) { rc = FWIME_ECUDA; break; }
             x->opt_zchunk = zbest;
             init_run(x, r, S);
             const int kk = std::min(K, x->g.nt - 1);
