@@ -162,6 +162,9 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #ifndef FWIME_IMG_F32X2
 #define FWIME_IMG_F32X2 1
 #endif
+#ifndef FWIME_IMG_PACK_NH
+#define FWIME_IMG_PACK_NH 21   // largest nh whose imaging kernel uses the packed form
+#endif
 #ifndef FWIME_SC_PAIRS
 #define FWIME_SC_PAIRS 0      // (step, shot) pairs per loop iteration of the scatter (sharing its weights);
                               // 0: two at nh 21 and 31 (measured -4.3 % at nh 31, -0.6 % at nh 21), else one
@@ -628,7 +631,7 @@ struct ImgTaskBody {
     // packed two-lane form: the products of one D sample with the L pair (2 q, 2 q + 1) of a window
     // accumulate in one register pair when both lie in the band; the band's edge entries whose
     // partner lies outside stay scalar
-    static constexpr bool PACK = FWIME_IMG_F32X2 && NH <= 21;   // measured slower at nh 31
+    static constexpr bool PACK = FWIME_IMG_F32X2 && NH <= FWIME_IMG_PACK_NH;   // measured slower at nh 31
     static constexpr int P1 = PACK ? W1 / 2 : 1, P2 = PACK && W2 >= 2 ? W2 / 2 : 1;
     float acc1[8][W1], acc2[8][W2];
     f32x2 pac1[8][P1], pac2[8][P2];
