@@ -154,16 +154,16 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src)
 #define FWIME_SC_A31 4
 #endif
 // packed two-lane FP32 (f32x2) forms of the multiply-adds, per kernel where they measured faster
-// (B~ + B~* on the Marmousi2-shaped grid: scatter -1 % at nh 21; imaging -5.5 % at nh 21, +2.7 %
-// at nh 31, so the imaging kernel packs only up to nh 21)
+// (scatter -1 % at nh 21; imaging -5.5 % at nh 21 (Marmousi2-shaped B~ + B~*), +1.4 % at nh 31
+// (North-Sea-shaped gradient), -16 % at nh 41 (Salt-shaped gradient): every nh but 31 packs)
 #ifndef FWIME_SC_F32X2
 #define FWIME_SC_F32X2 1
 #endif
 #ifndef FWIME_IMG_F32X2
 #define FWIME_IMG_F32X2 1
 #endif
-#ifndef FWIME_IMG_PACK_NH
-#define FWIME_IMG_PACK_NH 21   // largest nh whose imaging kernel uses the packed form
+#ifndef FWIME_IMG_UNPACKED_NH
+#define FWIME_IMG_UNPACKED_NH 31   // the nh whose imaging kernel keeps the scalar form (packed: +1.4 % time)
 #endif
 #ifndef FWIME_SC_PAIRS
 #define FWIME_SC_PAIRS 0      // (step, shot) pairs per loop iteration of the scatter (sharing its weights);
@@ -631,7 +631,7 @@ struct ImgTaskBody {
     // packed two-lane form: the products of one D sample with the L pair (2 q, 2 q + 1) of a window
     // accumulate in one register pair when both lie in the band; the band's edge entries whose
     // partner lies outside stay scalar
-    static constexpr bool PACK = FWIME_IMG_F32X2 && NH <= FWIME_IMG_PACK_NH;   // measured slower at nh 31
+    static constexpr bool PACK = FWIME_IMG_F32X2 && NH != FWIME_IMG_UNPACKED_NH;   // measured slower at nh 31
     static constexpr int P1 = PACK ? W1 / 2 : 1, P2 = PACK && W2 >= 2 ? W2 / 2 : 1;
     float acc1[8][W1], acc2[8][W2];
     f32x2 pac1[8][P1], pac2[8][P2];
