@@ -2279,7 +2279,7 @@ int fwime_autotune_schedule(fwime_ctx *x, int op, fwime_schedule *res)
             // stencil: the chunking candidates (a ladder and whole waves of resident warps)
             float tp = 0.f;
             const int zbest = pick_zchunk(x, r, S, {16, 32, 48, 64, 96, 128}, 4, &tp);
-            if (zbest == 0) { rc = FWIME_ECUDA; break; }
+            if (zbest == 0) { rc = fail(x, FWIME_ECUDA, "stencil chunking timing failed"); break; }
             x->opt_zchunk = zbest;
             init_run(x, r, S);
             const int kk = std::min(K, x->g.nt - 1);
