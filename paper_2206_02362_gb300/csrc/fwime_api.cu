@@ -342,6 +342,16 @@ static int plan(fwime_ctx *x, int op, WS &w, bool no_ckpt = false)
         budget = x->ws_bytes + fr;
         budget = budget > ((size_t)2 << 30) ? budget - ((size_t)2 << 30) : budget / 2;   // keep 2 GB slack
     }
+    // a default time-lag segment of 4 Hs that does not fit one shot falls back to 2 Hs (the halo then
+    // equals the segment's own samples; the kernels stay correct for any K)
+    if (x->opt_tlag > 0 && x->opt_K == 0 && w.K > 2 * tlag_Hs(x->g, x->opt_tlag) &&
+        (sz.model + sz.staging + sz.per_shot) * sizeof(float) > budget) {
+        w.K = std::max(std::min(std::max(auto_K(x->g.nt), 2 * tlag_Hs(x->g, x->opt_tlag)), x->g.nt - 1), 1);
+        w.nseg = (x->g.nt - 1 + w.K - 1) / w.K;
+        w.R = w.K + 2;
+        sz = op_sizes(x->g, x->nshot, x->nrec, x->P, x->NZ, x->NXP, op, w.K, x->opt_host_io != 0, no_ckpt,
+                      x->opt_tlag);
+    }
     const size_t fixed = (sz.model + sz.staging) * sizeof(float);
     const size_t per = sz.per_shot * sizeof(float);
     int S;

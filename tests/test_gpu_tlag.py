@@ -126,3 +126,24 @@ def test_time_lag_tomo_and_gradient_match_oracle(nh, lag, opts):
     assert rel(ta.double().cpu().numpy(), ref_ta) <= TOL
     assert rel(g.double().cpu().numpy(), g_ref) <= TOL
     assert abs(J - J_ref) <= 1e-5 * abs(J_ref) and abs(Jo - J_ref) <= 1e-5 * abs(J_ref)
+
+
+def test_time_lag_segment_falls_back_when_the_long_one_does_not_fit():
+    """The default time-lag segment (4 Hs steps) needs more workspace per shot than 2 Hs; under a budget
+    between the two the context plans 2 Hs segments instead of refusing, with the same results."""
+    c = TL(5, 3)                      # Hs = 12: default K = 48, fallback K = 24
+    v, w = c.v.astype(np.float64), c.w.astype(np.float64)
+    ref_i = oracle.born_ext_adj(c.og, v, c.ogeo, w, c.d.astype(np.float64))
+    img = torch.zeros(c.pt.shape, device="cuda")
+    ws = {}
+    for seg in (0, 24):
+        with c.ctx(shots_per_batch=1, segment=seg) as ctx:
+            ctx.born_ext_adj(T(c.v), T(c.w), T(c.d), img)
+            ws[seg] = ctx.get_option("workspace")
+    assert ws[0] > ws[24]
+    with fw.Context(c.fg, c.fgeo, max_workspace_bytes=(ws[0] + ws[24]) // 2, time_lag=c.lag,
+                    shots_per_batch=1) as ctx:
+        img.zero_()
+        ctx.born_ext_adj(T(c.v), T(c.w), T(c.d), img)
+        assert ctx.get_option("workspace") <= (ws[0] + ws[24]) // 2
+    assert rel(img.double().cpu().numpy(), ref_i) <= TOL
