@@ -254,7 +254,9 @@ int fwime_forward_group(fwime_ctx *const *ctxs, int n, const float *const *v, co
 /* Autotuner of the stencil kernel's tiling: plans the workspace of operator
  * `op` (so the batch size is the one the operator will use), then times the
  * time-step kernel on that batch for candidate rows-per-warp chunkings with
- * CUDA events and keeps the fastest (FWIME_OPT_ZCHUNK).  Synchronous.  Returns
+ * CUDA events (two passes, the faster of each kept) and keeps the fastest,
+ * except that among chunkings within 1 % of it the one whose last wave of
+ * resident warps is fullest wins (FWIME_OPT_ZCHUNK).  Synchronous.  Returns
  * the chosen chunking and its time per launch (either pointer may be NULL). */
 int fwime_autotune(fwime_ctx *ctx, int op, int *zchunk, float *us_per_launch);
 
@@ -325,8 +327,8 @@ int fwime_server_last_error(char *buf, size_t n);
 
 /* Schedule autotuner for operator `op`: segment length K (the automatic one, half and double, unless
  * FWIME_OPT_SEGMENT fixes it) x shots per launch S (the largest equal batch that fits at that K, and half
- * of it) x the stencil's rows per warp.  At every (K, S) it plans the operator's workspace, times the stencil
- * for its chunking candidates and the operator's extension kernels once over a full segment of K x S
+ * of it) x the stencil's rows per warp.  At every (K, S) it plans the operator's workspace, picks the stencil
+ * chunking as fwime_autotune does, times the operator's extension kernels once over a full segment of K x S
  * (step, shot) pairs with CUDA events, and models the time per shot as
  *   ((nt - 1) props t_stencil + nseg (scatters t_scatter + images t_image)) / S
  * with the operator's launches per step and per segment.  The fastest schedule is set as the context's
