@@ -25,6 +25,10 @@ namespace fwk {
 #define FWIME_TL_IMG_MINB 4   // resident CTAs the imaging kernel is compiled for (up to 21 lags, JC <= 24; spills beyond)
 #endif
 constexpr int TL_TX = 128;      // threads per CTA (consecutive columns)
+#ifndef FWIME_TLI_TX
+#define FWIME_TLI_TX 128
+#endif
+constexpr int TLI_TX = FWIME_TLI_TX;   // threads per CTA of the lag imaging kernel
 // JC, the outputs of one residue class a thread handles (one chunk), is 16, 24 or 32, chosen per
 // segment by tlag_jc so that the chunks cover the class's outputs with the fewest wasted window loads
 
@@ -136,11 +140,12 @@ __global__ void __launch_bounds__(TL_TX) k_tlag_scatter_gen(const TlagArgs a)
 // CTA: computed once per iteration into shared memory.  Within a residue class the chunks' windows
 // overlap by 2 hm samples, carried over in registers (each D sample loaded once per class and segment).
 template <int NH, int JC>
-__global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_MINB : 1) k_tlag_image(const TlagArgs a)
+__global__ void __launch_bounds__(TLI_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_MINB * 128 / TLI_TX : 1)
+    k_tlag_image(const TlagArgs a)
 {
     constexpr int HM = (NH - 1) / 2, NW = JC + 2 * HM;
     __shared__ long long s_doff[NW], s_loff[JC];
-    const int X = a.x_lo + blockIdx.x * TL_TX + threadIdx.x;
+    const int X = a.x_lo + blockIdx.x * TLI_TX + threadIdx.x;
     const bool act = X < a.x_hi;                          // no early exit: the CTA shares barriers
     const int Z = a.z_lo + blockIdx.y;
     const long long pp = (long long)Z * a.NXP + (act ? X : a.x_lo);
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(TL_TX, (NH <= 21 && JC <= 24) ? FWIME_TL_IMG_M
             for (int base = a.n0 + r, k0 = 0; base < a.n1; base += step * JC, k0 = 2 * HM) {
                 const int m0 = base - step * HM;
                 __syncthreads();                          // every thread is done with the previous tables
-                for (int k = threadIdx.x; k < NW + JC; k += TL_TX) {
+                for (int k = threadIdx.x; k < NW + JC; k += TLI_TX) {
                     if (k < NW) {
                         const int m = m0 + step * k;
                         s_doff[k] = (m >= 0 && m <= a.nt - 2) ? tl_slot(a.D, m) : -1;
@@ -308,17 +313,18 @@ cudaError_t launch_tlag_scatter(const TlagArgs &a, cudaStream_t st)
 template <int NH>
 static void launch_tlag_image_nh(const TlagArgs &a, dim3 grid, cudaStream_t st)
 {
-    if (a.jc == 20) k_tlag_image<NH, 20><<<grid, TL_TX, 0, st>>>(a);
-    else if (a.jc == 24) k_tlag_image<NH, 24><<<grid, TL_TX, 0, st>>>(a);
-    else if (a.jc == 32) k_tlag_image<NH, 32><<<grid, TL_TX, 0, st>>>(a);
-    else k_tlag_image<NH, 16><<<grid, TL_TX, 0, st>>>(a);
+    if (a.jc == 20) k_tlag_image<NH, 20><<<grid, TLI_TX, 0, st>>>(a);
+    else if (a.jc == 24) k_tlag_image<NH, 24><<<grid, TLI_TX, 0, st>>>(a);
+    else if (a.jc == 32) k_tlag_image<NH, 32><<<grid, TLI_TX, 0, st>>>(a);
+    else k_tlag_image<NH, 16><<<grid, TLI_TX, 0, st>>>(a);
 }
 
 cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
 {
     if (a.n1 <= a.n0 || a.x_hi <= a.x_lo || a.z_hi <= a.z_lo) return cudaSuccess;
     if (a.jc != 16 && a.jc != 20 && a.jc != 24 && a.jc != 32) return cudaErrorInvalidValue;
-    dim3 grid((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo);
+    dim3 grid((a.x_hi - a.x_lo + TLI_TX - 1) / TLI_TX, a.z_hi - a.z_lo);
+    dim3 grid_gen((a.x_hi - a.x_lo + TL_TX - 1) / TL_TX, a.z_hi - a.z_lo);
     switch (a.nh) {
     case 1: launch_tlag_image_nh<1>(a, grid, st); break;
     case 3: launch_tlag_image_nh<3>(a, grid, st); break;
@@ -327,7 +333,7 @@ cudaError_t launch_tlag_image(const TlagArgs &a, cudaStream_t st)
     case 21: launch_tlag_image_nh<21>(a, grid, st); break;
     case 31: launch_tlag_image_nh<31>(a, grid, st); break;
     case 41: launch_tlag_image_nh<41>(a, grid, st); break;
-    default: k_tlag_image_gen<<<grid, TL_TX, 0, st>>>(a);
+    default: k_tlag_image_gen<<<grid_gen, TL_TX, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
