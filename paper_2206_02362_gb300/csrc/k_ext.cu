@@ -903,10 +903,7 @@ __global__ void __launch_bounds__(EXT_TX) k_image_gen(const ImgArgs a)
 // Local imaging: a thread owns 4 consecutive columns (16-byte loads) of one row, a CTA 512 columns, so
 // every (step, shot) pair is read as long contiguous row segments; columns start at x_lo rounded down to
 // a multiple of 4 and only [x_lo, x_hi) is accumulated.
-#ifndef FWIME_LOC_TX
-#define FWIME_LOC_TX 128
-#endif
-constexpr int LOC_TX = FWIME_LOC_TX;
+constexpr int LOC_TX = 128;
 __device__ __forceinline__ float4 ldg4e(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __global__ void __launch_bounds__(LOC_TX) k_image_local(const ImgArgs a, int xa)
 {
