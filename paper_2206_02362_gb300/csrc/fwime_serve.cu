@@ -29,10 +29,6 @@
 #include "../../include/fwime.h"
 #include "fwime_internal.h"
 
-#ifndef FWIME_SERVE_WORKERS
-#define FWIME_SERVE_WORKERS 12   // enqueue threads at most (each issues one request's launches at a time)
-#endif
-
 namespace fwk {
 
 namespace {
@@ -424,7 +420,7 @@ int fwime_server_create(fwime_ctx **out, size_t memory_budget, int max_active, i
     s->budget = memory_budget;
     s->options = options;
     s->max_active = (options & FWIME_SERVE_PLAIN) ? 1 : max_active;
-    s->nworkers = std::min(FWIME_SERVE_WORKERS, s->max_active);
+    s->nworkers = std::min(12, s->max_active);
     s->dispatcher = std::thread(dispatch_loop, s);
     for (int i = 0; i < s->nworkers; ++i) s->workers.emplace_back(worker_loop, s);
     *out = ctx_for_server(s);
