@@ -603,17 +603,19 @@ static int scatter(Run &r, int Sb, int n0, int kk, const float *W, RingRef in, R
     return FWIME_OK;
 }
 
+// img_local (IMG_EXT only): the same launch also adds the IMG_LOCAL terms of M2 and Ds into it
 static int image(Run &r, int Sb, int n0, int kk, int mode, RingRef D, RingRef L, RingRef M2, RingRef Ds, float alpha,
-                 const float *pt, float *img)
+                 const float *pt, float *img, float *img_local = nullptr)
 {
     fwime_ctx *x = r.x;
     ImgArgs a{};
     a.NXP = x->NXP; a.nh = x->g.nh; a.hm = (x->g.nh - 1) / 2; a.S = Sb; a.npair = kk * Sb; a.n0 = n0; a.P = x->P;
     a.z_lo = x->o; a.z_hi = x->o + x->g.nz; a.x_lo = x->o; a.x_hi = x->o + x->g.nx;   // the physical columns
-    a.D = D; a.L = L; a.M2 = M2; a.Ds = Ds; a.alpha = alpha; a.pt = pt; a.img = img;
+    a.D = D; a.L = L; a.M2 = M2; a.Ds = Ds; a.alpha = alpha; a.pt = pt; a.img = img; a.img_local = img_local;
     const double pts = (double)x->g.nz * x->g.nx;
     const double per = 8.0 + (M2.base ? 4 : 0) + (Ds.base ? 4 : 0);
-    const double once = mode == IMG_EXT ? 8.0 * x->g.nh : (mode == IMG_CONTRACT ? 8.0 + 4.0 * x->g.nh : 8.0);
+    const double once = mode == IMG_EXT ? 8.0 * x->g.nh + (img_local ? 8.0 : 0.0)
+                                        : (mode == IMG_CONTRACT ? 8.0 + 4.0 * x->g.nh : 8.0);
     LAUNCH(FWIME_K_IMAGE, pts * ((double)a.npair * per + once), launch_image(a, mode, x->st));
     return FWIME_OK;
 }
@@ -1379,10 +1381,10 @@ static int run_tomo_adj(fwime_ctx *x, Run &r, int mode, const float *v, const fl
                 TRY(prop(r, Sb, Mu2 + ((m + 1) % R) * SP, Mu2 + ((m + 2) % R) * SP, Mu2 + (m % R) * SP, nullptr,
                          nullptr, 0, Er + (m - n0 - 1) * SP, 1.f));
             }
-            TRY(image(r, Sb, n0, kk, IMG_LOCAL, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(Mu2, SP, R, 1),
-                      ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc1));
-            TRY(image(r, Sb, n0, kk, IMG_EXT, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1),
-                      ringref(nullptr, 0, 0, 0), ringref(nullptr, 0, 0, 0), 0.f, nullptr, r.w.acc2));
+            // the extended image of the residual's adjoint field (contracted with p~ at the end) and, in the
+            // same launch, the local terms D0 (alpha lambda^ + mu2) + Ds lambda^
+            TRY(image(r, Sb, n0, kk, IMG_EXT, ringref(D0r, SP, 0, 0), ringref(Mu, SP, R, 1), ringref(Mu2, SP, R, 1),
+                      ringref(Dsr, SP, 0, 0), grad ? 1.f : 0.f, nullptr, r.w.acc2, r.w.acc1));
         }
     }
     if (bwd)

@@ -163,6 +163,7 @@ struct ImgArgs {
     float alpha;                   // IMG_LOCAL: weight of D * L
     const float *pt;               // IMG_CONTRACT: p~ padded [nh][P]
     float *img;                    // IMG_EXT: [nh][P]; others: [P]
+    float *img_local;              // IMG_EXT, optional: [P] += the IMG_LOCAL terms (alpha D L + D M2 + Ds L)
 };
 
 // time-lag extension: one segment [n0, n1) of output steps, S shots

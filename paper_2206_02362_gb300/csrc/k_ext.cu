@@ -577,6 +577,18 @@ __host__ __device__ constexpr bool img_tasks_tile(int nh)
 static_assert(img_tasks_tile(1) && img_tasks_tile(3) && img_tasks_tile(5) && img_tasks_tile(11) &&
               img_tasks_tile(21) && img_tasks_tile(31) && img_tasks_tile(41), "imaging tasks must tile the band");
 
+// the task whose first window holds offset 0 for all 8 of a lane's ut (wt - ut = 0): it owns h = 0
+__host__ __device__ constexpr int img_h0_task(int nh)
+{
+    for (int k = 0; k < img_ntask(nh); ++k) {
+        const ImgTask t = img_task(nh, k);
+        if (t.lo1 <= 0 && t.lo1 + 4 * t.nl1 > 7) return k;
+    }
+    return -1;
+}
+static_assert(img_h0_task(1) >= 0 && img_h0_task(3) >= 0 && img_h0_task(5) >= 0 && img_h0_task(11) >= 0 &&
+              img_h0_task(21) >= 0 && img_h0_task(31) >= 0 && img_h0_task(41) >= 0, "h = 0 in one first window");
+
 __host__ __device__ constexpr int img_hc(int len)     // chunk pairs of a parity array (== 2 mod 8: no conflicts)
 {
     int h = 2 * ((len + 15) / 16);
@@ -617,15 +629,20 @@ struct ImgShape {
     static constexpr int OFFD = (8 * HCD + 31) / 32 * 32 + 16, OFFL = (8 * HCL + 31) / 32 * 32 + 16;
     static constexpr int REGD = OFFD + 8 * HCD;              // D region (floats); the L region follows
     static constexpr int STG = (REGD + OFFL + 8 * HCL + 3) / 4 * 4;
+    // with the local terms two more D-shaped regions follow (second adjoint field, scattered D2t)
+    static constexpr int STGL = STG + 2 * REGD;
     static constexpr int NCD = (2 * LD + TX - 1) / TX, NCL = (2 * LL + TX - 1) / TX;
     static constexpr size_t SMEM = (size_t)EXT_STAGES * STG * sizeof(float);
+    static constexpr size_t SMEML = (size_t)EXT_STAGES * STGL * sizeof(float);
     static_assert(REGD % 8 == 0 && LO % 4 == 0, "alignment");
 };
 
-// one task's share of a pair: products of the lane's 8 D samples with its L window(s)
-template <int NH, int K>
+// one task's share of a pair: products of the lane's 8 D samples with its L window(s).  LOCAL: the task
+// that owns h = 0 also sums the local terms D M2 + Ds L at its 8 points (x = u, where it holds D(u) and L(u))
+template <int NH, int K, bool LOCAL = false>
 struct ImgTaskBody {
     static constexpr ImgTask T = img_task(NH, K);
+    static constexpr bool LH0 = LOCAL && K == img_h0_task(NH);
     static constexpr int HM = (NH - 1) / 2;
     static constexpr int W1 = 4 * T.nl1, W2 = T.nl2 > 0 ? 4 * T.nl2 : 1;
     // packed two-lane form: the products of one D sample with the L pair (2 q, 2 q + 1) of a window
@@ -635,6 +652,7 @@ struct ImgTaskBody {
     static constexpr int P1 = PACK ? W1 / 2 : 1, P2 = PACK && W2 >= 2 ? W2 / 2 : 1;
     float acc1[8][W1], acc2[8][W2];
     f32x2 pac1[8][P1], pac2[8][P2];
+    float loc[LH0 ? 8 : 1];
 
     __device__ __forceinline__ static constexpr bool in1(int i, int j) { return (T.lo1 + j - i) <= HM && (T.lo1 + j - i) >= -HM; }
     __device__ __forceinline__ static constexpr bool in2(int i, int j)
@@ -657,6 +675,8 @@ struct ImgTaskBody {
 #pragma unroll
             for (int q = 0; q < P2; ++q) pac2[i][q] = pk(0.f, 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < (LH0 ? 8 : 1); ++i) loc[i] = 0.f;
     }
     // loads the lane's L window [8 b + LOW, 8 b + LOW + 4 NL) of wt: chunks c0 + q of the L region
     // (which starts at wt = LO), chunk c at slot (c & 1) hcl + (c >> 1)
@@ -671,18 +691,30 @@ struct ImgTaskBody {
             lv[4 * q] = v.x; lv[4 * q + 1] = v.y; lv[4 * q + 2] = v.z; lv[4 * q + 3] = v.w;
         }
     }
-    __device__ __forceinline__ void pair(const float *sd, const float *sl, int b)
+    // the lane's 8 samples of a D-shaped region (its ut = 8 b .. 8 b + 7 of its parity)
+    __device__ __forceinline__ static void load8(float (&v)[8], const float *sd, int b)
+    {
+        const float4 d0 = *reinterpret_cast<const float4 *>(sd + 4 * b);
+        const float4 d1 = *reinterpret_cast<const float4 *>(sd + 4 * (ImgShape<NH>::HCD + b));
+        v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
+        v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
+    }
+    // sm2, sds: the lane's parity array of the second adjoint field and the scattered D2t (LOCAL only)
+    __device__ __forceinline__ void pair(const float *sd, const float *sl, int b, const float *sm2 = nullptr,
+                                         const float *sds = nullptr)
     {
         using Sh = ImgShape<NH>;
         float dv[8];
-        {
-            const float4 d0 = *reinterpret_cast<const float4 *>(sd + 4 * b);
-            const float4 d1 = *reinterpret_cast<const float4 *>(sd + 4 * (Sh::HCD + b));
-            dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
-            dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
-        }
+        load8(dv, sd, b);
         float l1[W1];
         load_window<T.lo1, T.nl1>(l1, sl, b, Sh::HCL);
+        if constexpr (LH0) {   // x = u_i: D(u_i) = dv[i], L(u_i) = l1[i - lo1]
+            float mv[8], sv[8];
+            load8(mv, sm2, b);
+            load8(sv, sds, b);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) loc[i] = fmaf(sv[i], l1[i - T.lo1], fmaf(dv[i], mv[i], loc[i]));
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const f32x2 dd = pk(dv[i], dv[i]);
@@ -731,9 +763,18 @@ struct ImgTaskBody {
         return acc2[i][j];
     }
     // adds the accumulators into img at x = x1 + i + o, h = o - i (o = lo + j), x1 = the lane's
-    // first u + its first ut offset; only physical columns [x_lo, x_hi)
+    // first u + its first ut offset; only physical columns [x_lo, x_hi).  LOCAL: img_local at x = x1 + 2 i
+    // gains alpha x (its h = 0 sum of D L) + its local terms
     __device__ __forceinline__ void store(const ImgArgs &a, long long rowoff, int x1)
     {
+        if constexpr (LH0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int x = x1 + 2 * i;
+                if (x >= a.x_lo && x < a.x_hi)
+                    a.img_local[rowoff + x] += fmaf(a.alpha, val1(i, i - T.lo1), loc[i]);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
 #pragma unroll
@@ -758,11 +799,13 @@ struct ImgTaskBody {
 // instantiation of the same pipeline): the non-.aligned form of bar.sync
 __device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;\n" ::: "memory"); }
 
-template <int NH, int K>
+template <int NH, int K, bool LOCAL = false>
 __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *sm, int lane)
 {
     using Sh = ImgShape<NH>;
     constexpr int NS = EXT_STAGES;
+    constexpr int STG = LOCAL ? Sh::STGL : Sh::STG;   // floats per stage
+    constexpr unsigned MOFF = 4u * Sh::STG, SOFF = 4u * (Sh::STG + Sh::REGD);   // bytes to the local regions
     const int Z = a.z_lo + blockIdx.y;
     const long long rowoff = (long long)Z * a.NXP;
     const int ub = u_lo + 256 * blockIdx.x;         // even
@@ -778,21 +821,32 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
     const int colD = ub + t, colL = ub + 2 * Sh::LO + t;
     // all copied columns, [ub + 2 LO, ub + 2 LO + 2 LL) (which contains the D window), inside the row
     const bool interior = ub + 2 * Sh::LO >= 0 && ub + 2 * Sh::LO + 2 * Sh::LL <= a.NXP;
-    PairRow pd, pl;
+    PairRow pd, pl, pm, ps;
     pd.init(a.D, a.n0, a.S, a.P, rowoff);
     pl.init(a.L, a.n0, a.S, a.P, rowoff);
+    if constexpr (LOCAL) {
+        pm.init(a.M2, a.n0, a.S, a.P, rowoff);
+        ps.init(a.Ds, a.n0, a.S, a.P, rowoff);
+    }
     int st_in = 0, st_c = 0;
     constexpr int FD = 2 * Sh::LD / Sh::TX, RD = 2 * Sh::LD - FD * Sh::TX;   // full copy rounds, remainder
     constexpr int FL = 2 * Sh::LL / Sh::TX, RL = 2 * Sh::LL - FL * Sh::TX;
     auto issue = [&](int p) {
         if (p < a.npair) {
-            const unsigned so = 4u * st_in * Sh::STG;
+            const unsigned so = 4u * st_in * STG;
             if (interior) {
                 const float *sd = pd.row + colD, *sl = pl.row + colL;
                 cpa4_run<CSTEP, 4 * Sh::TX>(dD + so, sd, std::make_integer_sequence<int, FD>{});
                 if (RD > 0 && t < RD) cpa4_imm<CSTEP * FD, 4 * Sh::TX * FD>(dD + so, sd);
                 cpa4_run<CSTEP, 4 * Sh::TX>(dL + so, sl, std::make_integer_sequence<int, FL>{});
                 if (RL > 0 && t < RL) cpa4_imm<CSTEP * FL, 4 * Sh::TX * FL>(dL + so, sl);
+                if constexpr (LOCAL) {   // the second adjoint field and the scattered D2t: D's window and layout
+                    const float *smv = pm.row + colD, *ssv = ps.row + colD;
+                    cpa4_run<CSTEP, 4 * Sh::TX>(dD + so + MOFF, smv, std::make_integer_sequence<int, FD>{});
+                    if (RD > 0 && t < RD) cpa4_imm<CSTEP * FD, 4 * Sh::TX * FD>(dD + so + MOFF, smv);
+                    cpa4_run<CSTEP, 4 * Sh::TX>(dD + so + SOFF, ssv, std::make_integer_sequence<int, FD>{});
+                    if (RD > 0 && t < RD) cpa4_imm<CSTEP * FD, 4 * Sh::TX * FD>(dD + so + SOFF, ssv);
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < Sh::NCD; ++c) {
@@ -800,6 +854,10 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
                         const int col = colD + Sh::TX * c;
                         const bool ok = col >= 0 && col < a.NXP;
                         cpa4(dD + so + CSTEP * c, pd.row + (ok ? col : 0), ok);
+                        if constexpr (LOCAL) {
+                            cpa4(dD + so + MOFF + CSTEP * c, pm.row + (ok ? col : 0), ok);
+                            cpa4(dD + so + SOFF + CSTEP * c, ps.row + (ok ? col : 0), ok);
+                        }
                     }
                 }
 #pragma unroll
@@ -813,11 +871,15 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
             }
             pd.next();
             pl.next();
+            if constexpr (LOCAL) {
+                pm.next();
+                ps.next();
+            }
         }
         st_in = st_in + 1 == NS ? 0 : st_in + 1;
         cpa_commit();
     };
-    ImgTaskBody<NH, K> body;
+    ImgTaskBody<NH, K, LOCAL> body;
     body.zero();
     // two pairs per barrier: the prologue fills NS - 2 stages; iteration p waits for pairs p and p + 1,
     // then refills the stages of pairs p - 2 and p - 1, which every warp finished before the barrier
@@ -828,30 +890,35 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
         cta_barrier();
         issue(p + NS - 2);
         issue(p + NS - 1);
-        const float *s0 = sm + st_c * Sh::STG;
+        const float *s0 = sm + st_c * STG;
         st_c = st_c + 1 == NS ? 0 : st_c + 1;
-        const float *s1 = sm + st_c * Sh::STG;
+        const float *s1 = sm + st_c * STG;
         st_c = st_c + 1 == NS ? 0 : st_c + 1;
-        body.pair(s0 + par * Sh::OFFD, s0 + Sh::REGD + par * Sh::OFFL, b);
-        if (p + 1 < a.npair) body.pair(s1 + par * Sh::OFFD, s1 + Sh::REGD + par * Sh::OFFL, b);
+        const int pd0 = par * Sh::OFFD;
+        body.pair(s0 + pd0, s0 + Sh::REGD + par * Sh::OFFL, b, s0 + Sh::STG + pd0, s0 + Sh::STG + Sh::REGD + pd0);
+        if (p + 1 < a.npair)
+            body.pair(s1 + pd0, s1 + Sh::REGD + par * Sh::OFFL, b, s1 + Sh::STG + pd0, s1 + Sh::STG + Sh::REGD + pd0);
     }
     cpa_wait<0>();
     // u of the lane's first sample: ub + par + 16 b; x = (u + w) / 2 = ub + par + 16 b + i + o
     body.store(a, rowoff, ub + par + 16 * b);
 }
 
-template <int NH>
+// LOCAL: also the local imaging terms (alpha D L + D M2 + Ds L at h = 0) into img_local, which otherwise
+// take their own k_image_local launch re-reading D and L
+template <int NH, bool LOCAL = false>
 __global__ void __launch_bounds__(ImgShape<NH>::TX, FWIME_IMG_MINB) k_image_ps(const ImgArgs a, int u_lo)
 {
     extern __shared__ float4 sm4[];
     float *sm = reinterpret_cast<float *>(sm4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NT = ImgShape<NH>::NT;
     // warp-uniform dispatch: every warp runs the same pipeline (barriers included) with its own task
-    if (warp == 0) img_task_run<NH, 0>(a, u_lo, sm, lane);
-    if constexpr (ImgShape<NH>::NT > 1) if (warp == 1) img_task_run<NH, 1 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
-    if constexpr (ImgShape<NH>::NT > 2) if (warp == 2) img_task_run<NH, 2 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
-    if constexpr (ImgShape<NH>::NT > 3) if (warp == 3) img_task_run<NH, 3 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
-    if constexpr (ImgShape<NH>::NT > 4) if (warp == 4) img_task_run<NH, 4 % ImgShape<NH>::NT>(a, u_lo, sm, lane);
+    if (warp == 0) img_task_run<NH, 0, LOCAL>(a, u_lo, sm, lane);
+    if constexpr (NT > 1) if (warp == 1) img_task_run<NH, 1 % NT, LOCAL>(a, u_lo, sm, lane);
+    if constexpr (NT > 2) if (warp == 2) img_task_run<NH, 2 % NT, LOCAL>(a, u_lo, sm, lane);
+    if constexpr (NT > 3) if (warp == 3) img_task_run<NH, 3 % NT, LOCAL>(a, u_lo, sm, lane);
+    if constexpr (NT > 4) if (warp == 4) img_task_run<NH, 4 % NT, LOCAL>(a, u_lo, sm, lane);
 }
 
 
@@ -970,15 +1037,30 @@ static void launch_image_ps(const ImgArgs &a, cudaStream_t st)
     dim3 grid((a.x_hi + Sh::HM - u_lo + 255) / 256, a.z_hi - a.z_lo);
     // once per instantiation, before any launch (and any capture), thread-safe (function-local static)
     static const cudaError_t attr =
-        cudaFuncSetAttribute(k_image_ps<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        cudaFuncSetAttribute(k_image_ps<NH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM) ==
+                cudaSuccess
+            ? cudaFuncSetAttribute(k_image_ps<NH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEML)
+            : cudaErrorUnknown;
     (void)attr;
-    k_image_ps<NH><<<grid, Sh::TX, Sh::SMEM, st>>>(a, u_lo);
+    if (a.img_local) k_image_ps<NH, true><<<grid, Sh::TX, Sh::SMEML, st>>>(a, u_lo);
+    else k_image_ps<NH, false><<<grid, Sh::TX, Sh::SMEM, st>>>(a, u_lo);
 }
 
 template <int MODE>
 static cudaError_t launch_image_mode(const ImgArgs &a, cudaStream_t st)
 {
     if (MODE != IMG_EXT) return launch_image_gen<MODE>(a, st);
+    if (a.img_local && (a.nh != 1 && a.nh != 3 && a.nh != 5 && a.nh != 11 && a.nh != 21 && a.nh != 31 && a.nh != 41)) {
+        // generic nh: the extended image, then the local terms in their own kernel
+        ImgArgs e = a;
+        e.img_local = nullptr;
+        const cudaError_t err = launch_image_gen<MODE>(e, st);
+        if (err != cudaSuccess) return err;
+        ImgArgs l = a;
+        l.img = a.img_local;
+        l.img_local = nullptr;
+        return launch_image(l, IMG_LOCAL, st);
+    }
     switch (a.nh) {
     case 1: launch_image_ps<1>(a, st); break;
     case 3: launch_image_ps<3>(a, st); break;
