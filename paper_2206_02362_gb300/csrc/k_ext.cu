@@ -906,13 +906,8 @@ __device__ __forceinline__ void img_task_run(const ImgArgs &a, int u_lo, float *
 
 // LOCAL: also the local imaging terms (alpha D L + D M2 + Ds L at h = 0) into img_local, which otherwise
 // take their own k_image_local launch re-reading D and L
-// The fused variant needs 155-164 registers; at nh 31 (the gradient of the North-Sea-shaped workload) it fits
-// 128 without spills, which keeps 4 CTAs per SM instead of 3
-template <int NH, bool LOCAL>
-constexpr int img_min_blocks() { return LOCAL && NH == 31 ? 65536 / (128 * ImgShape<NH>::TX) : FWIME_IMG_MINB; }
-
 template <int NH, bool LOCAL = false>
-__global__ void __launch_bounds__(ImgShape<NH>::TX, (img_min_blocks<NH, LOCAL>())) k_image_ps(const ImgArgs a, int u_lo)
+__global__ void __launch_bounds__(ImgShape<NH>::TX, FWIME_IMG_MINB) k_image_ps(const ImgArgs a, int u_lo)
 {
     extern __shared__ float4 sm4[];
     float *sm = reinterpret_cast<float *>(sm4);
